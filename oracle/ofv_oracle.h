@@ -1,0 +1,49 @@
+/*
+ * FP64 CPU oracle of the dense optical-flow velocimetry estimator.
+ * TEST INFRASTRUCTURE ONLY: called by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the estimator.  Shares nothing with
+ * the CUDA path.  Definitions and citations are in ofv_oracle.c.
+ */
+#ifndef OFV_ORACLE_H
+#define OFV_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int psl;              /* pyramid sub-levels; levels 0..psl (PSL = 0: no pyramid) */
+    int kr;               /* kernel radius: window (2KR+1)^2 */
+    int it;               /* Gauss-Newton iterations per level */
+    int nr;               /* normalization radius; 0 = off */
+    int bits;             /* > 0: inputs are counts, I = raw / (2^bits - 1) */
+    int prefilter;        /* 1: 5x5 correlation with w25 after normalization */
+    const double *w25;    /* row-major 5x5 weights (used when prefilter = 1) */
+    double eps_rel;       /* relative determinant guard */
+    double eps_abs;       /* absolute trace guard */
+    double eps_n;         /* normalization floor */
+    int increment_form;   /* 1: V = V0(m) + H^-1 sum G(-It) instead of the direct form */
+} orc_params;
+
+void orc_scale(int64_t n, const double *raw, int bits, double *out);
+void orc_normalize(int H, int W, const double *I, int nr, double eps_n, double *out);
+void orc_prefilter(int H, int W, const double *I, const double *w25, double *out);
+void orc_reduce(int H, int W, const double *P, double *out);
+double orc_bilinear(const double *P, int H, int W, double px, double py);
+void orc_central_diff(int H, int W, const double *P, double *Dx, double *Dy);
+void orc_box_sum(int H, int W, const double *in, int kr, double *out);
+void orc_upsample(int Hc, int Wc, const double *uc, const double *vc, int H, int W,
+                  double *u, double *v);
+int orc_iterate(int H, int W, const double *P1, const double *P2, const double *u0,
+                const double *v0, int kr, double eps_rel, double eps_abs, int increment_form,
+                double *u, double *v, double *ndet, unsigned char *guarded);
+void orc_level_sizes(int H, int W, int psl, int *Hs, int *Ws);
+int orc_ingest(int H, int W, const double *raw, const orc_params *p, double *out);
+int orc_pyramid(int H, int W, const double *raw, const orc_params *p, double *out);
+int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_params *p,
+             double *u, double *v, double *ndet, unsigned char *guard0);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
