@@ -1,0 +1,169 @@
+/*
+ * ofv.h -- C ABI of the GB300 (sm_103a) dense optical-flow velocimetry
+ * estimator of Pimienta & Aider, "High Resolution and High-Speed Live Optical
+ * Flow Velocimetry" (arXiv 2509.25924).
+ *
+ * The estimator turns two frames I^t, I^t' into one displacement vector
+ * V = (u, v) per pixel, in px/frame (the velocity is V / dt; Eq. 1).  It
+ * follows the six-step pipeline of Sec. 2: local intensity normalization,
+ * Burt-Adelson Gaussian pyramid with PSL sub-levels, per-pixel Lucas-Kanade
+ * estimate minimising the symmetric SSD of Eq. 2 by IT Gauss-Newton
+ * iterations over a (2KR+1)^2 window, and x2 up-sampling of the field from
+ * each level to the next finer one.
+ *
+ * Conventions shared by every entry point
+ *   - Images and fields are dense row-major H x W arrays (no row padding):
+ *     element (i, j) is row i, column j, at offset i*W + j.  u is the
+ *     displacement along +x (columns), v along +y (rows), attributed to the
+ *     pixel centre taken as the midpoint between the two exposures.
+ *   - Unless an entry point says "host", every data pointer is a device
+ *     pointer of the device that was current when the handle was created.
+ *     The caller owns all image, field and weight buffers; the handle owns
+ *     its workspace (pyramids, ping-pong fields, staging).
+ *   - Work is enqueued on the given stream (NULL = the legacy default stream)
+ *     and the call returns without synchronising; results are valid once the
+ *     stream has reached them.  Buffers passed to a call must stay valid until
+ *     then.
+ *   - No exception crosses the ABI.  Every call returns an ofv_status.
+ *     Argument and shape errors are detected on the host before any work is
+ *     enqueued.  An asynchronous device error is reported as OFV_ERR_CUDA by
+ *     the call that observes it.  ofv_last_error() describes the most recent
+ *     failure in the calling thread.
+ *   - A handle is not thread-safe.  Distinct handles on distinct streams are
+ *     independent.
+ */
+#ifndef OFV_H
+#define OFV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t / CUstream. */
+typedef struct CUstream_st *ofv_stream_t;
+
+typedef enum {
+    OFV_OK = 0,
+    OFV_ERR_INVALID_ARG = 1, /* null pointer, out-of-range parameter */
+    OFV_ERR_SHAPE = 2,       /* image too small for PSL and KR, or too large */
+    OFV_ERR_ALLOC = 3,       /* device or pinned-host allocation failed */
+    OFV_ERR_CUDA = 4,        /* a CUDA call failed (message in ofv_last_error) */
+    OFV_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    OFV_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} ofv_status;
+
+typedef enum { OFV_IN_U8 = 0, OFV_IN_U16 = 1, OFV_IN_F32 = 2 } ofv_input_t;
+
+/* Storage of the level images (normalized input and pyramid).  Sums, solve
+   and fields are always FP32. */
+typedef enum { OFV_STORE_F32 = 0, OFV_STORE_F16 = 1, OFV_STORE_BF16 = 2 } ofv_storage_t;
+
+/* OFV_PATH_FUSED: one kernel per (level, iteration) doing warp, gradients,
+   products, separable window sums and the solve in shared memory.
+   OFV_PATH_PLAIN: the same arithmetic split into separate kernels that pass
+   five product planes through device memory (kept for comparison). */
+typedef enum { OFV_PATH_FUSED = 0, OFV_PATH_PLAIN = 1 } ofv_path_t;
+
+typedef struct {
+    int levels_psl;     /* PSL >= 0 pyramid sub-levels; levels = PSL + 1 (Sec. 2; Table 2 uses 2..4) */
+    int kernel_radius;  /* KR, 1..16: window (2KR+1)^2, uniform weights (Sec. 2; Table 2 uses 2..7) */
+    int iterations;     /* IT, 1..64 Gauss-Newton iterations per level (Sec. 2; Table 2 uses 1..4) */
+    int norm_radius;    /* NR, 0..16 local normalization radius; 0 = off (Sec. 2; Table 2 uses 1..4) */
+    int input;          /* ofv_input_t of the frames passed to compute calls */
+    int bit_depth;      /* integer inputs: significant bits, 1..16 (u8: <= 8); I = raw / (2^bits - 1) */
+    int storage;        /* ofv_storage_t */
+    int path;           /* ofv_path_t */
+    int prefilter;      /* 1: 5x5 correlation (weights set by ofv_set_prefilter) after normalization */
+    float det_rel_eps;  /* guard: keep V0 where det <= eps * (Sxx + Syy)^2 (default 1e-6) */
+    float det_abs_eps;  /* guard: keep V0 where Sxx + Syy <= eps (default 1e-20) */
+    float norm_eps;     /* normalization floor: (I - mu) / sqrt(var + eps^2) (default 1e-2) */
+} ofv_params;
+
+typedef struct ofv_handle ofv_handle;
+
+/* Fill *p with the defaults: PSL 2, KR 4, IT 3, NR 0, 12-bit uint16 input,
+   FP32 storage, fused path, no pre-filter, guards 1e-6 / 1e-20, floor 1e-2. */
+void ofv_default_params(ofv_params *p);
+
+/* Create a handle for H x W frames with parameters *p (copied).  Allocates
+   the whole workspace on the current device.  Every level must be at least
+   max(8, 2KR+1) pixels in both dimensions (else OFV_ERR_SHAPE); H * W must
+   not exceed 2^31 - 1.  On failure *out is set to NULL and nothing leaks. */
+ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out);
+
+/* Free the handle and its workspace (synchronises the device work it owns).
+   NULL is accepted. */
+ofv_status ofv_destroy(ofv_handle *h);
+
+/* Copy the 25 pre-filter weights (row-major 5x5, device pointer) into the
+   handle, on stream s.  out(i,j) = sum_{a,b=-2..2} w[(a+2)*5+(b+2)] * I(i+a, j+b),
+   clamp-to-edge.  Only meaningful when params.prefilter = 1; the weights
+   start as the identity (1 at the centre). */
+ofv_status ofv_set_prefilter(ofv_handle *h, const float *w25, ofv_stream_t s);
+
+/* Estimate the displacement field between frames I1 (time t) and I2 (time
+   t + dt), both H x W of the handle's input type.  Writes u and v (H x W
+   float each).  I1, I2, u and v are device pointers; u and v must not alias
+   the inputs. */
+ofv_status ofv_compute(ofv_handle *h, const void *I1, const void *I2, float *u, float *v,
+                       ofv_stream_t s);
+
+/* As ofv_compute, but I1, I2, u and v are HOST pointers.  The frames are
+   copied to handle-owned device staging, the field is copied back, all on
+   stream s; the host outputs are valid once s has been synchronised.  Use
+   page-locked host memory for asynchronous copies. */
+ofv_status ofv_compute_host(ofv_handle *h, const void *I1, const void *I2, float *u, float *v,
+                            ofv_stream_t s);
+
+/* Time-resolved sequence: n_frames >= 2 frames F_0..F_{n-1}, frame k at
+   frames + k * frame_stride_bytes (device), give n_frames - 1 fields, pair
+   k = (F_k, F_{k+1}), written to u + k * field_stride and v + k * field_stride
+   (elements).  Each frame is normalized and reduced once and its pyramid is
+   reused by the two pairs it belongs to. */
+ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
+                                size_t frame_stride_bytes, float *u, float *v, size_t field_stride,
+                                ofv_stream_t s);
+
+/* Dimensions of pyramid level l (0 = full resolution). */
+ofv_status ofv_level_shape(const ofv_handle *h, int level, int *H, int *W);
+
+/* Copy level l of frame f (0 = I1, 1 = I2) of the last computed pair, as
+   dense FP32, into dst (device, level H x W floats). */
+ofv_status ofv_read_level(ofv_handle *h, int frame, int level, float *dst, ofv_stream_t s);
+
+/* ---- kernel timing --------------------------------------------------- */
+/* Kernel classes reported by ofv_profile_read. */
+typedef enum {
+    OFV_K_INGEST = 0,   /* scale (+ normalize, + pre-filter) into level 0 */
+    OFV_K_REDUCE = 1,   /* one pyramid reduction, both frames */
+    OFV_K_ITERATE = 2,  /* one Gauss-Newton iteration of one level (the fused kernel,
+                           or the group of kernels of the plain path) */
+    OFV_K_COUNT = 3
+} ofv_kernel_class;
+
+/* enable != 0: from now on every launch of this handle is bracketed by CUDA
+   events on its stream; disable to stop.  Enabling clears earlier records. */
+ofv_status ofv_profile_enable(ofv_handle *h, int enable);
+
+/* Synchronise the recorded events and report, for kernel class k, the total
+   device time (ms), the number of launches and the algorithmic bytes those
+   launches must move (inputs read once, outputs written once). */
+ofv_status ofv_profile_read(ofv_handle *h, int k, double *total_ms, int64_t *launches,
+                            double *alg_bytes);
+
+/* Message describing the most recent failure in the calling thread. */
+const char *ofv_last_error(void);
+
+/* Name of a status code. */
+const char *ofv_status_string(ofv_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int ofv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFV_H */

@@ -1,0 +1,229 @@
+"""Python binding of the GB300 optical-flow velocimetry library (libofv.so).
+
+Argument marshalling only: every step of the estimator runs in the CUDA
+kernels behind the C ABI declared in ``include/ofv.h``.  Functions carry the
+C names.  Device buffers are passed as torch CUDA tensors (or raw integer
+addresses); streams as ``torch.cuda.Stream`` objects (or raw handles); the
+current torch stream is used when none is given.
+
+Importing this package loads libofv.so and raises if it is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter",
+    "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_level_shape", "ofv_read_level",
+    "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
+    "Flow", "lib_path", "EXPORTED_SYMBOLS",
+]
+
+OFV_OK, OFV_ERR_INVALID_ARG, OFV_ERR_SHAPE, OFV_ERR_ALLOC, OFV_ERR_CUDA, OFV_ERR_TIMEOUT, OFV_ERR_UNSUPPORTED = range(7)
+OFV_IN_U8, OFV_IN_U16, OFV_IN_F32 = range(3)
+OFV_STORE_F32, OFV_STORE_F16, OFV_STORE_BF16 = range(3)
+OFV_PATH_FUSED, OFV_PATH_PLAIN = range(2)
+OFV_K_INGEST, OFV_K_REDUCE, OFV_K_ITERATE, OFV_K_COUNT = range(4)
+
+EXPORTED_SYMBOLS = [
+    "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_compute",
+    "ofv_compute_host", "ofv_compute_sequence", "ofv_level_shape", "ofv_read_level",
+    "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
+]
+
+
+class OfvError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {_status_name(status)}: {message}")
+
+
+class Params(ctypes.Structure):
+    """Mirror of ofv_params (include/ofv.h)."""
+    _fields_ = [
+        ("levels_psl", ctypes.c_int), ("kernel_radius", ctypes.c_int), ("iterations", ctypes.c_int),
+        ("norm_radius", ctypes.c_int), ("input", ctypes.c_int), ("bit_depth", ctypes.c_int),
+        ("storage", ctypes.c_int), ("path", ctypes.c_int), ("prefilter", ctypes.c_int),
+        ("det_rel_eps", ctypes.c_float), ("det_abs_eps", ctypes.c_float), ("norm_eps", ctypes.c_float),
+    ]
+
+
+def _load_library():
+    path = _build.LIB
+    if not os.path.exists(path):
+        path = _build.build_library()
+    lib = ctypes.CDLL(path)
+    P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "ofv_default_params": ([ctypes.POINTER(Params)], None),
+        "ofv_create": ([I, I, ctypes.POINTER(Params), ctypes.POINTER(P)], I),
+        "ofv_destroy": ([P], I),
+        "ofv_set_prefilter": ([P, P, P], I),
+        "ofv_compute": ([P, P, P, P, P, P], I),
+        "ofv_compute_host": ([P, P, P, P, P, P], I),
+        "ofv_compute_sequence": ([P, I, P, Z, P, P, Z, P], I),
+        "ofv_level_shape": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "ofv_read_level": ([P, I, I, P, P], I),
+        "ofv_profile_enable": ([P, I], I),
+        "ofv_profile_read": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_double)], I),
+        "ofv_last_error": ([], ctypes.c_char_p),
+        "ofv_status_string": ([I], ctypes.c_char_p),
+        "ofv_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib, path
+
+
+_lib, lib_path = _load_library()
+
+
+def _status_name(st: int) -> str:
+    return _lib.ofv_status_string(st).decode()
+
+
+def _check(st: int, where: str):
+    if st != OFV_OK:
+        raise OfvError(st, where, _lib.ofv_last_error().decode())
+
+
+def _addr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy array (host)
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# --- C names ----------------------------------------------------------------
+def ofv_default_params(**overrides) -> Params:
+    p = Params()
+    _lib.ofv_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"ofv_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+def ofv_create(H: int, W: int, params: Params | None = None) -> int:
+    params = params or ofv_default_params()
+    h = ctypes.c_void_p()
+    _check(_lib.ofv_create(H, W, ctypes.byref(params), ctypes.byref(h)), "ofv_create")
+    return h.value
+
+
+def ofv_destroy(h: int):
+    _check(_lib.ofv_destroy(h), "ofv_destroy")
+
+
+def ofv_set_prefilter(h: int, w25, stream=None):
+    _check(_lib.ofv_set_prefilter(h, _addr(w25), _stream(stream)), "ofv_set_prefilter")
+
+
+def ofv_compute(h: int, I1, I2, u, v, stream=None):
+    _check(_lib.ofv_compute(h, _addr(I1), _addr(I2), _addr(u), _addr(v), _stream(stream)), "ofv_compute")
+
+
+def ofv_compute_host(h: int, I1, I2, u, v, stream=None):
+    _check(_lib.ofv_compute_host(h, _addr(I1), _addr(I2), _addr(u), _addr(v), _stream(stream)),
+           "ofv_compute_host")
+
+
+def ofv_compute_sequence(h: int, n_frames: int, frames, frame_stride_bytes: int, u, v, field_stride: int,
+                         stream=None):
+    _check(_lib.ofv_compute_sequence(h, n_frames, _addr(frames), frame_stride_bytes, _addr(u), _addr(v),
+                                     field_stride, _stream(stream)), "ofv_compute_sequence")
+
+
+def ofv_level_shape(h: int, level: int):
+    H, W = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.ofv_level_shape(h, level, ctypes.byref(H), ctypes.byref(W)), "ofv_level_shape")
+    return H.value, W.value
+
+
+def ofv_read_level(h: int, frame: int, level: int, dst, stream=None):
+    _check(_lib.ofv_read_level(h, frame, level, _addr(dst), _stream(stream)), "ofv_read_level")
+
+
+def ofv_profile_enable(h: int, enable: bool):
+    _check(_lib.ofv_profile_enable(h, 1 if enable else 0), "ofv_profile_enable")
+
+
+def ofv_profile_read(h: int, k: int):
+    ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.ofv_profile_read(h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)), "ofv_profile_read")
+    return ms.value, n.value, b.value
+
+
+def ofv_last_error() -> str:
+    return _lib.ofv_last_error().decode()
+
+
+def ofv_status_string(st: int) -> str:
+    return _status_name(st)
+
+
+def ofv_version() -> int:
+    return _lib.ofv_version()
+
+
+# --- convenience --------------------------------------------------------------
+_IN_DTYPE = {OFV_IN_U8: "uint8", OFV_IN_U16: "uint16", OFV_IN_F32: "float32"}
+
+
+class Flow:
+    """Owns one ofv handle for H x W frames.
+
+    ``Flow(H, W, **params)`` with ofv_params field names; ``flow(I1, I2)``
+    returns (u, v) as new float32 CUDA tensors on the current stream."""
+
+    def __init__(self, H: int, W: int, params: Params | None = None, **overrides):
+        self.params = params or ofv_default_params(**overrides)
+        self.H, self.W = H, W
+        self.h = ofv_create(H, W, self.params)
+
+    def __call__(self, I1, I2, u=None, v=None, stream=None):
+        import torch
+        for t in (I1, I2):
+            if not (t.is_cuda and t.is_contiguous() and tuple(t.shape) == (self.H, self.W)):
+                raise ValueError("frames must be contiguous CUDA tensors of shape (H, W)")
+            if str(t.dtype).split(".")[-1] != _IN_DTYPE[self.params.input]:
+                raise TypeError(f"frames must be {_IN_DTYPE[self.params.input]}")
+        if u is None:
+            u = torch.empty((self.H, self.W), dtype=torch.float32, device=I1.device)
+        if v is None:
+            v = torch.empty((self.H, self.W), dtype=torch.float32, device=I1.device)
+        ofv_compute(self.h, I1, I2, u, v, stream)
+        return u, v
+
+    def close(self):
+        if getattr(self, "h", None):
+            ofv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,598 @@
+// C ABI of the OFV estimator: handle, workspace, argument checks and the
+// level loop of Sec. 2 (normalize -> pyramid -> per level IT Gauss-Newton
+// iterations of Eq. 2 -> up-sample to the next finer level).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ofv.h"
+#include "ofv_common.cuh"
+
+using namespace ofv;
+
+namespace {
+
+thread_local char g_err[1024] = "no error";
+
+ofv_status fail(ofv_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+ofv_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(OFV_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+constexpr int kMaxLevels = 16;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int store_bytes(int st) { return st == OFV_STORE_F32 ? 4 : 2; }
+int input_bytes(int in) { return in == OFV_IN_U8 ? 1 : (in == OFV_IN_U16 ? 2 : 4); }
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double bytes;
+};
+
+}  // namespace
+
+struct ofv_handle {
+    int H, W;
+    ofv_params p;
+    int L;
+    int Hs[kMaxLevels], Ws[kMaxLevels], pitch[kMaxLevels];
+    int vpitch;
+    int device;
+    void *arena;
+    size_t arena_bytes;
+    void *lvl[2][kMaxLevels];  // two pyramid slots
+    float2 *vbuf[2];
+    float *w25;
+    float *tmp[2];
+    PlainBufs plain;
+    // host-pointer entry point staging (allocated on first use)
+    void *stage;
+    size_t stage_bytes;
+    // which slot holds I1 of the last computed pair
+    int last_slot1;
+    // kernel timing
+    bool prof;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_next;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+ofv_status check_params(const ofv_params *p)
+{
+    if (!p) return fail(OFV_ERR_INVALID_ARG, "params is NULL");
+    if (p->levels_psl < 0 || p->levels_psl > kMaxLevels - 1)
+        return fail(OFV_ERR_INVALID_ARG, "levels_psl=%d outside 0..%d", p->levels_psl, kMaxLevels - 1);
+    if (p->kernel_radius < 1 || p->kernel_radius > 16)
+        return fail(OFV_ERR_INVALID_ARG, "kernel_radius=%d outside 1..16", p->kernel_radius);
+    if (p->iterations < 1 || p->iterations > 64)
+        return fail(OFV_ERR_INVALID_ARG, "iterations=%d outside 1..64", p->iterations);
+    if (p->norm_radius < 0 || p->norm_radius > 16)
+        return fail(OFV_ERR_INVALID_ARG, "norm_radius=%d outside 0..16", p->norm_radius);
+    if (p->input != OFV_IN_U8 && p->input != OFV_IN_U16 && p->input != OFV_IN_F32)
+        return fail(OFV_ERR_INVALID_ARG, "input=%d is not an ofv_input_t", p->input);
+    if (p->input != OFV_IN_F32) {
+        const int maxb = p->input == OFV_IN_U8 ? 8 : 16;
+        if (p->bit_depth < 1 || p->bit_depth > maxb)
+            return fail(OFV_ERR_INVALID_ARG, "bit_depth=%d outside 1..%d", p->bit_depth, maxb);
+    }
+    if (p->storage != OFV_STORE_F32 && p->storage != OFV_STORE_F16 && p->storage != OFV_STORE_BF16)
+        return fail(OFV_ERR_INVALID_ARG, "storage=%d is not an ofv_storage_t", p->storage);
+    if (p->path != OFV_PATH_FUSED && p->path != OFV_PATH_PLAIN)
+        return fail(OFV_ERR_INVALID_ARG, "path=%d is not an ofv_path_t", p->path);
+    if (p->prefilter != 0 && p->prefilter != 1)
+        return fail(OFV_ERR_INVALID_ARG, "prefilter=%d is not 0 or 1", p->prefilter);
+    if (!(p->det_rel_eps >= 0.f) || !std::isfinite(p->det_rel_eps) || !(p->det_abs_eps >= 0.f) ||
+        !std::isfinite(p->det_abs_eps) || !(p->norm_eps > 0.f) || !std::isfinite(p->norm_eps))
+        return fail(OFV_ERR_INVALID_ARG, "guard / normalization epsilons must be finite (norm_eps > 0)");
+    return OFV_OK;
+}
+
+ofv_status last_launch(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return OFV_OK;
+}
+
+cudaEvent_t pool_event(ofv_handle *h)
+{
+    if (h->pool_next < h->pool.size()) return h->pool[h->pool_next++];
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->pool.push_back(e);
+    h->pool_next = h->pool.size();
+    return e;
+}
+
+// Bracket a launch with events when timing is on.
+struct ProfScope {
+    ofv_handle *h;
+    cudaStream_t s;
+    int cls;
+    double bytes;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(ofv_handle *h_, cudaStream_t s_, int cls_, double bytes_) : h(h_), s(s_), cls(cls_), bytes(bytes_)
+    {
+        if (h->prof) {
+            e0 = pool_event(h);
+            if (e0) cudaEventRecord(e0, s);
+        }
+    }
+    ~ProfScope()
+    {
+        if (h->prof && e0) {
+            cudaEvent_t e1 = pool_event(h);
+            if (e1) {
+                cudaEventRecord(e1, s);
+                h->recs.push_back(ProfRec{cls, e0, e1, bytes});
+            }
+        }
+    }
+};
+
+// Stage 1-2: ingest frames into pyramid slots and reduce.  frames[k] goes to
+// slot slots[k].
+ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf,
+                          cudaStream_t s)
+{
+    const ofv_params &p = h->p;
+    const int sb = store_bytes(p.storage), ib = input_bytes(p.input);
+    IngestArgs ia[2];
+    for (int k = 0; k < nf; ++k) {
+        IngestArgs &a = ia[k];
+        a.raw = frames[k];
+        a.out = h->lvl[slots[k]][0];
+        a.tmp = h->tmp[k];
+        a.w25 = h->w25;
+        a.H = h->H;
+        a.W = h->W;
+        a.pitch = h->pitch[0];
+        a.in_type = p.input;
+        a.bits = p.bit_depth;
+        a.nr = p.norm_radius;
+        a.eps_n = p.norm_eps;
+        a.prefilter = p.prefilter;
+    }
+    {
+        const double N = (double)h->H * h->W;
+        ProfScope ps(h, s, OFV_K_INGEST, nf * N * (ib + sb));
+        ofv_status st = last_launch(launch_ingest_frames(ia, nf, p.storage, s), "ingest launch");
+        if (st != OFV_OK) return st;
+    }
+    for (int l = 1; l < h->L; ++l) {
+        ReduceArgs ra[2];
+        for (int k = 0; k < nf; ++k) {
+            ReduceArgs &r = ra[k];
+            r.src = h->lvl[slots[k]][l - 1];
+            r.Hs = h->Hs[l - 1];
+            r.Ws = h->Ws[l - 1];
+            r.spitch = h->pitch[l - 1];
+            r.dst = h->lvl[slots[k]][l];
+            r.Hd = h->Hs[l];
+            r.Wd = h->Ws[l];
+            r.dpitch = h->pitch[l];
+        }
+        const double bytes = nf * (double)sb * ((double)h->Hs[l - 1] * h->Ws[l - 1] + (double)h->Hs[l] * h->Ws[l]);
+        ProfScope ps(h, s, OFV_K_REDUCE, bytes);
+        ofv_status st = last_launch(launch_reduce_frames(ra, nf, p.storage, s), "reduce launch");
+        if (st != OFV_OK) return st;
+    }
+    return OFV_OK;
+}
+
+// Stages 3-6: coarse-to-fine Gauss-Newton on the pyramids in slots s1, s2.
+ofv_status run_levels(ofv_handle *h, int s1, int s2, float *u, float *v, cudaStream_t s)
+{
+    const ofv_params &p = h->p;
+    const int sb = store_bytes(p.storage);
+    int cur = 0;  // index of the vbuf holding the latest field
+    bool have = false;
+    for (int l = h->L - 1; l >= 0; --l) {
+        for (int t = 0; t < p.iterations; ++t) {
+            IterArgs a;
+            memset(&a, 0, sizeof a);
+            a.P1 = h->lvl[s1][l];
+            a.P2 = h->lvl[s2][l];
+            a.H = h->Hs[l];
+            a.W = h->Ws[l];
+            a.pitch = h->pitch[l];
+            a.vpitch = h->vpitch;
+            a.vcpitch = h->vpitch;
+            a.kr = p.kernel_radius;
+            a.eps_rel = p.det_rel_eps;
+            a.eps_abs = p.det_abs_eps;
+            int mode;
+            const double Nl = (double)a.H * a.W;
+            double vread = 0.0;
+            if (t == 0 && l == h->L - 1) {
+                mode = V0_ZERO;
+            } else if (t == 0) {
+                mode = V0_UP;
+                a.Vc = h->vbuf[cur];
+                a.Hc = h->Hs[l + 1];
+                a.Wc = h->Ws[l + 1];
+                vread = 8.0 * a.Hc * a.Wc;
+            } else {
+                mode = V0_SAME;
+                a.V0 = h->vbuf[cur];
+                vread = 8.0 * Nl;
+            }
+            const bool last = (l == 0 && t == p.iterations - 1);
+            const int nxt = have ? 1 - cur : 0;
+            if (last) {
+                a.u_out = u;
+                a.v_out = v;
+            } else {
+                a.Vout = h->vbuf[nxt];
+            }
+            const double bytes = 2.0 * sb * Nl + 8.0 * Nl + vread;
+            ProfScope ps(h, s, OFV_K_ITERATE, bytes);
+            cudaError_t e = p.path == OFV_PATH_PLAIN ? launch_iter_plain(a, h->plain, p.storage, mode, s)
+                                                     : launch_iter_fused(a, p.storage, mode, s);
+            ofv_status st = last_launch(e, "iteration launch");
+            if (st != OFV_OK) return st;
+            cur = nxt;
+            have = true;
+        }
+    }
+    return OFV_OK;
+}
+
+ofv_status pending_error(const char *where)
+{
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, where);
+    }
+    return OFV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ofv_default_params(ofv_params *p)
+{
+    if (!p) return;
+    p->levels_psl = 2;
+    p->kernel_radius = 4;
+    p->iterations = 3;
+    p->norm_radius = 0;
+    p->input = OFV_IN_U16;
+    p->bit_depth = 12;
+    p->storage = OFV_STORE_F32;
+    p->path = OFV_PATH_FUSED;
+    p->prefilter = 0;
+    p->det_rel_eps = 1e-6f;
+    p->det_abs_eps = 1e-20f;
+    p->norm_eps = 1e-2f;
+}
+
+ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
+{
+    if (!out) return fail(OFV_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    ofv_status st = check_params(p);
+    if (st != OFV_OK) return st;
+    if (H < 1 || W < 1) return fail(OFV_ERR_SHAPE, "H=%d W=%d must be positive", H, W);
+    if ((int64_t)H * W > 2147483647LL) return fail(OFV_ERR_SHAPE, "H*W=%lld exceeds 2^31-1", (long long)H * W);
+    const int L = p->levels_psl + 1;
+    int Hs[kMaxLevels], Ws[kMaxLevels];
+    Hs[0] = H;
+    Ws[0] = W;
+    for (int l = 1; l < L; ++l) {
+        Hs[l] = (Hs[l - 1] + 1) / 2;
+        Ws[l] = (Ws[l - 1] + 1) / 2;
+    }
+    const int minsz = 2 * p->kernel_radius + 1 > 8 ? 2 * p->kernel_radius + 1 : 8;
+    if (Hs[L - 1] < minsz || Ws[L - 1] < minsz)
+        return fail(OFV_ERR_SHAPE, "coarsest level %dx%d is below max(8, 2KR+1)=%d (H=%d W=%d PSL=%d KR=%d)",
+                    Hs[L - 1], Ws[L - 1], minsz, H, W, p->levels_psl, p->kernel_radius);
+
+    ofv_handle *h = new (std::nothrow) ofv_handle();
+    if (!h) return fail(OFV_ERR_ALLOC, "host allocation of the handle failed");
+    h->H = H;
+    h->W = W;
+    h->p = *p;
+    h->L = L;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return fail(OFV_ERR_CUDA, "cudaGetDevice failed");
+    }
+    for (int l = 0; l < L; ++l) {
+        h->Hs[l] = Hs[l];
+        h->Ws[l] = Ws[l];
+        h->pitch[l] = pitch_for(Ws[l]);
+    }
+    h->vpitch = pitch_for(W);
+    const int sb = store_bytes(p->storage);
+
+    // arena layout
+    size_t off = 0;
+    size_t lvl_off[2][kMaxLevels];
+    for (int f = 0; f < 2; ++f)
+        for (int l = 0; l < L; ++l) {
+            lvl_off[f][l] = off;
+            off = align_up(off + (size_t)Hs[l] * h->pitch[l] * sb, 256);
+        }
+    size_t vb_off[2];
+    for (int k = 0; k < 2; ++k) {
+        vb_off[k] = off;
+        off = align_up(off + (size_t)H * h->vpitch * sizeof(float2), 256);
+    }
+    const size_t w_off = off;
+    off = align_up(off + 25 * sizeof(float), 256);
+    size_t tmp_off[2] = {0, 0};
+    if (p->prefilter)
+        for (int k = 0; k < 2; ++k) {
+            tmp_off[k] = off;
+            off = align_up(off + (size_t)H * h->pitch[0] * sizeof(float), 256);
+        }
+    size_t prod_off = 0, hsum_off = 0, vtmp_off = 0;
+    const size_t plane = (size_t)H * h->pitch[0];
+    if (p->path == OFV_PATH_PLAIN) {
+        prod_off = off;
+        off = align_up(off + 5 * plane * sizeof(float), 256);
+        hsum_off = off;
+        off = align_up(off + 5 * plane * sizeof(float), 256);
+        vtmp_off = off;
+        off = align_up(off + (size_t)H * h->vpitch * sizeof(float2), 256);
+    }
+    h->arena_bytes = off;
+    cudaError_t e = cudaMalloc(&h->arena, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(OFV_ERR_ALLOC, "cudaMalloc of %zu workspace bytes failed: %s", off, cudaGetErrorString(e));
+    }
+    char *base = static_cast<char *>(h->arena);
+    for (int f = 0; f < 2; ++f)
+        for (int l = 0; l < L; ++l) h->lvl[f][l] = base + lvl_off[f][l];
+    for (int k = 0; k < 2; ++k) h->vbuf[k] = reinterpret_cast<float2 *>(base + vb_off[k]);
+    h->w25 = reinterpret_cast<float *>(base + w_off);
+    for (int k = 0; k < 2; ++k) h->tmp[k] = p->prefilter ? reinterpret_cast<float *>(base + tmp_off[k]) : nullptr;
+    if (p->path == OFV_PATH_PLAIN) {
+        h->plain.prod = reinterpret_cast<float *>(base + prod_off);
+        h->plain.hsum = reinterpret_cast<float *>(base + hsum_off);
+        h->plain.vtmp = reinterpret_cast<float2 *>(base + vtmp_off);
+        h->plain.plane = plane;
+    }
+    float ident[25] = {0};
+    ident[12] = 1.f;
+    e = cudaMemcpy(h->w25, ident, sizeof ident, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(h->arena);
+        delete h;
+        return cuda_fail(e, "initialising the pre-filter weights");
+    }
+    h->last_slot1 = 0;
+    *out = h;
+    return OFV_OK;
+}
+
+ofv_status ofv_destroy(ofv_handle *h)
+{
+    if (!h) return OFV_OK;
+    DeviceGuard g(h->device);
+    ofv_status st = OFV_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "synchronising before destroy");
+    for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
+    if (h->stage) cudaFree(h->stage);
+    if (h->arena) cudaFree(h->arena);
+    delete h;
+    return st;
+}
+
+ofv_status ofv_set_prefilter(ofv_handle *h, const float *w25, ofv_stream_t s)
+{
+    if (!h || !w25) return fail(OFV_ERR_INVALID_ARG, "handle or weights is NULL");
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaMemcpyAsync(h->w25, w25, 25 * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e, "copying pre-filter weights");
+    return OFV_OK;
+}
+
+ofv_status ofv_compute(ofv_handle *h, const void *I1, const void *I2, float *u, float *v, ofv_stream_t s)
+{
+    if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
+    if (!I1 || !I2 || !u || !v) return fail(OFV_ERR_INVALID_ARG, "I1, I2, u and v must be non-NULL");
+    if (u == v) return fail(OFV_ERR_INVALID_ARG, "u and v must be distinct buffers");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    ofv_status st = pending_error("error pending before ofv_compute");
+    if (st != OFV_OK) return st;
+    cudaStream_t cs = (cudaStream_t)s;
+    const void *fr[2] = {I1, I2};
+    const int slots[2] = {0, 1};
+    st = build_pyramids(h, fr, slots, 2, cs);
+    if (st != OFV_OK) return st;
+    h->last_slot1 = 0;
+    return run_levels(h, 0, 1, u, v, cs);
+}
+
+ofv_status ofv_compute_host(ofv_handle *h, const void *I1, const void *I2, float *u, float *v, ofv_stream_t s)
+{
+    if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
+    if (!I1 || !I2 || !u || !v) return fail(OFV_ERR_INVALID_ARG, "I1, I2, u and v must be non-NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    const size_t N = (size_t)h->H * h->W;
+    const size_t in_b = align_up(N * input_bytes(h->p.input), 256);
+    const size_t out_b = align_up(N * sizeof(float), 256);
+    const size_t need = 2 * in_b + 2 * out_b;
+    if (!h->stage) {
+        cudaError_t e = cudaMalloc(&h->stage, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->stage = nullptr;
+            return fail(OFV_ERR_ALLOC, "cudaMalloc of %zu staging bytes failed", need);
+        }
+        h->stage_bytes = need;
+    }
+    char *b = static_cast<char *>(h->stage);
+    void *d1 = b, *d2 = b + in_b;
+    float *du = reinterpret_cast<float *>(b + 2 * in_b), *dv = reinterpret_cast<float *>(b + 2 * in_b + out_b);
+    cudaStream_t cs = (cudaStream_t)s;
+    const size_t ib = N * input_bytes(h->p.input);
+    cudaError_t e = cudaMemcpyAsync(d1, I1, ib, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d2, I2, ib, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy of the frames");
+    ofv_status st = ofv_compute(h, d1, d2, du, dv, s);
+    if (st != OFV_OK) return st;
+    e = cudaMemcpyAsync(u, du, N * sizeof(float), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, N * sizeof(float), cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy of the field");
+    return OFV_OK;
+}
+
+ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames, size_t frame_stride_bytes,
+                                float *u, float *v, size_t field_stride, ofv_stream_t s)
+{
+    if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
+    if (!frames || !u || !v) return fail(OFV_ERR_INVALID_ARG, "frames, u and v must be non-NULL");
+    if (n_frames < 2) return fail(OFV_ERR_INVALID_ARG, "n_frames=%d must be >= 2", n_frames);
+    const size_t N = (size_t)h->H * h->W;
+    if (frame_stride_bytes < N * input_bytes(h->p.input))
+        return fail(OFV_ERR_INVALID_ARG, "frame_stride_bytes=%zu is smaller than one frame", frame_stride_bytes);
+    if (field_stride < N) return fail(OFV_ERR_INVALID_ARG, "field_stride=%zu is smaller than one field", field_stride);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    ofv_status st = pending_error("error pending before ofv_compute_sequence");
+    if (st != OFV_OK) return st;
+    cudaStream_t cs = (cudaStream_t)s;
+    const char *fb = static_cast<const char *>(frames);
+    // first pair: both frames
+    {
+        const void *fr[2] = {fb, fb + frame_stride_bytes};
+        const int slots[2] = {0, 1};
+        st = build_pyramids(h, fr, slots, 2, cs);
+        if (st != OFV_OK) return st;
+    }
+    for (int k = 0; k + 1 < n_frames; ++k) {
+        const int s1 = k & 1, s2 = (k + 1) & 1;
+        if (k > 0) {
+            const void *fr[1] = {fb + (size_t)(k + 1) * frame_stride_bytes};
+            const int slots[1] = {s2};
+            st = build_pyramids(h, fr, slots, 1, cs);
+            if (st != OFV_OK) return st;
+        }
+        st = run_levels(h, s1, s2, u + (size_t)k * field_stride, v + (size_t)k * field_stride, cs);
+        if (st != OFV_OK) return st;
+        h->last_slot1 = s1;
+    }
+    return OFV_OK;
+}
+
+ofv_status ofv_level_shape(const ofv_handle *h, int level, int *H, int *W)
+{
+    if (!h || !H || !W) return fail(OFV_ERR_INVALID_ARG, "NULL argument");
+    if (level < 0 || level >= h->L) return fail(OFV_ERR_INVALID_ARG, "level=%d outside 0..%d", level, h->L - 1);
+    *H = h->Hs[level];
+    *W = h->Ws[level];
+    return OFV_OK;
+}
+
+ofv_status ofv_read_level(ofv_handle *h, int frame, int level, float *dst, ofv_stream_t s)
+{
+    if (!h || !dst) return fail(OFV_ERR_INVALID_ARG, "NULL argument");
+    if (frame != 0 && frame != 1) return fail(OFV_ERR_INVALID_ARG, "frame=%d must be 0 or 1", frame);
+    if (level < 0 || level >= h->L) return fail(OFV_ERR_INVALID_ARG, "level=%d outside 0..%d", level, h->L - 1);
+    DeviceGuard g(h->device);
+    const int slot = frame == 0 ? h->last_slot1 : 1 - h->last_slot1;
+    return last_launch(launch_read_level(h->lvl[slot][level], h->Hs[level], h->Ws[level], h->pitch[level],
+                                         h->p.storage, dst, (cudaStream_t)s),
+                       "read_level launch");
+}
+
+ofv_status ofv_profile_enable(ofv_handle *h, int enable)
+{
+    if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    if (enable) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "synchronising before enabling timing");
+        h->recs.clear();
+        h->pool_next = 0;
+    }
+    h->prof = enable != 0;
+    return OFV_OK;
+}
+
+ofv_status ofv_profile_read(ofv_handle *h, int k, double *total_ms, int64_t *launches, double *alg_bytes)
+{
+    if (!h || !total_ms || !launches || !alg_bytes) return fail(OFV_ERR_INVALID_ARG, "NULL argument");
+    if (k < 0 || k >= OFV_K_COUNT) return fail(OFV_ERR_INVALID_ARG, "kernel class %d outside 0..%d", k, OFV_K_COUNT - 1);
+    DeviceGuard g(h->device);
+    double ms = 0.0, bytes = 0.0;
+    int64_t n = 0;
+    for (const ProfRec &r : h->recs) {
+        if (r.cls != k) continue;
+        cudaError_t e = cudaEventSynchronize(r.e1);
+        if (e != cudaSuccess) return cuda_fail(e, "waiting for a timing event");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, r.e0, r.e1);
+        if (e != cudaSuccess) return cuda_fail(e, "reading a timing event");
+        ms += t;
+        bytes += r.bytes;
+        ++n;
+    }
+    *total_ms = ms;
+    *launches = n;
+    *alg_bytes = bytes;
+    return OFV_OK;
+}
+
+const char *ofv_last_error(void) { return g_err; }
+
+const char *ofv_status_string(ofv_status s)
+{
+    switch (s) {
+    case OFV_OK: return "OFV_OK";
+    case OFV_ERR_INVALID_ARG: return "OFV_ERR_INVALID_ARG";
+    case OFV_ERR_SHAPE: return "OFV_ERR_SHAPE";
+    case OFV_ERR_ALLOC: return "OFV_ERR_ALLOC";
+    case OFV_ERR_CUDA: return "OFV_ERR_CUDA";
+    case OFV_ERR_TIMEOUT: return "OFV_ERR_TIMEOUT";
+    case OFV_ERR_UNSUPPORTED: return "OFV_ERR_UNSUPPORTED";
+    }
+    return "OFV_ERR_UNKNOWN";
+}
+
+int ofv_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Shared device helpers and launch descriptors of the OFV CUDA path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace ofv {
+
+enum Store : int { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+enum In : int { IN_U8 = 0, IN_U16 = 1, IN_F32 = 2 };
+
+// Source of the field V0 that the first warp of an iteration uses.
+enum V0Mode : int {
+    V0_ZERO = 0,  // coarsest level, first iteration: V0 = 0
+    V0_SAME = 1,  // previous iteration of the same level
+    V0_UP = 2     // first iteration of a finer level: 2 * bilinear(Vc, x/2, y/2)
+};
+
+// Level images are stored with a row pitch (elements) that is a multiple of
+// 64, so every row starts 128-byte aligned in all storage types.
+constexpr int kPitchAlign = 64;
+inline int pitch_for(int w) { return (w + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
+
+__device__ __forceinline__ float ld_store(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_store(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float ld_store(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+__device__ __forceinline__ void st_store(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_store(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st_store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// One level of one pair, as seen by an iteration kernel.
+struct IterArgs {
+    const void *P1, *P2;  // level images (storage type), pitch `pitch` elements
+    int H, W, pitch;
+    const float2 *V0;     // V0_SAME: field of the previous iteration, pitch vpitch
+    const float2 *Vc;     // V0_UP: field of level l+1 (Hc x Wc), pitch vcpitch
+    int Hc, Wc, vcpitch;
+    float2 *Vout;         // interleaved output (pitch vpitch), or null when planar
+    float *u_out, *v_out; // planar dense output (level 0, last iteration)
+    int vpitch;
+    int kr;
+    float eps_rel, eps_abs;
+};
+
+// Host-side launchers (defined in the kernel translation units).
+cudaError_t launch_iter_fused(const IterArgs &a, int store, int mode, cudaStream_t s);
+
+struct PlainBufs {
+    float *prod;  // 5 planes, each H x pitch floats
+    float *hsum;  // 5 planes, each H x pitch floats
+    float2 *vtmp; // up-sampled V0 plane (pitch vpitch)
+    size_t plane; // elements per plane
+};
+cudaError_t launch_iter_plain(const IterArgs &a, const PlainBufs &b, int store, int mode,
+                              cudaStream_t s);
+
+struct IngestArgs {
+    const void *raw;   // H x W input, dense
+    void *out;         // level 0 storage, pitch elements
+    float *tmp;        // FP32 scratch (H x pitch) used when the pre-filter is on
+    const float *w25;  // pre-filter weights (device)
+    int H, W, pitch;
+    int in_type, bits;
+    int nr;
+    float eps_n;
+    int prefilter;
+};
+// Ingest nframes (1 or 2) frames in one launch.
+cudaError_t launch_ingest_frames(const IngestArgs *f, int nframes, int store, cudaStream_t s);
+
+struct ReduceArgs {
+    const void *src; int Hs, Ws, spitch;
+    void *dst; int Hd, Wd, dpitch;
+};
+// Reduce one level of nframes (1 or 2) frames in one launch.
+cudaError_t launch_reduce_frames(const ReduceArgs *f, int nframes, int store, cudaStream_t s);
+
+cudaError_t launch_read_level(const void *src, int H, int W, int pitch, int store, float *dst,
+                              cudaStream_t s);
+
+}  // namespace ofv

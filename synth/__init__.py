@@ -69,6 +69,8 @@ class _Field(ctypes.Structure):
         ("lo_x", ctypes.c_void_p), ("lo_y", ctypes.c_void_p), ("lo_gamma", ctypes.c_void_p),
         ("lo_rc", ctypes.c_double),
         ("scale", ctypes.c_double),
+        ("grid_h", ctypes.c_int64), ("grid_w", ctypes.c_int64),
+        ("grid_u", ctypes.c_void_p), ("grid_v", ctypes.c_void_p),
     ]
 
 
@@ -145,6 +147,16 @@ class Field:
     def set_scale(self, scale: float) -> "Field":
         self._s.scale = scale
         return self
+
+    def sampled(self, H: int, W: int) -> "Field":
+        """This field sampled at every pixel centre of an H x W grid and
+        interpolated bilinearly: cheap to evaluate for long particle streams."""
+        u, v = self.grid(H, W)
+        g = Field()
+        g._keep = [np.ascontiguousarray(u), np.ascontiguousarray(v)]
+        g._s.grid_h, g._s.grid_w = H, W
+        g._s.grid_u, g._s.grid_v = g._keep[0].ctypes.data, g._keep[1].ctypes.data
+        return g
 
     # -- evaluation ----------------------------------------------------
     def __call__(self, x, y):
@@ -245,14 +257,20 @@ def stream_field(H: int, W: int) -> Field:
 
 
 def stream_frames(H: int = 1024, W: int = 1024, n_frames: int = 1001, seed: int = 2,
-                  ppp: float = 0.08, bits: int = 12, noise: float = 0.01) -> np.ndarray:
+                  ppp: float = 0.08, bits: int = 12, noise: float = 0.01, field: Field | None = None,
+                  field_max: float = 5.0, exclude=None) -> np.ndarray:
     """Time-resolved 12-bit sequence (n_frames x H x W uint16) of particles
-    advected by a steady Rankine vortex (R 32 px, 3 px peak) plus a uniform
-    (1.3, -0.7) px/frame shift.  Pair i is (F_i, F_{i+1})."""
-    f = stream_field(H, W)
-    m = _margin(5.0, 3.0)
+    advected by a steady field, by default a Rankine vortex (R 32 px, 3 px
+    peak) plus a uniform (1.3, -0.7) px/frame shift.  Pair i is (F_i, F_{i+1}).
+    ``exclude(x, y)`` drops particles whose starting position it flags."""
+    f = stream_field(H, W) if field is None else field
+    m = _margin(field_max, 3.0)
     n = int(round(ppp * (W + 2 * m) * (H + 2 * m)))
     x, y, sg, a = particles(seed, n, -m, W + m, -m, H + m, 2.0, 3.0)
+    if exclude is not None:
+        keep = ~exclude(x, y)
+        x, y, sg, a = [np.ascontiguousarray(t[keep]) for t in (x, y, sg, a)]
+        n = x.size
     out = np.empty((n_frames, H, W), dtype=np.uint16)
     rc = _load().syn_stream(H, W, n_frames, n, _ptr(x), _ptr(y), _ptr(sg), _ptr(a), ctypes.byref(f._s),
                             m, noise, seed + 1000003, bits, OUT_U16, _ptr(out))

@@ -97,7 +97,29 @@ typedef struct {
     double lo_rc;
     /* overall multiplier applied to the sum of all parts */
     double scale;
+    /* when grid_h > 0 the field is instead the bilinear interpolation
+       (clamp-to-edge) of displacements sampled at every pixel centre of a
+       grid_h x grid_w grid (used to advect long particle streams cheaply) */
+    int64_t grid_h, grid_w;
+    const double *grid_u, *grid_v;
 } syn_field;
+
+static void grid_at(const syn_field *f, double x, double y, double *dx, double *dy)
+{
+    double fx0 = floor(x), fy0 = floor(y);
+    double fx = x - fx0, fy = y - fy0;
+    int64_t x0 = (int64_t)fx0, y0 = (int64_t)fy0;
+    int64_t xa = x0 < 0 ? 0 : (x0 > f->grid_w - 1 ? f->grid_w - 1 : x0);
+    int64_t xb = x0 + 1 < 0 ? 0 : (x0 + 1 > f->grid_w - 1 ? f->grid_w - 1 : x0 + 1);
+    int64_t ya = y0 < 0 ? 0 : (y0 > f->grid_h - 1 ? f->grid_h - 1 : y0);
+    int64_t yb = y0 + 1 < 0 ? 0 : (y0 + 1 > f->grid_h - 1 ? f->grid_h - 1 : y0 + 1);
+    const double *U = f->grid_u, *V = f->grid_v;
+    int64_t W = f->grid_w;
+    *dx = (1 - fy) * ((1 - fx) * U[ya * W + xa] + fx * U[ya * W + xb]) +
+          fy * ((1 - fx) * U[yb * W + xa] + fx * U[yb * W + xb]);
+    *dy = (1 - fy) * ((1 - fx) * V[ya * W + xa] + fx * V[ya * W + xb]) +
+          fy * ((1 - fx) * V[yb * W + xa] + fx * V[yb * W + xb]);
+}
 
 /* Rankine displacement at midpoint (x, y).  A particle at radius r turns by
    phi(r) = u_theta(r) / r about the centre; frame 1 and frame 2 hold it at
@@ -135,6 +157,13 @@ void syn_field_eval(const syn_field *f, int64_t n, const double *x, const double
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double px = x[i], py = y[i];
+        if (f->grid_h > 0) {
+            double gx, gy;
+            grid_at(f, px, py, &gx, &gy);
+            dx[i] = f->scale * gx;
+            dy[i] = f->scale * gy;
+            continue;
+        }
         double sx = f->ux, sy = f->uy;
         if (f->rk_R > 0.0) {
             double ax, ay;
@@ -219,10 +248,19 @@ static void render_rows(int H, int W, int r0, int r1, int64_t n, const double *x
         if (j1 > W - 1) j1 = W - 1;
         if (j1 < j0 || i1 < i0) continue;
         double inv = 1.0 / (sqrt(2.0) * s);
-        for (int j = j0; j <= j1; ++j)
-            ex[j - j0] = erf((j + 0.5 - x[p]) * inv) - erf((j - 0.5 - x[p]) * inv);
-        for (int i = i0; i <= i1; ++i)
-            ey[i - i0] = erf((i + 0.5 - y[p]) * inv) - erf((i - 0.5 - y[p]) * inv);
+        /* adjacent pixels share a boundary: one erf per pixel edge */
+        double lo = erf((j0 - 0.5 - x[p]) * inv);
+        for (int j = j0; j <= j1; ++j) {
+            double hi = erf((j + 0.5 - x[p]) * inv);
+            ex[j - j0] = hi - lo;
+            lo = hi;
+        }
+        lo = erf((i0 - 0.5 - y[p]) * inv);
+        for (int i = i0; i <= i1; ++i) {
+            double hi = erf((i + 0.5 - y[p]) * inv);
+            ey[i - i0] = hi - lo;
+            lo = hi;
+        }
         /* amp * (pi/2) sigma^2 */
         double a = amp[p] * 1.5707963267948966 * s * s;
         for (int i = i0; i <= i1; ++i) {

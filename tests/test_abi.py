@@ -1,0 +1,120 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/ofv.h declares, and rejects bad arguments before
+touching the device.  Also checks that the oracle and the CUDA path share
+no code."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2509_25924_gb300 as ofv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(ofv_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_function():
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    out = subprocess.run(["nm", "-D", "--defined-only", ofv.lib_path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (ofv_[a-z0-9_]+)", out))
+    missing = declared - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    lib = ctypes.CDLL(ofv.lib_path)
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_binding_names_match_the_header():
+    declared = _declared_functions()
+    for name in declared:
+        assert hasattr(ofv, name), f"binding lacks {name}"
+
+
+def test_defaults_follow_the_documented_values():
+    p = ofv.ofv_default_params()
+    assert (p.levels_psl, p.kernel_radius, p.iterations, p.norm_radius) == (2, 4, 3, 0)
+    assert (p.input, p.bit_depth, p.storage, p.path, p.prefilter) == (ofv.OFV_IN_U16, 12, ofv.OFV_STORE_F32,
+                                                                      ofv.OFV_PATH_FUSED, 0)
+    assert abs(p.det_rel_eps - 1e-6) < 1e-12 and abs(p.norm_eps - 1e-2) < 1e-9
+
+
+@pytest.mark.parametrize("field,value", [
+    ("levels_psl", -1), ("levels_psl", 16), ("kernel_radius", 0), ("kernel_radius", 17),
+    ("iterations", 0), ("iterations", 65), ("norm_radius", -1), ("input", 7), ("storage", 3),
+    ("path", 2), ("prefilter", 2), ("bit_depth", 0), ("bit_depth", 17), ("det_rel_eps", float("nan")),
+    ("norm_eps", 0.0),
+])
+def test_invalid_parameters_are_rejected_on_the_host(field, value):
+    p = ofv.ofv_default_params(**{field: value})
+    with pytest.raises(ofv.OfvError) as ei:
+        ofv.ofv_create(1024, 1024, p)
+    assert ei.value.status == ofv.OFV_ERR_INVALID_ARG
+
+
+def test_u8_bit_depth_limit():
+    p = ofv.ofv_default_params(input=ofv.OFV_IN_U8, bit_depth=12)
+    with pytest.raises(ofv.OfvError) as ei:
+        ofv.ofv_create(256, 256, p)
+    assert ei.value.status == ofv.OFV_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("H,W,psl,kr", [(32, 32, 2, 4), (64, 17, 1, 5), (0, 64, 0, 1), (64, 64, 3, 4),
+                                        (100000, 100000, 0, 1)])
+def test_shape_limits(H, W, psl, kr):
+    p = ofv.ofv_default_params(levels_psl=psl, kernel_radius=kr)
+    with pytest.raises(ofv.OfvError) as ei:
+        ofv.ofv_create(H, W, p)
+    assert ei.value.status == ofv.OFV_ERR_SHAPE
+    assert "coarsest" in ofv.ofv_last_error() or "H" in ofv.ofv_last_error()
+
+
+def test_null_arguments_are_rejected():
+    lib = ctypes.CDLL(ofv.lib_path)
+    lib.ofv_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.ofv_create.restype = ctypes.c_int
+    assert lib.ofv_create(64, 64, None, None) == ofv.OFV_ERR_INVALID_ARG
+    out = ctypes.c_void_p()
+    assert lib.ofv_create(64, 64, None, ctypes.byref(out)) == ofv.OFV_ERR_INVALID_ARG
+    assert out.value is None
+    lib.ofv_compute.argtypes = [ctypes.c_void_p] * 6
+    lib.ofv_compute.restype = ctypes.c_int
+    assert lib.ofv_compute(None, None, None, None, None, None) == ofv.OFV_ERR_INVALID_ARG
+    lib.ofv_destroy.argtypes = [ctypes.c_void_p]
+    lib.ofv_destroy.restype = ctypes.c_int
+    assert lib.ofv_destroy(None) == ofv.OFV_OK
+
+
+def test_status_strings():
+    assert ofv.ofv_status_string(ofv.OFV_ERR_SHAPE) == "OFV_ERR_SHAPE"
+    assert ofv.ofv_status_string(99) == "OFV_ERR_UNKNOWN"
+
+
+def _py_and_c_sources(d):
+    for base, _, files in os.walk(os.path.join(ROOT, d)):
+        for f in files:
+            if f.endswith((".py", ".c", ".h", ".cu", ".cuh", ".cpp")):
+                yield os.path.join(base, f)
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    for f in _py_and_c_sources("oracle"):
+        text = open(f).read()
+        assert "paper_2509_25924_gb300" not in text and "ofv.h" not in text, f
+    for f in _py_and_c_sources("paper_2509_25924_gb300"):
+        text = open(f).read()
+        assert not re.search(r"\boracle\b", text.replace("oracle-free", "")), f
+        assert "ofv_oracle" not in text, f

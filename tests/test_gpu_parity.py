@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA estimator through the C ABI vs the FP64 oracle, on
+the same seeded synthetic inputs.
+
+Tolerances (written here, derived in the design notes):
+  * FP32 storage: max |dV| <= 1e-3 px over pixels whose final normalized
+    determinant det/(Sxx+Syy)^2 (from the oracle) is >= 1e-3; ill-conditioned
+    pixels amplify FP32 round-off by the condition number and are reported,
+    not compared;
+  * FP16 / BF16 storage: RMS |dV| <= 1e-2 px over the same pixels;
+  * stage outputs (level images): 2e-6 relative to the image range.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2509_25924_gb300 as ofv  # noqa: E402
+import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+FP32_TOL = 1e-3
+REDUCED_RMS_TOL = 1e-2
+NDET_MIN = 1e-3
+
+_IN = {np.dtype(np.float32): ofv.OFV_IN_F32, np.dtype(np.uint16): ofv.OFV_IN_U16,
+       np.dtype(np.uint8): ofv.OFV_IN_U8}
+
+
+def gpu_flow(I1, I2, bits=12, w25=None, **kw):
+    H, W = I1.shape
+    kw.setdefault("input", _IN[I1.dtype])
+    kw.setdefault("bit_depth", bits)
+    if w25 is not None:
+        kw["prefilter"] = 1
+    p = ofv.ofv_default_params(**kw)
+    h = ofv.ofv_create(H, W, p)
+    try:
+        t1 = torch.from_numpy(np.ascontiguousarray(I1)).to(DEV)
+        t2 = torch.from_numpy(np.ascontiguousarray(I2)).to(DEV)
+        if w25 is not None:
+            ofv.ofv_set_prefilter(h, torch.tensor(np.asarray(w25, np.float32).reshape(25), device=DEV))
+        u = torch.empty((H, W), dtype=torch.float32, device=DEV)
+        v = torch.empty_like(u)
+        ofv.ofv_compute(h, t1, t2, u, v)
+        torch.cuda.synchronize()
+        return u.cpu().numpy(), v.cpu().numpy()
+    finally:
+        ofv.ofv_destroy(h)
+
+
+def oracle_flow(I1, I2, bits=12, w25=None, psl=2, kr=4, it=3, nr=0):
+    b = bits if I1.dtype != np.float32 else 0
+    return oracle.flow(I1.astype(np.float64), I2.astype(np.float64),
+                       oracle.Params(psl=psl, kr=kr, it=it, nr=nr, bits=b, prefilter=w25), diagnostics=True)
+
+
+def compare(u, v, ou, ov, nd, tol=FP32_TOL, rms_tol=None, max_masked=0.01, label=""):
+    m = nd >= NDET_MIN
+    masked = 1.0 - m.mean()
+    d = np.hypot(u - ou, v - ov)
+    assert np.isfinite(u).all() and np.isfinite(v).all(), f"{label}: non-finite output"
+    assert masked <= max_masked, f"{label}: {masked:.3%} ill-conditioned pixels"
+    dmax = max(np.abs(u - ou)[m].max(), np.abs(v - ov)[m].max())
+    rms = float(np.sqrt(np.mean(d[m] ** 2)))
+    print(f"{label}: max|dV|={dmax:.3e} rms={rms:.3e} masked={masked:.4%}")
+    if rms_tol is None:
+        assert dmax <= tol, f"{label}: max |dV| {dmax:.3e} > {tol}"
+    else:
+        assert rms <= rms_tol, f"{label}: rms |dV| {rms:.3e} > {rms_tol}"
+    return dmax, rms
+
+
+PARAMS = dict(levels_psl=2, kernel_radius=4, iterations=3)
+
+
+# --------------------------------------------------------------------------
+# the 256x256 float32 Rankine pair (3 levels, KR 4, IT 3)
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def rankine():
+    I1, I2, tu, tv = synth.rankine_pair()
+    ou, ov, nd, _ = oracle_flow(I1, I2)
+    return I1, I2, ou, ov, nd, tu, tv
+
+
+@pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN])
+def test_rankine_fp32_matches_oracle(rankine, path):
+    I1, I2, ou, ov, nd, tu, tv = rankine
+    u, v = gpu_flow(I1, I2, path=path, **PARAMS)
+    compare(u, v, ou, ov, nd, label=f"rankine256 path={path}")
+    err = np.hypot(u - tu, v - tv).mean()
+    assert err < 0.27
+
+
+def test_fused_and_plain_agree(rankine):
+    I1, I2 = rankine[:2]
+    a = gpu_flow(I1, I2, path=ofv.OFV_PATH_FUSED, **PARAMS)
+    b = gpu_flow(I1, I2, path=ofv.OFV_PATH_PLAIN, **PARAMS)
+    nd = rankine[4]
+    m = nd >= NDET_MIN
+    assert max(np.abs(a[0] - b[0])[m].max(), np.abs(a[1] - b[1])[m].max()) < 2e-4
+
+
+def test_runs_are_bitwise_deterministic(rankine):
+    I1, I2 = rankine[:2]
+    a = gpu_flow(I1, I2, **PARAMS)
+    b = gpu_flow(I1, I2, **PARAMS)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("storage", [ofv.OFV_STORE_F32, ofv.OFV_STORE_F16, ofv.OFV_STORE_BF16])
+@pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN])
+def test_zero_motion_is_exactly_zero(storage, path):
+    I1, _, _, _ = synth.rankine_pair(128, 160, seed=3)
+    u, v = gpu_flow(I1, I1.copy(), storage=storage, path=path, **PARAMS)
+    assert np.all(u == 0.0) and np.all(v == 0.0)
+
+
+def test_frame_swap_negates_the_field(rankine):
+    I1, I2 = rankine[:2]
+    u, v = gpu_flow(I1, I2, **PARAMS)
+    us, vs = gpu_flow(I2, I1, **PARAMS)
+    assert np.abs(us + u).max() <= 1e-6 and np.abs(vs + v).max() <= 1e-6
+
+
+# --------------------------------------------------------------------------
+# stages
+# --------------------------------------------------------------------------
+def _levels(h, L):
+    out = []
+    for f in (0, 1):
+        lv = []
+        for l in range(L):
+            H, W = ofv.ofv_level_shape(h, l)
+            t = torch.empty((H, W), dtype=torch.float32, device=DEV)
+            ofv.ofv_read_level(h, f, l, t)
+            lv.append(t)
+        out.append(lv)
+    torch.cuda.synchronize()
+    return [[t.cpu().numpy() for t in lv] for lv in out]
+
+
+@pytest.mark.parametrize("nr,pre", [(0, False), (2, False), (1, True)])
+@pytest.mark.parametrize("shape", [(256, 256), (97, 131)])
+def test_ingest_and_pyramid_levels_match_oracle(nr, pre, shape):
+    H, W = shape
+    I1, I2 = synth.translation_pair(H, W, (0.7, -0.4), seed=12, kind=synth.OUT_U16, noise=0.01)
+    rng = np.random.default_rng(5)
+    w = None
+    if pre:
+        w = rng.standard_normal((5, 5)) * 0.05
+        w[2, 2] += 1.0
+        w = w.astype(np.float32).astype(np.float64)
+    psl = 2 if H >= 128 else 1
+    p = ofv.ofv_default_params(levels_psl=psl, kernel_radius=2, iterations=1, norm_radius=nr,
+                               prefilter=1 if pre else 0)
+    h = ofv.ofv_create(H, W, p)
+    try:
+        if pre:
+            ofv.ofv_set_prefilter(h, torch.tensor(w.astype(np.float32).reshape(25), device=DEV))
+        t1 = torch.from_numpy(I1).to(DEV); t2 = torch.from_numpy(I2).to(DEV)
+        u = torch.empty((H, W), device=DEV); v = torch.empty_like(u)
+        ofv.ofv_compute(h, t1, t2, u, v)
+        got = _levels(h, psl + 1)
+    finally:
+        ofv.ofv_destroy(h)
+    op = oracle.Params(psl=psl, kr=2, it=1, nr=nr, bits=12, prefilter=w)
+    for f, raw in enumerate((I1, I2)):
+        want = oracle.pyramid(raw.astype(np.float64), op)
+        for l in range(psl + 1):
+            rng_ = max(1.0, np.abs(want[l]).max())
+            err = np.abs(got[f][l] - want[l]).max() / rng_
+            assert err < 2e-6, f"frame {f} level {l}: rel err {err:.2e}"
+
+
+@pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN])
+@pytest.mark.parametrize("psl,it", [(0, 1), (1, 1), (0, 3)])
+def test_single_level_and_upsample_paths(path, psl, it):
+    """PSL 0 IT 1 is one iteration from V = 0 (textbook LK); PSL 1 IT 1 adds
+    the up-sampling of the coarse field into the first fine iteration."""
+    I1, I2 = synth.translation_pair(97, 131, (0.45, -0.3), seed=31, kind=synth.OUT_F32)
+    u, v = gpu_flow(I1, I2, path=path, levels_psl=psl, kernel_radius=3, iterations=it)
+    ou, ov, nd, _ = oracle_flow(I1, I2, psl=psl, kr=3, it=it)
+    compare(u, v, ou, ov, nd, tol=FP32_TOL, label=f"97x131 psl={psl} it={it} path={path}")
+
+
+@pytest.mark.parametrize("H,W,psl,kr,it", [(36, 36, 2, 4, 3), (300, 200, 2, 4, 3), (129, 257, 1, 7, 2),
+                                            (64, 1000, 1, 1, 4), (511, 33, 1, 5, 3)])
+def test_ragged_shapes_and_minimum_levels(H, W, psl, kr, it):
+    I1, I2 = synth.translation_pair(H, W, (1.1, 0.6), seed=H + W, kind=synth.OUT_F32)
+    u, v = gpu_flow(I1, I2, levels_psl=psl, kernel_radius=kr, iterations=it)
+    ou, ov, nd, _ = oracle_flow(I1, I2, psl=psl, kr=kr, it=it)
+    compare(u, v, ou, ov, nd, label=f"{H}x{W} psl={psl} kr={kr} it={it}", max_masked=0.05)
+
+
+def test_u8_input_with_paper_benchmark_parameters():
+    """NR 2, KR 10, IT 3 on 8-bit frames (the parameter set of the paper's
+    throughput benchmark, Sec. 6), PSL 1."""
+    I1, I2 = synth.translation_pair(256, 256, (1.6, -0.9), seed=41, kind=synth.OUT_U8, bits=8, noise=0.01)
+    u, v = gpu_flow(I1, I2, bits=8, levels_psl=1, kernel_radius=10, iterations=3, norm_radius=2)
+    ou, ov, nd, _ = oracle_flow(I1, I2, bits=8, psl=1, kr=10, it=3, nr=2)
+    compare(u, v, ou, ov, nd, label="u8 NR2 KR10")
+
+
+def test_prefilter_path():
+    I1, I2 = synth.translation_pair(160, 192, (0.8, 1.2), seed=51, kind=synth.OUT_U16, noise=0.01)
+    rng = np.random.default_rng(9)
+    w = rng.standard_normal((5, 5)) * 0.05
+    w[2, 2] += 1.0
+    w = w.astype(np.float32).astype(np.float64)
+    u, v = gpu_flow(I1, I2, w25=w, norm_radius=1, **PARAMS)
+    ou, ov, nd, _ = oracle_flow(I1, I2, w25=w, nr=1)
+    compare(u, v, ou, ov, nd, label="prefilter")
+
+
+@pytest.mark.parametrize("storage", [ofv.OFV_STORE_F16, ofv.OFV_STORE_BF16])
+def test_reduced_storage_rms(storage):
+    I1, I2, _, _ = synth.turbulence_pair(512, 512, seed=3)
+    u, v = gpu_flow(I1, I2, storage=storage, **PARAMS)
+    ou, ov, nd, _ = oracle_flow(I1, I2)
+    compare(u, v, ou, ov, nd, rms_tol=REDUCED_RMS_TOL, label=f"turb512 storage={storage}")
+
+
+# --------------------------------------------------------------------------
+# entry points
+# --------------------------------------------------------------------------
+def test_sequence_equals_pairwise_and_host_entry_point():
+    F = synth.stream_frames(192, 256, 5, seed=2)
+    p = ofv.ofv_default_params(**PARAMS)
+    H, W = 192, 256
+    h = ofv.ofv_create(H, W, p)
+    try:
+        fr = torch.from_numpy(F).to(DEV)
+        us = torch.empty((4, H, W), device=DEV); vs = torch.empty_like(us)
+        ofv.ofv_compute_sequence(h, 5, fr, H * W * 2, us, vs, H * W)
+        for k in range(4):
+            u = torch.empty((H, W), device=DEV); v = torch.empty_like(u)
+            ofv.ofv_compute(h, fr[k], fr[k + 1], u, v)
+            torch.cuda.synchronize()
+            assert torch.equal(u, us[k]) and torch.equal(v, vs[k])
+        hu = torch.empty((H, W)).pin_memory(); hv = torch.empty((H, W)).pin_memory()
+        h1 = torch.from_numpy(F[1]).pin_memory(); h2 = torch.from_numpy(F[2]).pin_memory()
+        ofv.ofv_compute_host(h, h1, h2, hu, hv)
+        torch.cuda.synchronize()
+        assert torch.equal(hu, us[1].cpu()) and torch.equal(hv, vs[1].cpu())
+    finally:
+        ofv.ofv_destroy(h)
+
+
+def test_profile_counts_launches_and_bytes():
+    I1, I2, _, _ = synth.rankine_pair()
+    p = ofv.ofv_default_params(input=ofv.OFV_IN_F32, **PARAMS)
+    h = ofv.ofv_create(256, 256, p)
+    try:
+        t1 = torch.from_numpy(I1).to(DEV); t2 = torch.from_numpy(I2).to(DEV)
+        u = torch.empty((256, 256), device=DEV); v = torch.empty_like(u)
+        ofv.ofv_profile_enable(h, True)
+        ofv.ofv_compute(h, t1, t2, u, v)
+        ms, n, b = ofv.ofv_profile_read(h, ofv.OFV_K_ITERATE)
+        assert n == 9 and ms > 0
+        N = [256 * 256, 128 * 128, 64 * 64]
+        want = sum(3 * (2 * 4 + 8) * n_ for n_ in N) + 8 * (N[2] * 2 + N[1] * 2 + N[0] * 2) + 8 * (N[2] + N[1])
+        assert abs(b - want) < 1e-6 * want
+        _, nr, _ = ofv.ofv_profile_read(h, ofv.OFV_K_REDUCE)
+        assert nr == 2
+        ofv.ofv_profile_enable(h, False)
+    finally:
+        ofv.ofv_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# full-size workloads (the configurations the benchmark times)
+# --------------------------------------------------------------------------
+def test_full_1mp_stream_pair_fp32():
+    F = synth.stream_frames(1024, 1024, 2, seed=2)
+    u, v = gpu_flow(F[0], F[1], **PARAMS)
+    ou, ov, nd, _ = oracle_flow(F[0], F[1])
+    compare(u, v, ou, ov, nd, label="1Mp stream pair fp32")
+
+
+def test_full_4mp_turbulence_fp16_and_fp32():
+    I1, I2, _, _ = synth.turbulence_pair(2048, 2048, seed=3)
+    ou, ov, nd, _ = oracle_flow(I1, I2)
+    u, v = gpu_flow(I1, I2, storage=ofv.OFV_STORE_F16, **PARAMS)
+    compare(u, v, ou, ov, nd, rms_tol=REDUCED_RMS_TOL, label="4Mp turb fp16")
+    u, v = gpu_flow(I1, I2, **PARAMS)
+    compare(u, v, ou, ov, nd, label="4Mp turb fp32")
+
+
+def test_full_21mp_wake_fp32():
+    I1, I2, _, inside = synth.wake_pair(seed=4)
+    u, v = gpu_flow(I1, I2, **PARAMS)
+    ou, ov, nd, _ = oracle_flow(I1, I2)
+    compare(u, v, ou, ov, nd, label="21Mp wake fp32", max_masked=0.05)
