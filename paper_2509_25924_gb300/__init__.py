@@ -53,9 +53,7 @@ class Params(ctypes.Structure):
 
 
 def _load_library():
-    path = _build.LIB
-    if not os.path.exists(path):
-        path = _build.build_library()
+    path = _build.build_library()  # no-op when the library is up to date
     lib = ctypes.CDLL(path)
     P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
     sig = {
