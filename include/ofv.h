@@ -127,6 +127,37 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
                                 size_t frame_stride_bytes, float *u, float *v, size_t field_stride,
                                 ofv_stream_t s);
 
+/* ---- allocation-free variant -------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc: code that records work into a CUDA graph by stream
+ * capture and must not add allocation nodes, host applications whose device
+ * memory is owned by another allocator, and real-time loops that forbid any
+ * allocation once running.
+ *
+ * ofv_compute_noalloc computes the same field as ofv_create + ofv_compute
+ * with the same kernels (fused path only; params->path must be
+ * OFV_PATH_FUSED, else OFV_ERR_UNSUPPORTED) but allocates nothing: its
+ * workspace is a fixed device array of OFV_NOALLOC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The caller passes the frames I1, I2 (H x W, params->input type),
+ * the outputs u, v (H x W float) and, when params->prefilter = 1, the 25
+ * pre-filter weights w25 (device, row-major 5x5; may be NULL otherwise).
+ * A request whose workspace would exceed the array (about 27 bytes per pixel
+ * at FP32 storage: 1024 x 1024 fits, 2048 x 2048 does not) is rejected with
+ * OFV_ERR_SHAPE and a message giving the bytes needed.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  All calls share the one array and
+ * leave their intermediates in it; every intermediate is written before it
+ * is read, so no call depends on what an earlier one left.  Calls whose GPU
+ * work overlaps (different streams, or different host threads, without
+ * ordering between them) race on the array and corrupt each other's
+ * results: order them on one stream. */
+#define OFV_NOALLOC_SCRATCH_BYTES (64u << 20)
+ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *params, const float *w25, const void *I1,
+                               const void *I2, float *u, float *v, ofv_stream_t s);
+
 /* Dimensions of pyramid level l (0 = full resolution). */
 ofv_status ofv_level_shape(const ofv_handle *h, int level, int *H, int *W);
 

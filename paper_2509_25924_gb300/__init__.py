@@ -18,7 +18,8 @@ from . import build as _build
 
 __all__ = [
     "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter",
-    "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_level_shape", "ofv_read_level",
+    "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_level_shape",
+    "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
     "Flow", "lib_path", "EXPORTED_SYMBOLS",
 ]
@@ -28,10 +29,11 @@ OFV_IN_U8, OFV_IN_U16, OFV_IN_F32 = range(3)
 OFV_STORE_F32, OFV_STORE_F16, OFV_STORE_BF16 = range(3)
 OFV_PATH_FUSED, OFV_PATH_PLAIN = range(2)
 OFV_K_INGEST, OFV_K_REDUCE, OFV_K_ITERATE, OFV_K_COUNT = range(4)
+OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED_SYMBOLS = [
     "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_compute",
-    "ofv_compute_host", "ofv_compute_sequence", "ofv_level_shape", "ofv_read_level",
+    "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_level_shape", "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
 ]
 
@@ -64,6 +66,7 @@ def _load_library():
         "ofv_compute": ([P, P, P, P, P, P], I),
         "ofv_compute_host": ([P, P, P, P, P, P], I),
         "ofv_compute_sequence": ([P, I, P, Z, P, P, Z, P], I),
+        "ofv_compute_noalloc": ([I, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
         "ofv_level_shape": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "ofv_read_level": ([P, I, I, P, P], I),
         "ofv_profile_enable": ([P, I], I),
@@ -152,6 +155,14 @@ def ofv_compute_sequence(h: int, n_frames: int, frames, frame_stride_bytes: int,
                          stream=None):
     _check(_lib.ofv_compute_sequence(h, n_frames, _addr(frames), frame_stride_bytes, _addr(u), _addr(v),
                                      field_stride, _stream(stream)), "ofv_compute_sequence")
+
+
+def ofv_compute_noalloc(H: int, W: int, params: Params, w25, I1, I2, u, v, stream=None):
+    """Same field as ofv_create + ofv_compute, for callers that must not
+    allocate device memory: the workspace is the library's fixed scratch
+    array (OFV_NOALLOC_SCRATCH_BYTES).  See include/ofv.h for its limits."""
+    _check(_lib.ofv_compute_noalloc(H, W, ctypes.byref(params), _addr(w25), _addr(I1), _addr(I2), _addr(u),
+                                    _addr(v), _stream(stream)), "ofv_compute_noalloc")
 
 
 def ofv_level_shape(h: int, level: int):

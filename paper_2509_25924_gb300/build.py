@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libofv.so")
 
-SOURCES = ["ofv_capi.cu", "k_pyramid.cu", "k_fused.cu", "k_plain.cu"]
+SOURCES = ["ofv_capi.cu", "k_pyramid.cu", "k_fused.cu", "k_plain.cu", "ofv_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
               "--expt-relaxed-constexpr"]

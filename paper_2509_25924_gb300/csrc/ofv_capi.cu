@@ -283,6 +283,11 @@ ofv_status pending_error(const char *where)
 
 }  // namespace
 
+namespace ofv {
+// Record a failure message for ofv_last_error() from another translation unit.
+void set_error_message(const char *msg) { fail(OFV_OK, "%s", msg); }
+}  // namespace ofv
+
 extern "C" {
 
 void ofv_default_params(ofv_params *p)
