@@ -62,10 +62,14 @@ typedef enum { OFV_IN_U8 = 0, OFV_IN_U16 = 1, OFV_IN_F32 = 2 } ofv_input_t;
 typedef enum { OFV_STORE_F32 = 0, OFV_STORE_F16 = 1, OFV_STORE_BF16 = 2 } ofv_storage_t;
 
 /* OFV_PATH_FUSED: one kernel per (level, iteration) doing warp, gradients,
-   products, separable window sums and the solve in shared memory.
+   products, window sums and the solve on chip: for KR <= 10 the block kernel
+   (both images staged in shared memory over a 48x48 or 32x32 output tile,
+   window sums by additions only), for larger KR the tile kernel.
+   OFV_PATH_TILE: always the tile kernel (one CTA per 32x32 output tile with
+   the products of tile and halo in shared memory); kept for comparison.
    OFV_PATH_PLAIN: the same arithmetic split into separate kernels that pass
    five product planes through device memory (kept for comparison). */
-typedef enum { OFV_PATH_FUSED = 0, OFV_PATH_PLAIN = 1 } ofv_path_t;
+typedef enum { OFV_PATH_FUSED = 0, OFV_PATH_PLAIN = 1, OFV_PATH_TILE = 2 } ofv_path_t;
 
 typedef struct {
     int levels_psl;     /* PSL >= 0 pyramid sub-levels; levels = PSL + 1 (Sec. 2; Table 2 uses 2..4) */
@@ -80,6 +84,9 @@ typedef struct {
     float det_rel_eps;  /* guard: keep V0 where det <= eps * (Sxx + Syy)^2 (default 1e-6) */
     float det_abs_eps;  /* guard: keep V0 where Sxx + Syy <= eps (default 1e-20) */
     float norm_eps;     /* normalization floor: (I - mu) / sqrt(var + eps^2) (default 1e-2) */
+    int max_batch;      /* pairs of a sequence per iteration launch, 0..8; 0 = auto (as many as keep
+                           about 16 Mp per launch).  Each costs one more pyramid and two fields of
+                           workspace. */
 } ofv_params;
 
 typedef struct ofv_handle ofv_handle;

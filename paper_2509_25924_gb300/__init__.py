@@ -27,7 +27,7 @@ __all__ = [
 OFV_OK, OFV_ERR_INVALID_ARG, OFV_ERR_SHAPE, OFV_ERR_ALLOC, OFV_ERR_CUDA, OFV_ERR_TIMEOUT, OFV_ERR_UNSUPPORTED = range(7)
 OFV_IN_U8, OFV_IN_U16, OFV_IN_F32 = range(3)
 OFV_STORE_F32, OFV_STORE_F16, OFV_STORE_BF16 = range(3)
-OFV_PATH_FUSED, OFV_PATH_PLAIN = range(2)
+OFV_PATH_FUSED, OFV_PATH_PLAIN, OFV_PATH_TILE = range(3)
 OFV_K_INGEST, OFV_K_REDUCE, OFV_K_ITERATE, OFV_K_COUNT = range(4)
 OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
         ("norm_radius", ctypes.c_int), ("input", ctypes.c_int), ("bit_depth", ctypes.c_int),
         ("storage", ctypes.c_int), ("path", ctypes.c_int), ("prefilter", ctypes.c_int),
         ("det_rel_eps", ctypes.c_float), ("det_abs_eps", ctypes.c_float), ("norm_eps", ctypes.c_float),
+        ("max_batch", ctypes.c_int),
     ]
 
 

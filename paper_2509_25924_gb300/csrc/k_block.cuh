@@ -1,0 +1,345 @@
+// Block-tiled fused Gauss-Newton iteration (Sec. 2 step 3, Eq. 2), the
+// kernel behind OFV_PATH_FUSED for window radii 1..10.
+//
+// One CTA owns a TS x TS tile of output pixels (TS = 48 for KR <= 5, else
+// 32) and works entirely on chip in five phases:
+//   0. stage the two level images over the tile, its KR window halo, a
+//      REACH px warp margin and the gradient stencil into shared memory
+//      (clamp-to-edge applied while staging, 16-byte cp.async rows away from
+//      the image border);
+//   1. the five products of every pixel of tile + halo (bilinear value and
+//      central-difference gradient of both frames at k -/+ V0/2) into
+//      shared memory; taps farther than REACH px come from global memory;
+//   2. horizontal window sums, in place, one (row, channel) per thread;
+//   3. vertical window sums, in place, one (column, channel) per thread;
+//   4. the guarded 2x2 solve per output pixel and the store of V.
+// Window sums use the van Herk / Gil-Werman block decomposition (suffix sums
+// of one block of 2KR+1 values plus prefix sums of the next), so every sum
+// is formed by additions only -- no running subtraction that would cancel
+// digits the ill-conditioned solves need -- at three additions per output.
+// Products of pixels outside the image are zero, which truncates the
+// windows at the border.
+#pragma once
+#include "iter_math.cuh"
+
+namespace ofv {
+
+constexpr int kBlockReach = 4;  // |warp offset| served from the staged tile (px)
+constexpr int kBlockMaxKR = 10;
+constexpr int kBlockMaxBatch = kMaxPairsPerLaunch;
+
+struct BlockParams {
+    IterArgs a[kBlockMaxBatch];  // one per pair (blockIdx.z)
+    int mode;                    // V0Mode, uniform per launch
+};
+
+template <int KR> struct BlockShape {
+    static constexpr int TS = KR <= 5 ? 48 : 32;          // output tile edge
+    static constexpr int NT = KR <= 5 ? 512 : 256;        // threads
+    static constexpr int RW = TS + 2 * KR;                // product region edge
+    static constexpr int RWP = RW | 1;                    // odd row pitch of the product planes
+    static constexpr int SH = RW + 2 * kBlockReach + 3;   // staged rows
+};
+
+template <typename T, int KR> struct StageShape {
+    static constexpr int VEC = 16 / (int)sizeof(T);
+    static constexpr int SW = BlockShape<KR>::RW + 2 * kBlockReach + 3 + VEC - 1;  // incl. alignment slack
+    static constexpr int NV = (SW + VEC - 1) / VEC;                               // 16-byte vectors per row
+    static constexpr int SP = NV * VEC;                                           // staged row pitch
+};
+
+// floats of the five product planes, rounded up so the staged images that
+// follow start 16-byte aligned
+template <int KR> struct ProdFloats {
+    static constexpr int v = (5 * BlockShape<KR>::RW * BlockShape<KR>::RWP + 3) / 4 * 4;
+};
+
+template <typename T, int KR>
+constexpr size_t block_smem_bytes()
+{
+    return sizeof(float) * ProdFloats<KR>::v + sizeof(T) * 2 * BlockShape<KR>::SH * StageShape<T, KR>::SP;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// V0 at (x, y) with the mode chosen at run time (uniform per launch).
+__device__ __forceinline__ float2 fetch_v0_rt(const IterArgs &a, int mode, int x, int y)
+{
+    if (mode == V0_SAME) return fetch_v0<V0_SAME>(a, x, y);
+    if (mode == V0_UP) return fetch_v0<V0_UP>(a, x, y);
+    return make_float2(0.f, 0.f);
+}
+
+// Global-memory sampler for warps beyond the staged margin (rare).
+template <typename T>
+__device__ __noinline__ Sample sample_global(const T *__restrict__ P, int H, int W, int pitch, int x, int y, float dx,
+                                             float dy)
+{
+    return sample_level(P, H, W, pitch, x, y, dx, dy);
+}
+
+// Bilinear value and gradient of a level image at (x + dx, y + dy), from the
+// staged tile when the border-remapped taps lie within REACH px of (x, y).
+// st points at staged element (row sy0, column sx0).  Same arithmetic as
+// sample_level.
+template <typename T, int SP>
+__device__ __forceinline__ Sample sample_staged(const T *__restrict__ st, int sx0, int sy0, const T *__restrict__ Pg,
+                                                int H, int W, int pitch, int x, int y, float dx, float dy)
+{
+    const float lim_x = (float)(W + 4), lim_y = (float)(H + 4);
+    const float cdx = fminf(fmaxf(dx, -lim_x), lim_x);
+    const float cdy = fminf(fmaxf(dy, -lim_y), lim_y);
+    const float flx = floorf(cdx), fly = floorf(cdy);
+    float fx = cdx - flx, fy = cdy - fly;
+    int x0 = x + (int)flx, y0 = y + (int)fly;
+    if (x0 < 0) { x0 = 0; fx = 0.f; }
+    if (x0 > W - 2) { x0 = W - 2; fx = 1.f; }
+    if (y0 < 0) { y0 = 0; fy = 0.f; }
+    if (y0 > H - 2) { y0 = H - 2; fy = 1.f; }
+    if (abs(x0 - x) > kBlockReach || abs(y0 - y) > kBlockReach) return sample_global(Pg, H, W, pitch, x, y, dx, dy);
+    const T *rm = st + (y0 - 1 - sy0) * SP + (x0 - 1 - sx0);
+    const T *r0 = rm + SP, *r1 = rm + 2 * SP, *rp = rm + 3 * SP;
+    const float e0 = to_f(rm[1]), e1 = to_f(rm[2]);
+    const float q00 = to_f(r0[0]), q01 = to_f(r0[1]), q02 = to_f(r0[2]), q03 = to_f(r0[3]);
+    const float q10 = to_f(r1[0]), q11 = to_f(r1[1]), q12 = to_f(r1[2]), q13 = to_f(r1[3]);
+    const float e2 = to_f(rp[1]), e3 = to_f(rp[2]);
+    const float wx0 = 1.f - fx, wy0 = 1.f - fy;
+    Sample s;
+    s.val = wy0 * (wx0 * q01 + fx * q02) + fy * (wx0 * q11 + fx * q12);
+    const float dxa0 = 0.5f * (q02 - q00), dxb0 = 0.5f * (q03 - q01);
+    const float dxa1 = 0.5f * (q12 - q10), dxb1 = 0.5f * (q13 - q11);
+    s.gx = wy0 * (wx0 * dxa0 + fx * dxb0) + fy * (wx0 * dxa1 + fx * dxb1);
+    const float dya0 = 0.5f * (q11 - e0), dyb0 = 0.5f * (q12 - e1);
+    const float dya1 = 0.5f * (e2 - q01), dyb1 = 0.5f * (e3 - q02);
+    s.gy = wy0 * (wx0 * dya0 + fx * dyb0) + fy * (wx0 * dya1 + fx * dyb1);
+    return s;
+}
+
+// Bilinear value and doubled gradient (undivided central differences) of a
+// staged 4x4 neighbourhood: rm points at the tap left of column x0 in row
+// y0-1.  Interpolation as a + f (b - a).
+template <typename T, int SP>
+__device__ __forceinline__ Sample bilin_staged(const T *__restrict__ rm, float fx, float fy)
+{
+    const T *r0 = rm + SP, *r1 = rm + 2 * SP, *rp = rm + 3 * SP;
+    const float e0 = to_f(rm[1]), e1 = to_f(rm[2]);
+    const float q00 = to_f(r0[0]), q01 = to_f(r0[1]), q02 = to_f(r0[2]), q03 = to_f(r0[3]);
+    const float q10 = to_f(r1[0]), q11 = to_f(r1[1]), q12 = to_f(r1[2]), q13 = to_f(r1[3]);
+    const float e2 = to_f(rp[1]), e3 = to_f(rp[2]);
+    Sample s;
+    const float v0 = fmaf(fx, q02 - q01, q01), v1 = fmaf(fx, q12 - q11, q11);
+    s.val = fmaf(fy, v1 - v0, v0);
+    const float da0 = q02 - q00, db0 = q03 - q01, da1 = q12 - q10, db1 = q13 - q11;
+    const float gx0 = fmaf(fx, db0 - da0, da0), gx1 = fmaf(fx, db1 - da1, da1);
+    s.gx = fmaf(fy, gx1 - gx0, gx0);
+    const float ea0 = q11 - e0, eb0 = q12 - e1, ea1 = e2 - q01, eb1 = e3 - q02;
+    const float gy0 = fmaf(fx, eb0 - ea0, ea0), gy1 = fmaf(fx, eb1 - ea1, ea1);
+    s.gy = fmaf(fy, gy1 - gy0, gy0);
+    return s;
+}
+
+// Products of one pixel (x, y) of a tile whose staged region lies inside
+// the image: no clamping or border remap is needed while the warp stays
+// within REACH px.  The frame-1 offset -h and frame-2 offset +h share their
+// fractional part: floor(-h) = -floor(h) - 1 and frac(-h) = 1 - frac(h)
+// unless h is an integer.  Farther warps take the general sampler.
+template <typename T, int SP>
+__device__ __forceinline__ void products_interior(const T *__restrict__ st1, const T *__restrict__ st2, int sx0,
+                                                  int sy0, const IterArgs &a, int x, int y, float2 V0, float p[5])
+{
+    const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
+    const float flx = floorf(hx), fly = floorf(hy);
+    Sample s1, s2;
+    float Gx, Gy;
+    if (flx >= -kBlockReach && flx <= kBlockReach - 1 && fly >= -kBlockReach && fly <= kBlockReach - 1) {
+        const int ix = (int)flx, iy = (int)fly;
+        const float fx2 = hx - flx, fy2 = hy - fly;
+        const bool zx = fx2 == 0.f, zy = fy2 == 0.f;
+        const int ix1 = zx ? -ix : -ix - 1, iy1 = zy ? -iy : -iy - 1;
+        const float fx1 = zx ? 0.f : 1.f - fx2, fy1 = zy ? 0.f : 1.f - fy2;
+        const int base = (y - 1 - sy0) * SP + (x - 1 - sx0);
+        s2 = bilin_staged<T, SP>(st2 + base + iy * SP + ix, fx2, fy2);
+        s1 = bilin_staged<T, SP>(st1 + base + iy1 * SP + ix1, fx1, fy1);
+        // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4
+        Gx = 0.25f * (s1.gx + s2.gx);
+        Gy = 0.25f * (s1.gy + s2.gy);
+    } else {
+        const T *P1 = static_cast<const T *>(a.P1), *P2 = static_cast<const T *>(a.P2);
+        s1 = sample_global(P1, a.H, a.W, a.pitch, x, y, -hx, -hy);
+        s2 = sample_global(P2, a.H, a.W, a.pitch, x, y, hx, hy);
+        Gx = 0.5f * (s1.gx + s2.gx);
+        Gy = 0.5f * (s1.gy + s2.gy);
+    }
+    const float It = s2.val - s1.val;
+    const float r = Gx * V0.x + Gy * V0.y - It;
+    p[0] = Gx * Gx;
+    p[1] = Gx * Gy;
+    p[2] = Gy * Gy;
+    p[3] = Gx * r;
+    p[4] = Gy * r;
+}
+
+// Window sums of one line of the product planes, in place: for outputs
+// o = 0 .. TS-1, line[o*stride] <- sum_{j=0}^{2KR} line[(o+j)*stride].
+// Outputs are formed block by block (blocks of WIN = 2KR+1): the sums of a
+// block are suffix sums of its own values plus prefix sums of the next 2KR
+// values.  A block's writes land on its own outputs only, which later
+// blocks no longer read.
+template <int KR, int TS, bool TAIL>
+__device__ __forceinline__ void window_block(float *line, int stride, int b)
+{
+    constexpr int WIN = 2 * KR + 1;
+    float v[2 * WIN - 1];
+#pragma unroll
+    for (int j = 0; j < 2 * WIN - 1; ++j) v[j] = (!TAIL || b + j < TS + 2 * KR) ? line[(b + j) * stride] : 0.f;
+    float s[WIN];
+    s[WIN - 1] = v[WIN - 1];
+#pragma unroll
+    for (int i = WIN - 2; i >= 0; --i) s[i] = v[i] + s[i + 1];
+    line[b * stride] = s[0];
+    float pre = 0.f;
+#pragma unroll
+    for (int i = 1; i < WIN; ++i) {
+        pre += v[WIN + i - 1];
+        if (!TAIL || b + i < TS) line[(b + i) * stride] = s[i] + pre;
+    }
+}
+
+template <int KR, int TS>
+__device__ __forceinline__ void window_sums_inplace(float *line, int stride)
+{
+    constexpr int WIN = 2 * KR + 1;
+    constexpr int NFULL = TS / WIN;  // blocks whose outputs and inputs are all in range
+    int b = 0;
+#pragma unroll 1
+    for (int k = 0; k < NFULL; ++k, b += WIN) window_block<KR, TS, false>(line, stride, b);
+    if (b < TS) window_block<KR, TS, true>(line, stride, b);
+}
+
+template <typename T, int KR>
+__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __grid_constant__ BlockParams prm)
+{
+    using BS = BlockShape<KR>;
+    using SS = StageShape<T, KR>;
+    constexpr int TS = BS::TS, NT = BS::NT, RW = BS::RW, RWP = BS::RWP, SH = BS::SH;
+    constexpr int SP = SS::SP, NV = SS::NV, VEC = SS::VEC;
+    constexpr int PLANE = RW * RWP;
+
+    extern __shared__ float4 smem_f4[];
+    float *prod = reinterpret_cast<float *>(smem_f4);                // [5][RW][RWP]
+    T *stage = reinterpret_cast<T *>(prod + ProdFloats<KR>::v);     // [2][SH][SP]
+
+    const IterArgs &a = prm.a[blockIdx.z];
+    const int mode = prm.mode;
+    const int tid = threadIdx.x;
+    const int H = a.H, W = a.W, pitch = a.pitch;
+    const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int px0 = tx0 - KR, py0 = ty0 - KR;                      // product region origin
+    const int sy0 = py0 - kBlockReach - 1;                         // staged row origin
+    const int sxn = px0 - kBlockReach - 1;
+    const int sx0 = (sxn >= 0 ? sxn / VEC : -((-sxn + VEC - 1) / VEC)) * VEC;  // floor to a VEC multiple
+    const T *P1 = static_cast<const T *>(a.P1);
+    const T *P2 = static_cast<const T *>(a.P2);
+
+    // phase 0: stage both frames (rows sy0 .. sy0+SH-1, columns sx0 .. sx0+SP-1)
+    const bool vec_ok = sx0 >= 0 && sx0 + SP <= W;
+    if (vec_ok) {
+        for (int t = tid; t < 2 * SH * NV; t += NT) {
+            const int f = t >= SH * NV ? 1 : 0;
+            const int r = t - f * SH * NV;
+            const int row = r / NV, v = r - row * NV;
+            const int gy = min(max(sy0 + row, 0), H - 1);
+            cp_async16(stage + (f * SH + row) * SP + v * VEC, (f ? P2 : P1) + (int64_t)gy * pitch + sx0 + v * VEC);
+        }
+        cp_async_wait_all();
+    } else {
+        for (int t = tid; t < 2 * SH * SP; t += NT) {
+            const int f = t >= SH * SP ? 1 : 0;
+            const int r = t - f * SH * SP;
+            const int row = r / SP, c = r - row * SP;
+            const int gy = min(max(sy0 + row, 0), H - 1);
+            const int gx = min(max(sx0 + c, 0), W - 1);
+            stage[(f * SH + row) * SP + c] = (f ? P2 : P1)[(int64_t)gy * pitch + gx];
+        }
+    }
+    __syncthreads();
+
+    // phase 1: products on tile + halo.  A tile whose staged rows and columns
+    // all lie inside the image needs no clamping or border remap.
+    const bool interior = vec_ok && sy0 >= 0 && sy0 + SH <= H;
+    for (int idx = tid; idx < RW * RW; idx += NT) {
+        const int ry = idx / RW, rx = idx - ry * RW;
+        const int gy = py0 + ry, gx = px0 + rx;
+        float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (interior) {
+            const float2 V0 = fetch_v0_rt(a, mode, gx, gy);
+            products_interior<T, SP>(stage, stage + SH * SP, sx0, sy0, a, gx, gy, V0, p);
+        } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            const float2 V0 = fetch_v0_rt(a, mode, gx, gy);
+            const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
+            const Sample s1 = sample_staged<T, SP>(stage, sx0, sy0, P1, H, W, pitch, gx, gy, -hx, -hy);
+            const Sample s2 = sample_staged<T, SP>(stage + SH * SP, sx0, sy0, P2, H, W, pitch, gx, gy, hx, hy);
+            const float Gx = 0.5f * (s1.gx + s2.gx), Gy = 0.5f * (s1.gy + s2.gy);
+            const float It = s2.val - s1.val;
+            const float r = Gx * V0.x + Gy * V0.y - It;
+            p[0] = Gx * Gx;
+            p[1] = Gx * Gy;
+            p[2] = Gy * Gy;
+            p[3] = Gx * r;
+            p[4] = Gy * r;
+        }
+        float *q = prod + ry * RWP + rx;
+        q[0] = p[0];
+        q[PLANE] = p[1];
+        q[2 * PLANE] = p[2];
+        q[3 * PLANE] = p[3];
+        q[4 * PLANE] = p[4];
+    }
+    __syncthreads();
+
+    // phase 2: horizontal window sums, one (row, channel) per thread
+    for (int t = tid; t < 5 * RW; t += NT) {
+        const int c = t / RW, row = t - c * RW;
+        window_sums_inplace<KR, TS>(prod + c * PLANE + row * RWP, 1);
+    }
+    __syncthreads();
+
+    // phase 3: vertical window sums, one (column, channel) per thread
+    for (int t = tid; t < 5 * TS; t += NT) {
+        const int c = t / TS, col = t - c * TS;
+        window_sums_inplace<KR, TS>(prod + c * PLANE + col, RWP);
+    }
+    __syncthreads();
+
+    // phase 4: guarded solve and store
+    for (int idx = tid; idx < TS * TS; idx += NT) {
+        const int oy = idx / TS, ox = idx - oy * TS;
+        const int gy = ty0 + oy, gx = tx0 + ox;
+        if (gy >= H || gx >= W) continue;
+        const float *q = prod + oy * RWP + ox;
+        const float sxx = q[0], sxy = q[PLANE], syy = q[2 * PLANE], sxr = q[3 * PLANE], syr = q[4 * PLANE];
+        const float tr = sxx + syy;
+        const float det = sxx * syy - sxy * sxy;
+        float2 V;
+        if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr)
+            V = fetch_v0_rt(a, mode, gx, gy);
+        else
+            V = make_float2((syy * sxr - sxy * syr) / det, (sxx * syr - sxy * sxr) / det);
+        if (a.u_out) {
+            a.u_out[(int64_t)gy * W + gx] = V.x;
+            a.v_out[(int64_t)gy * W + gx] = V.y;
+        } else {
+            a.Vout[(int64_t)gy * a.vpitch + gx] = V;
+        }
+    }
+}
+
+}  // namespace ofv

@@ -1,0 +1,44 @@
+// Block-tiled iteration kernel instantiated for __nv_bfloat16 level storage, window
+// radii 1..10.
+#include "k_block.cuh"
+
+namespace ofv {
+
+namespace {
+size_t g_granted_bf16[64][kBlockMaxKR + 1];
+
+template <int KR>
+cudaError_t run_bf16(const BlockParams &p, dim3 grid, int dev, cudaStream_t s)
+{
+    constexpr size_t smem = block_smem_bytes<__nv_bfloat16, KR>();
+    auto kern = k_iter_block<__nv_bfloat16, KR>;
+    if (dev < 0 || dev >= 64 || g_granted_bf16[dev][KR] < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) g_granted_bf16[dev][KR] = smem;
+    }
+    kern<<<grid, BlockShape<KR>::NT, smem, s>>>(p);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_block_bf16(const BlockParams &p, int kr, int npairs, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const IterArgs &a = p.a[0];
+    switch (kr) {
+#define OFV_BLOCK_CASE(K)                                                                          \
+    case K: {                                                                                      \
+        constexpr int TS = BlockShape<K>::TS;                                                      \
+        return run_bf16<K>(p, dim3((a.W + TS - 1) / TS, (a.H + TS - 1) / TS, npairs), dev, s);     \
+    }
+    OFV_BLOCK_CASE(1) OFV_BLOCK_CASE(2) OFV_BLOCK_CASE(3) OFV_BLOCK_CASE(4) OFV_BLOCK_CASE(5)
+    OFV_BLOCK_CASE(6) OFV_BLOCK_CASE(7) OFV_BLOCK_CASE(8) OFV_BLOCK_CASE(9) OFV_BLOCK_CASE(10)
+#undef OFV_BLOCK_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ofv

@@ -14,7 +14,7 @@ template <> __device__ __forceinline__ float ld_in<uint8_t>(const uint8_t *p) { 
 template <> __device__ __forceinline__ float ld_in<uint16_t>(const uint16_t *p) { return (float)__ldg(p); }
 template <> __device__ __forceinline__ float ld_in<float>(const float *p) { return __ldg(p); }
 
-struct IngestPair { IngestArgs f[2]; float scale; };
+struct IngestPair { IngestArgs f[kMaxFramesPerLaunch]; float scale; };
 
 // Scaled intensity I = raw * scale (scale = 1/(2^bits - 1), or 1 for FP32
 // input), then, for NR > 0, (I - mu) / sqrt(var + eps_n^2) with mu and var
@@ -86,12 +86,13 @@ static cudaError_t ingest_t(const IngestPair &p, int nframes, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Ingest nframes (1 or 2) frames in one launch (gridDim.z = nframes).
+// Ingest nframes (1 .. kMaxFramesPerLaunch) frames in one launch
+// (gridDim.z = nframes).
 cudaError_t launch_ingest_frames(const IngestArgs *f, int nframes, int store, cudaStream_t s)
 {
+    if (nframes < 1 || nframes > kMaxFramesPerLaunch) return cudaErrorInvalidValue;
     IngestPair p;
-    p.f[0] = f[0];
-    p.f[1] = f[nframes > 1 ? 1 : 0];
+    for (int k = 0; k < nframes; ++k) p.f[k] = f[k];
     p.scale = f[0].in_type == IN_F32 ? 1.0f : 1.0f / (float)((1u << f[0].bits) - 1u);
     switch (store) {
     case ST_F16: return ingest_t<__half>(p, nframes, s);
@@ -104,7 +105,7 @@ cudaError_t launch_ingest_frames(const IngestArgs *f, int nframes, int store, cu
 // Pyramid reduction: out(i,j) = sum_{a,b=-2..2} c_a c_b P(2i+a, 2j+b),
 // c = [1 4 6 4 1]/16, clamp-to-edge, out size ceil(H/2) x ceil(W/2).
 // ---------------------------------------------------------------------------
-struct ReducePair { ReduceArgs f[2]; };
+struct ReducePair { ReduceArgs f[kMaxFramesPerLaunch]; };
 
 template <typename TS>
 __global__ void __launch_bounds__(256) k_reduce(ReducePair p)
@@ -130,12 +131,12 @@ __global__ void __launch_bounds__(256) k_reduce(ReducePair p)
     st_store(static_cast<TS *>(a.dst) + (int64_t)i * a.dpitch + j, acc);
 }
 
-// Reduce one level of nframes (1 or 2) frames in one launch.
+// Reduce one level of nframes (1 .. kMaxFramesPerLaunch) frames in one launch.
 cudaError_t launch_reduce_frames(const ReduceArgs *f, int nframes, int store, cudaStream_t s)
 {
+    if (nframes < 1 || nframes > kMaxFramesPerLaunch) return cudaErrorInvalidValue;
     ReducePair p;
-    p.f[0] = f[0];
-    p.f[1] = f[nframes > 1 ? 1 : 0];
+    for (int k = 0; k < nframes; ++k) p.f[k] = f[k];
     dim3 blk(32, 8);
     dim3 grd((f[0].Wd + 31) / 32, (f[0].Hd + 7) / 8, nframes);
     switch (store) {

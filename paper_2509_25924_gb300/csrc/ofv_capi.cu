@@ -1,6 +1,11 @@
 // C ABI of the OFV estimator: handle, workspace, argument checks and the
 // level loop of Sec. 2 (normalize -> pyramid -> per level IT Gauss-Newton
 // iterations of Eq. 2 -> up-sample to the next finer level).
+//
+// Several pairs of a time-resolved sequence are processed together: their
+// frames are ingested and reduced in shared launches and each (level,
+// iteration) of the fused path is one launch over all of them, which keeps
+// the coarse levels from leaving the GPU idle.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,6 +39,8 @@ ofv_status cuda_fail(cudaError_t e, const char *where)
 }
 
 constexpr int kMaxLevels = 16;
+constexpr int kMaxBatch = kMaxPairsPerLaunch;
+constexpr int kMaxSlots = kMaxBatch + 1;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -52,21 +59,23 @@ struct ofv_handle {
     int H, W;
     ofv_params p;
     int L;
+    int B;       // pairs per launch in sequences
+    int nslots;  // pyramid slots (B + 1)
     int Hs[kMaxLevels], Ws[kMaxLevels], pitch[kMaxLevels];
     int vpitch;
     int device;
     void *arena;
     size_t arena_bytes;
-    void *lvl[2][kMaxLevels];  // two pyramid slots
-    float2 *vbuf[2];
+    void *lvl[kMaxSlots][kMaxLevels];
+    float2 *vbuf[2 * kMaxBatch];  // two ping-pong fields per pair
     float *w25;
-    float *tmp[2];
+    float *tmp[kMaxSlots];        // pre-filter input, one per frame of an ingest launch
     PlainBufs plain;
     // host-pointer entry point staging (allocated on first use)
     void *stage;
     size_t stage_bytes;
-    // which slot holds I1 of the last computed pair
-    int last_slot1;
+    // slots of I1 and I2 of the last computed pair
+    int last_s1, last_s2;
     // kernel timing
     bool prof;
     std::vector<ProfRec> recs;
@@ -111,13 +120,15 @@ ofv_status check_params(const ofv_params *p)
     }
     if (p->storage != OFV_STORE_F32 && p->storage != OFV_STORE_F16 && p->storage != OFV_STORE_BF16)
         return fail(OFV_ERR_INVALID_ARG, "storage=%d is not an ofv_storage_t", p->storage);
-    if (p->path != OFV_PATH_FUSED && p->path != OFV_PATH_PLAIN)
+    if (p->path != OFV_PATH_FUSED && p->path != OFV_PATH_PLAIN && p->path != OFV_PATH_TILE)
         return fail(OFV_ERR_INVALID_ARG, "path=%d is not an ofv_path_t", p->path);
     if (p->prefilter != 0 && p->prefilter != 1)
         return fail(OFV_ERR_INVALID_ARG, "prefilter=%d is not 0 or 1", p->prefilter);
     if (!(p->det_rel_eps >= 0.f) || !std::isfinite(p->det_rel_eps) || !(p->det_abs_eps >= 0.f) ||
         !std::isfinite(p->det_abs_eps) || !(p->norm_eps > 0.f) || !std::isfinite(p->norm_eps))
         return fail(OFV_ERR_INVALID_ARG, "guard / normalization epsilons must be finite (norm_eps > 0)");
+    if (p->max_batch < 0 || p->max_batch > kMaxBatch)
+        return fail(OFV_ERR_INVALID_ARG, "max_batch=%d outside 0..%d", p->max_batch, kMaxBatch);
     return OFV_OK;
 }
 
@@ -163,14 +174,13 @@ struct ProfScope {
     }
 };
 
-// Stage 1-2: ingest frames into pyramid slots and reduce.  frames[k] goes to
-// slot slots[k].
-ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf,
-                          cudaStream_t s)
+// Steps 1-2: ingest nf frames (frames[k] into pyramid slot slots[k]) and
+// reduce them, nf frames per launch.
+ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s)
 {
     const ofv_params &p = h->p;
     const int sb = store_bytes(p.storage), ib = input_bytes(p.input);
-    IngestArgs ia[2];
+    IngestArgs ia[kMaxFramesPerLaunch];
     for (int k = 0; k < nf; ++k) {
         IngestArgs &a = ia[k];
         a.raw = frames[k];
@@ -193,7 +203,7 @@ ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *s
         if (st != OFV_OK) return st;
     }
     for (int l = 1; l < h->L; ++l) {
-        ReduceArgs ra[2];
+        ReduceArgs ra[kMaxFramesPerLaunch];
         for (int k = 0; k < nf; ++k) {
             ReduceArgs &r = ra[k];
             r.src = h->lvl[slots[k]][l - 1];
@@ -213,55 +223,65 @@ ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *s
     return OFV_OK;
 }
 
-// Stages 3-6: coarse-to-fine Gauss-Newton on the pyramids in slots s1, s2.
-ofv_status run_levels(ofv_handle *h, int s1, int s2, float *u, float *v, cudaStream_t s)
+// Steps 3-6 for np pairs: pair k uses pyramid slots s1[k], s2[k], field
+// buffers vbuf[2k], vbuf[2k+1], and writes u[k], v[k].
+ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float *const *u, float *const *v,
+                      cudaStream_t s)
 {
     const ofv_params &p = h->p;
     const int sb = store_bytes(p.storage);
-    int cur = 0;  // index of the vbuf holding the latest field
+    int cur = 0;  // vbuf[2k + cur] holds the latest field of pair k
     bool have = false;
     for (int l = h->L - 1; l >= 0; --l) {
         for (int t = 0; t < p.iterations; ++t) {
-            IterArgs a;
-            memset(&a, 0, sizeof a);
-            a.P1 = h->lvl[s1][l];
-            a.P2 = h->lvl[s2][l];
-            a.H = h->Hs[l];
-            a.W = h->Ws[l];
-            a.pitch = h->pitch[l];
-            a.vpitch = h->vpitch;
-            a.vcpitch = h->vpitch;
-            a.kr = p.kernel_radius;
-            a.eps_rel = p.det_rel_eps;
-            a.eps_abs = p.det_abs_eps;
             int mode;
-            const double Nl = (double)a.H * a.W;
-            double vread = 0.0;
-            if (t == 0 && l == h->L - 1) {
-                mode = V0_ZERO;
-            } else if (t == 0) {
-                mode = V0_UP;
-                a.Vc = h->vbuf[cur];
-                a.Hc = h->Hs[l + 1];
-                a.Wc = h->Ws[l + 1];
-                vread = 8.0 * a.Hc * a.Wc;
-            } else {
-                mode = V0_SAME;
-                a.V0 = h->vbuf[cur];
-                vread = 8.0 * Nl;
-            }
+            if (t == 0 && l == h->L - 1) mode = V0_ZERO;
+            else if (t == 0) mode = V0_UP;
+            else mode = V0_SAME;
             const bool last = (l == 0 && t == p.iterations - 1);
             const int nxt = have ? 1 - cur : 0;
-            if (last) {
-                a.u_out = u;
-                a.v_out = v;
-            } else {
-                a.Vout = h->vbuf[nxt];
+            IterArgs a[kMaxBatch];
+            for (int k = 0; k < np; ++k) {
+                IterArgs &x = a[k];
+                memset(&x, 0, sizeof x);
+                x.P1 = h->lvl[s1[k]][l];
+                x.P2 = h->lvl[s2[k]][l];
+                x.H = h->Hs[l];
+                x.W = h->Ws[l];
+                x.pitch = h->pitch[l];
+                x.vpitch = h->vpitch;
+                x.vcpitch = h->vpitch;
+                x.kr = p.kernel_radius;
+                x.eps_rel = p.det_rel_eps;
+                x.eps_abs = p.det_abs_eps;
+                if (mode == V0_UP) {
+                    x.Vc = h->vbuf[2 * k + cur];
+                    x.Hc = h->Hs[l + 1];
+                    x.Wc = h->Ws[l + 1];
+                } else if (mode == V0_SAME) {
+                    x.V0 = h->vbuf[2 * k + cur];
+                }
+                if (last) {
+                    x.u_out = u[k];
+                    x.v_out = v[k];
+                } else {
+                    x.Vout = h->vbuf[2 * k + nxt];
+                }
             }
-            const double bytes = 2.0 * sb * Nl + 8.0 * Nl + vread;
+            const double Nl = (double)h->Hs[l] * h->Ws[l];
+            const double vread = mode == V0_SAME ? 8.0 * Nl
+                                 : mode == V0_UP ? 8.0 * (double)h->Hs[l + 1] * h->Ws[l + 1]
+                                                 : 0.0;
+            const double bytes = np * (2.0 * sb * Nl + 8.0 * Nl + vread);
             ProfScope ps(h, s, OFV_K_ITERATE, bytes);
-            cudaError_t e = p.path == OFV_PATH_PLAIN ? launch_iter_plain(a, h->plain, p.storage, mode, s)
-                                                     : launch_iter_fused(a, p.storage, mode, s);
+            cudaError_t e = cudaSuccess;
+            if (p.path == OFV_PATH_FUSED && block_supports(p.kernel_radius)) {
+                e = launch_iter_block(a, np, p.storage, mode, s);
+            } else {
+                for (int k = 0; k < np && e == cudaSuccess; ++k)
+                    e = p.path == OFV_PATH_PLAIN ? launch_iter_plain(a[k], h->plain, p.storage, mode, s)
+                                                 : launch_iter_fused(a[k], p.storage, mode, s);
+            }
             ofv_status st = last_launch(e, "iteration launch");
             if (st != OFV_OK) return st;
             cur = nxt;
@@ -305,6 +325,7 @@ void ofv_default_params(ofv_params *p)
     p->det_rel_eps = 1e-6f;
     p->det_abs_eps = 1e-20f;
     p->norm_eps = 1e-2f;
+    p->max_batch = 0;
 }
 
 ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
@@ -334,6 +355,15 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
     h->W = W;
     h->p = *p;
     h->L = L;
+    // pairs per launch: enough pixels per launch (~16 Mp) to fill the GPU at
+    // the coarse levels, within the workspace that costs
+    if (p->max_batch > 0) {
+        h->B = p->max_batch;
+    } else {
+        const long long b = (16LL << 20) / ((long long)H * W);
+        h->B = (int)(b < 1 ? 1 : (b > kMaxBatch ? kMaxBatch : b));
+    }
+    h->nslots = h->B + 1;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return fail(OFV_ERR_CUDA, "cudaGetDevice failed");
@@ -348,22 +378,22 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
 
     // arena layout
     size_t off = 0;
-    size_t lvl_off[2][kMaxLevels];
-    for (int f = 0; f < 2; ++f)
+    size_t lvl_off[kMaxSlots][kMaxLevels];
+    for (int f = 0; f < h->nslots; ++f)
         for (int l = 0; l < L; ++l) {
             lvl_off[f][l] = off;
             off = align_up(off + (size_t)Hs[l] * h->pitch[l] * sb, 256);
         }
-    size_t vb_off[2];
-    for (int k = 0; k < 2; ++k) {
+    size_t vb_off[2 * kMaxBatch];
+    for (int k = 0; k < 2 * h->B; ++k) {
         vb_off[k] = off;
         off = align_up(off + (size_t)H * h->vpitch * sizeof(float2), 256);
     }
     const size_t w_off = off;
     off = align_up(off + 25 * sizeof(float), 256);
-    size_t tmp_off[2] = {0, 0};
+    size_t tmp_off[kMaxSlots] = {};
     if (p->prefilter)
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < h->nslots; ++k) {
             tmp_off[k] = off;
             off = align_up(off + (size_t)H * h->pitch[0] * sizeof(float), 256);
         }
@@ -385,11 +415,11 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
         return fail(OFV_ERR_ALLOC, "cudaMalloc of %zu workspace bytes failed: %s", off, cudaGetErrorString(e));
     }
     char *base = static_cast<char *>(h->arena);
-    for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < h->nslots; ++f)
         for (int l = 0; l < L; ++l) h->lvl[f][l] = base + lvl_off[f][l];
-    for (int k = 0; k < 2; ++k) h->vbuf[k] = reinterpret_cast<float2 *>(base + vb_off[k]);
+    for (int k = 0; k < 2 * h->B; ++k) h->vbuf[k] = reinterpret_cast<float2 *>(base + vb_off[k]);
     h->w25 = reinterpret_cast<float *>(base + w_off);
-    for (int k = 0; k < 2; ++k) h->tmp[k] = p->prefilter ? reinterpret_cast<float *>(base + tmp_off[k]) : nullptr;
+    for (int k = 0; k < h->nslots; ++k) h->tmp[k] = p->prefilter ? reinterpret_cast<float *>(base + tmp_off[k]) : nullptr;
     if (p->path == OFV_PATH_PLAIN) {
         h->plain.prod = reinterpret_cast<float *>(base + prod_off);
         h->plain.hsum = reinterpret_cast<float *>(base + hsum_off);
@@ -404,7 +434,8 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
         delete h;
         return cuda_fail(e, "initialising the pre-filter weights");
     }
-    h->last_slot1 = 0;
+    h->last_s1 = 0;
+    h->last_s2 = 1;
     *out = h;
     return OFV_OK;
 }
@@ -446,8 +477,11 @@ ofv_status ofv_compute(ofv_handle *h, const void *I1, const void *I2, float *u, 
     const int slots[2] = {0, 1};
     st = build_pyramids(h, fr, slots, 2, cs);
     if (st != OFV_OK) return st;
-    h->last_slot1 = 0;
-    return run_levels(h, 0, 1, u, v, cs);
+    h->last_s1 = 0;
+    h->last_s2 = 1;
+    const int s1[1] = {0}, s2[1] = {1};
+    float *uu[1] = {u}, *vv[1] = {v};
+    return run_levels(h, 1, s1, s2, uu, vv, cs);
 }
 
 ofv_status ofv_compute_host(ofv_handle *h, const void *I1, const void *I2, float *u, float *v, ofv_stream_t s)
@@ -501,24 +535,35 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
     const char *fb = static_cast<const char *>(frames);
-    // first pair: both frames
-    {
-        const void *fr[2] = {fb, fb + frame_stride_bytes};
-        const int slots[2] = {0, 1};
-        st = build_pyramids(h, fr, slots, 2, cs);
-        if (st != OFV_OK) return st;
-    }
-    for (int k = 0; k + 1 < n_frames; ++k) {
-        const int s1 = k & 1, s2 = (k + 1) & 1;
-        if (k > 0) {
-            const void *fr[1] = {fb + (size_t)(k + 1) * frame_stride_bytes};
-            const int slots[1] = {s2};
-            st = build_pyramids(h, fr, slots, 1, cs);
-            if (st != OFV_OK) return st;
+    const int B = h->B, NS = h->nslots;
+    const int npairs = n_frames - 1;
+    // Frame f lives in slot f mod (B+1).  A group of up to B pairs (frames
+    // f0 .. f0+np) reuses the pyramid of its first frame, which the previous
+    // group built; the other slots held frames of the previous group only.
+    for (int f0 = 0; f0 < npairs; f0 += B) {
+        const int np = npairs - f0 < B ? npairs - f0 : B;
+        const void *fr[kMaxSlots];
+        int slots[kMaxSlots];
+        int nf = 0;
+        for (int f = (f0 == 0 ? 0 : f0 + 1); f <= f0 + np; ++f) {
+            fr[nf] = fb + (size_t)f * frame_stride_bytes;
+            slots[nf] = f % NS;
+            ++nf;
         }
-        st = run_levels(h, s1, s2, u + (size_t)k * field_stride, v + (size_t)k * field_stride, cs);
+        st = build_pyramids(h, fr, slots, nf, cs);
         if (st != OFV_OK) return st;
-        h->last_slot1 = s1;
+        int s1[kMaxBatch], s2[kMaxBatch];
+        float *uu[kMaxBatch], *vv[kMaxBatch];
+        for (int k = 0; k < np; ++k) {
+            s1[k] = (f0 + k) % NS;
+            s2[k] = (f0 + k + 1) % NS;
+            uu[k] = u + (size_t)(f0 + k) * field_stride;
+            vv[k] = v + (size_t)(f0 + k) * field_stride;
+        }
+        st = run_levels(h, np, s1, s2, uu, vv, cs);
+        if (st != OFV_OK) return st;
+        h->last_s1 = s1[np - 1];
+        h->last_s2 = s2[np - 1];
     }
     return OFV_OK;
 }
@@ -538,7 +583,7 @@ ofv_status ofv_read_level(ofv_handle *h, int frame, int level, float *dst, ofv_s
     if (frame != 0 && frame != 1) return fail(OFV_ERR_INVALID_ARG, "frame=%d must be 0 or 1", frame);
     if (level < 0 || level >= h->L) return fail(OFV_ERR_INVALID_ARG, "level=%d outside 0..%d", level, h->L - 1);
     DeviceGuard g(h->device);
-    const int slot = frame == 0 ? h->last_slot1 : 1 - h->last_slot1;
+    const int slot = frame == 0 ? h->last_s1 : h->last_s2;
     return last_launch(launch_read_level(h->lvl[slot][level], h->Hs[level], h->Ws[level], h->pitch[level],
                                          h->p.storage, dst, (cudaStream_t)s),
                        "read_level launch");
@@ -598,6 +643,6 @@ const char *ofv_status_string(ofv_status s)
     return "OFV_ERR_UNKNOWN";
 }
 
-int ofv_version(void) { return 100; }
+int ofv_version(void) { return 200; }
 
 }  // extern "C"

@@ -18,6 +18,11 @@ enum V0Mode : int {
     V0_UP = 2     // first iteration of a finer level: 2 * bilinear(Vc, x/2, y/2)
 };
 
+// Pairs of one time-resolved sequence processed by one iteration launch, and
+// frames ingested or reduced by one launch.
+constexpr int kMaxPairsPerLaunch = 8;
+constexpr int kMaxFramesPerLaunch = kMaxPairsPerLaunch + 1;
+
 // Level images are stored with a row pitch (elements) that is a multiple of
 // 64, so every row starts 128-byte aligned in all storage types.
 constexpr int kPitchAlign = 64;
@@ -26,6 +31,10 @@ inline int pitch_for(int w) { return (w + kPitchAlign - 1) / kPitchAlign * kPitc
 __device__ __forceinline__ float ld_store(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld_store(const __half *p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ float ld_store(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ void st_store(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_store(__half *p, float v) { *p = __float2half_rn(v); }
@@ -48,7 +57,11 @@ struct IterArgs {
 };
 
 // Host-side launchers (defined in the kernel translation units).
+// Tile kernel: one CTA per 32x32 output tile, products staged in shared memory.
 cudaError_t launch_iter_fused(const IterArgs &a, int store, int mode, cudaStream_t s);
+// Block-tiled kernel (KR 1..10): npairs pairs of equal level size in one launch.
+bool block_supports(int kr);
+cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s);
 
 struct PlainBufs {
     float *prod;  // 5 planes, each H x pitch floats

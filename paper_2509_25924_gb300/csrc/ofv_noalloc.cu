@@ -210,7 +210,8 @@ extern "C" ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *p, con
             } else {
                 a.Vout = vbuf[nxt];
             }
-            e = launch_iter_fused(a, p->storage, mode, cs);
+            e = block_supports(p->kernel_radius) ? launch_iter_block(&a, 1, p->storage, mode, cs)
+                                                 : launch_iter_fused(a, p->storage, mode, cs);
             cur = nxt;
             have = true;
         }

@@ -55,8 +55,8 @@ def test_defaults_follow_the_documented_values():
 @pytest.mark.parametrize("field,value", [
     ("levels_psl", -1), ("levels_psl", 16), ("kernel_radius", 0), ("kernel_radius", 17),
     ("iterations", 0), ("iterations", 65), ("norm_radius", -1), ("input", 7), ("storage", 3),
-    ("path", 2), ("prefilter", 2), ("bit_depth", 0), ("bit_depth", 17), ("det_rel_eps", float("nan")),
-    ("norm_eps", 0.0),
+    ("path", 3), ("prefilter", 2), ("bit_depth", 0), ("bit_depth", 17), ("det_rel_eps", float("nan")),
+    ("norm_eps", 0.0), ("max_batch", -1), ("max_batch", 9),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(field, value):
     p = ofv.ofv_default_params(**{field: value})

@@ -97,6 +97,7 @@ def compare(u, v, ou, ov, nd, tol=FP32_TOL, rms_tol=None, max_masked=0.01, label
 
 
 PARAMS = dict(levels_psl=2, kernel_radius=4, iterations=3)
+PATHS = [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN, ofv.OFV_PATH_TILE]
 
 
 # --------------------------------------------------------------------------
@@ -109,7 +110,7 @@ def rankine():
     return I1, I2, ou, ov, nd, tu, tv
 
 
-@pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN])
+@pytest.mark.parametrize("path", PATHS)
 def test_rankine_fp32_matches_oracle(rankine, path):
     I1, I2, ou, ov, nd, tu, tv = rankine
     u, v = gpu_flow(I1, I2, path=path, **PARAMS)
@@ -135,7 +136,7 @@ def test_runs_are_bitwise_deterministic(rankine):
 
 
 @pytest.mark.parametrize("storage", [ofv.OFV_STORE_F32, ofv.OFV_STORE_F16, ofv.OFV_STORE_BF16])
-@pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN])
+@pytest.mark.parametrize("path", PATHS)
 def test_zero_motion_is_exactly_zero(storage, path):
     I1, _, _, _ = synth.rankine_pair(128, 160, seed=3)
     u, v = gpu_flow(I1, I1.copy(), storage=storage, path=path, **PARAMS)
@@ -203,7 +204,7 @@ def test_ingest_and_pyramid_levels_match_oracle(nr, pre, shape):
             assert err < 2e-5, f"frame {f} level {l}: rel err {err:.2e}"
 
 
-@pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN])
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("psl,it", [(0, 1), (1, 1), (0, 3)])
 def test_single_level_and_upsample_paths(path, psl, it):
     """PSL 0 IT 1 is one iteration from V = 0 (textbook LK); PSL 1 IT 1 adds
@@ -222,6 +223,29 @@ def test_ragged_shapes_and_minimum_levels(H, W, psl, kr, it):
     ou, ov, nd, _ = oracle_flow(I1, I2, psl=psl, kr=kr, it=it)
     sens = fp32_sensitivity(I1, I2, psl=psl, kr=kr, it=it)
     compare(u, v, ou, ov, nd, label=f"{H}x{W} psl={psl} kr={kr} it={it}", max_masked=0.05, sens=sens)
+
+
+@pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_TILE])
+def test_large_displacement_uses_global_taps(path):
+    """A (9.3, -8.7) px shift with PSL 3: at level 0 the warp offsets exceed
+    the margin the block kernel stages in shared memory, so its taps come from
+    global memory; the result must not change."""
+    I1, I2 = synth.translation_pair(384, 320, (9.3, -8.7), seed=61, kind=synth.OUT_F32, ppp=0.06)
+    u, v = gpu_flow(I1, I2, path=path, levels_psl=3, kernel_radius=4, iterations=3)
+    ou, ov, nd, _ = oracle_flow(I1, I2, psl=3)
+    compare(u, v, ou, ov, nd, label=f"shift 9.3,-8.7 path={path}")
+    s = (slice(20, -20), slice(20, -20))
+    assert np.abs(ou[s] - 9.3).mean() < 0.1 and np.abs(ov[s] + 8.7).mean() < 0.1
+
+
+@pytest.mark.parametrize("kr", [1, 2, 3, 5, 6, 8, 9, 10, 12])
+def test_every_window_radius(kr):
+    """The block kernel is compiled per radius 1..10; 12 takes the tile kernel."""
+    I1, I2 = synth.translation_pair(200, 330, (1.7, 0.8), seed=70 + kr, kind=synth.OUT_F32)
+    u, v = gpu_flow(I1, I2, levels_psl=1, kernel_radius=kr, iterations=2)
+    ou, ov, nd, _ = oracle_flow(I1, I2, psl=1, kr=kr, it=2)
+    sens = fp32_sensitivity(I1, I2, psl=1, kr=kr, it=2) if kr <= 2 else None
+    compare(u, v, ou, ov, nd, label=f"kr={kr}", max_masked=0.05, sens=sens)
 
 
 def test_u8_input_with_paper_benchmark_parameters():
@@ -255,16 +279,22 @@ def test_reduced_storage_rms(storage):
 # --------------------------------------------------------------------------
 # entry points
 # --------------------------------------------------------------------------
-def test_sequence_equals_pairwise_and_host_entry_point():
-    F = synth.stream_frames(192, 256, 5, seed=2)
-    p = ofv.ofv_default_params(**PARAMS)
+@pytest.mark.parametrize("path,batch", [(ofv.OFV_PATH_FUSED, 0), (ofv.OFV_PATH_FUSED, 1), (ofv.OFV_PATH_FUSED, 3),
+                                        (ofv.OFV_PATH_FUSED, 8), (ofv.OFV_PATH_PLAIN, 3), (ofv.OFV_PATH_TILE, 2)])
+def test_sequence_equals_pairwise_and_host_entry_point(path, batch):
+    """Pairs batched into shared launches (groups of `batch`, a partial last
+    group, pyramids reused across groups) give bitwise the fields of one
+    ofv_compute per pair."""
+    n = 11
+    F = synth.stream_frames(192, 256, n, seed=2)
+    p = ofv.ofv_default_params(path=path, max_batch=batch, **PARAMS)
     H, W = 192, 256
     h = ofv.ofv_create(H, W, p)
     try:
         fr = torch.from_numpy(F).to(DEV)
-        us = torch.empty((4, H, W), device=DEV); vs = torch.empty_like(us)
-        ofv.ofv_compute_sequence(h, 5, fr, H * W * 2, us, vs, H * W)
-        for k in range(4):
+        us = torch.empty((n - 1, H, W), device=DEV); vs = torch.empty_like(us)
+        ofv.ofv_compute_sequence(h, n, fr, H * W * 2, us, vs, H * W)
+        for k in range(n - 1):
             u = torch.empty((H, W), device=DEV); v = torch.empty_like(u)
             ofv.ofv_compute(h, fr[k], fr[k + 1], u, v)
             torch.cuda.synchronize()
