@@ -250,40 +250,51 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __gr
     const T *P2 = static_cast<const T *>(a.P2);
 
     // phase 0: stage both frames (rows sy0 .. sy0+SH-1, columns sx0 .. sx0+SP-1)
+    // 16-byte chunks inside the image rows are copied asynchronously; chunks
+    // that straddle the left or right border are filled element by element
+    // with clamped columns.  Rows are clamped as a whole.
     const bool vec_ok = sx0 >= 0 && sx0 + SP <= W;
-    if (vec_ok) {
-        for (int t = tid; t < 2 * SH * NV; t += NT) {
-            const int f = t >= SH * NV ? 1 : 0;
-            const int r = t - f * SH * NV;
-            const int row = r / NV, v = r - row * NV;
-            const int gy = min(max(sy0 + row, 0), H - 1);
-            cp_async16(stage + (f * SH + row) * SP + v * VEC, (f ? P2 : P1) + (int64_t)gy * pitch + sx0 + v * VEC);
-        }
-        cp_async_wait_all();
-    } else {
-        for (int t = tid; t < 2 * SH * SP; t += NT) {
-            const int f = t >= SH * SP ? 1 : 0;
-            const int r = t - f * SH * SP;
-            const int row = r / SP, c = r - row * SP;
-            const int gy = min(max(sy0 + row, 0), H - 1);
-            const int gx = min(max(sx0 + c, 0), W - 1);
-            stage[(f * SH + row) * SP + c] = (f ? P2 : P1)[(int64_t)gy * pitch + gx];
+    for (int t = tid; t < 2 * SH * NV; t += NT) {
+        const int f = t >= SH * NV ? 1 : 0;
+        const int r = t - f * SH * NV;
+        const int row = r / NV, v = r - row * NV;
+        const int gy = min(max(sy0 + row, 0), H - 1);
+        const int gx0 = sx0 + v * VEC;
+        const T *src = (f ? P2 : P1) + (int64_t)gy * pitch;
+        T *dst = stage + (f * SH + row) * SP + v * VEC;
+        if (gx0 >= 0 && gx0 + VEC <= W) {
+            cp_async16(dst, src + gx0);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) dst[e] = src[min(max(gx0 + e, 0), W - 1)];
         }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // phase 1: products on tile + halo.  A tile whose staged rows and columns
     // all lie inside the image needs no clamping or border remap.
+    // Pixels at least REACH+1 px from every border take the same fast path
+    // inside border tiles too (their taps never clamp or remap).
     const bool interior = vec_ok && sy0 >= 0 && sy0 + SH <= H;
+    constexpr int DY = NT / RW, DX = NT % RW;  // index step in rows and columns
+    int ry = tid / RW, rx = tid - (tid / RW) * RW;
+    // V0 of the thread's next pixel is loaded one iteration ahead
+    float2 V0n = make_float2(0.f, 0.f);
+    if (ry < RW && py0 + ry >= 0 && py0 + ry < H && px0 + rx >= 0 && px0 + rx < W)
+        V0n = fetch_v0_rt(a, mode, px0 + rx, py0 + ry);
     for (int idx = tid; idx < RW * RW; idx += NT) {
-        const int ry = idx / RW, rx = idx - ry * RW;
         const int gy = py0 + ry, gx = px0 + rx;
+        const float2 V0c = V0n;
+        int nry = ry + DY, nrx = rx + DX;
+        if (nrx >= RW) { nrx -= RW; ++nry; }
+        if (idx + NT < RW * RW && py0 + nry >= 0 && py0 + nry < H && px0 + nrx >= 0 && px0 + nrx < W)
+            V0n = fetch_v0_rt(a, mode, px0 + nrx, py0 + nry);
         float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (interior) {
-            const float2 V0 = fetch_v0_rt(a, mode, gx, gy);
-            products_interior<T, SP>(stage, stage + SH * SP, sx0, sy0, a, gx, gy, V0, p);
+        if (interior || (gx > kBlockReach && gx < W - kBlockReach - 2 && gy > kBlockReach && gy < H - kBlockReach - 2)) {
+            products_interior<T, SP>(stage, stage + SH * SP, sx0, sy0, a, gx, gy, V0c, p);
         } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            const float2 V0 = fetch_v0_rt(a, mode, gx, gy);
+            const float2 V0 = V0c;
             const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
             const Sample s1 = sample_staged<T, SP>(stage, sx0, sy0, P1, H, W, pitch, gx, gy, -hx, -hy);
             const Sample s2 = sample_staged<T, SP>(stage + SH * SP, sx0, sy0, P2, H, W, pitch, gx, gy, hx, hy);
@@ -302,6 +313,8 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __gr
         q[2 * PLANE] = p[2];
         q[3 * PLANE] = p[3];
         q[4 * PLANE] = p[4];
+        ry = nry;
+        rx = nrx;
     }
     __syncthreads();
 
@@ -329,10 +342,12 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __gr
         const float tr = sxx + syy;
         const float det = sxx * syy - sxy * sxy;
         float2 V;
-        if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr)
+        if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr) {
             V = fetch_v0_rt(a, mode, gx, gy);
-        else
-            V = make_float2((syy * sxr - sxy * syr) / det, (sxx * syr - sxy * sxr) / det);
+        } else {
+            const float inv = __frcp_rn(det);  // one correctly rounded reciprocal, two products
+            V = make_float2((syy * sxr - sxy * syr) * inv, (sxx * syr - sxy * sxr) * inv);
+        }
         if (a.u_out) {
             a.u_out[(int64_t)gy * W + gx] = V.x;
             a.v_out[(int64_t)gy * W + gx] = V.y;
