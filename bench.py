@@ -290,6 +290,8 @@ def run_ours(args, ws, rank, local):
 
     if not args.no_sizes:
         line["sizes"] = sizes(ofv, torch, synth, dev, stream, frames, u, v)
+        line["live_21Mp"] = live_loop(ofv, torch, synth, dev, stream)
+        line["batched_64_uneven"] = batched_uneven(ofv, torch, synth, dev, stream)
 
     ofv.ofv_destroy(h)
     del u, v, frames
@@ -392,6 +394,97 @@ def sizes(ofv, torch, synth, dev, stream, frames1, u1, v1):
             del frames, u, v
             torch.cuda.empty_cache()
     return out
+
+
+def live_loop(ofv, torch, synth, dev, stream, n_pairs=2000, ring=8):
+    """21 Mp live analogue: a device ring of `ring` pre-generated pairs of
+    the cylinder-wake stream (5120x4096 u16), one CUDA graph per ring pair,
+    replayed back to back for n_pairs fields; per-field device time from
+    CUDA events between graph launches."""
+    H, W = 4096, 5120
+    fld, inside = synth.wake_field(H, W)
+    fr = synth.stream_frames(H, W, ring + 1, seed=4, ppp=0.1, field=fld, field_max=8.0, exclude=inside)
+    frames = torch.from_numpy(fr).to(dev)
+    u = torch.empty((2, H, W), dtype=torch.float32, device=dev)
+    v = torch.empty_like(u)
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params())
+    graphs = []
+    try:
+        for k in range(ring):
+            graphs.append(ofv.ofv_graph_create(h, frames[k], frames[k + 1], u[k % 2], v[k % 2]))
+        for k in range(ring):
+            ofv.ofv_graph_launch(graphs[k], stream)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_pairs + 1)]
+        ev[0].record(stream)
+        for i in range(n_pairs):
+            ofv.ofv_graph_launch(graphs[i % ring], stream)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        per = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(n_pairs)])
+        total = ev[0].elapsed_time(ev[-1])
+    finally:
+        for g in graphs:
+            ofv.ofv_graph_destroy(g)
+        ofv.ofv_destroy(h)
+    del frames, u, v
+    torch.cuda.empty_cache()
+    return {"workload": "5120x4096 u16 cylinder-wake stream, ring of 8 pairs, one CUDA graph per pair",
+            "pairs": n_pairs, "hz": n_pairs / (total / 1e3), "p50_ms": float(np.percentile(per, 50)),
+            "p99_ms": float(np.percentile(per, 99)), "max_ms": float(per.max())}
+
+
+def batched_uneven(ofv, torch, synth, dev, stream, n_pairs=64, reps=5):
+    """64 pairs with sizes drawn (seed 5) from {256^2, 512^2, 768x1024,
+    1024^2}, turbulence displacement: one ofv_compute_batched call (one
+    persistent launch for all iterations) vs one ofv_compute per pair.  Each
+    pair has its own device buffers; pairs of one size class share content."""
+    classes = [(256, 256), (512, 512), (768, 1024), (1024, 1024)]
+    rng = np.random.default_rng(5)
+    pick = rng.integers(0, len(classes), size=n_pairs)
+    content = {}
+    for c in sorted(set(pick.tolist())):
+        H, W = classes[c]
+        fld = synth.turbulence_field(H, W, seed=3 + c).sampled(H, W)
+        I1, I2 = synth.particle_pair(H, W, fld, ppp=0.1, dmin=2.0, dmax=3.0, seed=30 + c, noise=0.01,
+                                     kind=synth.OUT_U16, field_max=8.0)
+        content[c] = (torch.from_numpy(I1).to(dev), torch.from_numpy(I2).to(dev))
+    pairs = []
+    for c in pick.tolist():
+        H, W = classes[c]
+        a, b = content[c]
+        pairs.append((a.clone(), b.clone(), torch.empty((H, W), device=dev), torch.empty((H, W), device=dev)))
+    mpix = sum(p[0].numel() for p in pairs) / 1e6
+    h = ofv.ofv_create(256, 256, ofv.ofv_default_params())
+    try:
+        ofv.ofv_compute_batched(h, pairs, stream)  # tunes on first use
+        tune = ofv.ofv_batch_tuning(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ofv.ofv_compute_batched(h, pairs, stream)
+        torch.cuda.synchronize()
+        batched = n_pairs * reps / (time.perf_counter() - t0)
+    finally:
+        ofv.ofv_destroy(h)
+    handles = {c: ofv.ofv_create(*classes[c], ofv.ofv_default_params()) for c in content}
+    try:
+        def seq():
+            for c, p in zip(pick.tolist(), pairs):
+                ofv.ofv_compute(handles[c], p[0], p[1], p[2], p[3], stream)
+        seq()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            seq()
+        torch.cuda.synchronize()
+        sequential = n_pairs * reps / (time.perf_counter() - t0)
+    finally:
+        for hh in handles.values():
+            ofv.ofv_destroy(hh)
+    return {"pairs": n_pairs, "mpix_per_batch": mpix, "batched_fields_per_s": batched,
+            "batched_mvectors_per_s": batched * mpix / n_pairs, "sequential_fields_per_s": sequential,
+            "tuning": tune, "timing": "host wall clock over 5 batches (the batched call synchronises)"}
 
 
 def cpu_baseline(frames_h):

@@ -165,6 +165,58 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
 ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *params, const float *w25, const void *I1,
                                const void *I2, float *u, float *v, ofv_stream_t s);
 
+/* ---- many pairs of unequal size -----------------------------------------
+ * One pair of a batch: frames I1, I2 (H x W, the handle's input type) and
+ * outputs u, v (H x W float), all device pointers. */
+typedef struct {
+    int H, W;
+    const void *I1, *I2;
+    float *u, *v;
+} ofv_pair;
+
+/* Estimate n pairs of any sizes (each within the shape limits of
+ * ofv_create for the handle's parameters; the handle's own H, W do not
+ * matter) with the handle's parameters.  pairs is a HOST array.  The frames
+ * are ingested and reduced size class by size class, then every (level,
+ * iteration, tile) of every pair runs in ONE persistent launch of the fused
+ * kernel: CTAs take work units from a queue in the order of a schedule, and
+ * a unit of one Gauss-Newton iteration waits (bounded) until the previous
+ * iteration of its pair is complete.  The first batch of a given signature
+ * (sorted sizes and parameters) runs the autotuner: each candidate schedule
+ * (all pairs stage by stage, or groups of 8 pairs) and persistent grid (one
+ * or two CTAs per SM) is timed on the batch itself and the fastest is kept
+ * for later batches of that signature.  The call returns when the batch is
+ * complete (it synchronises s).  A workspace for the batch is allocated on
+ * first use and grown when a larger batch arrives.  Needs the fused path with
+ * KR <= 10 (else OFV_ERR_UNSUPPORTED).  OFV_ERR_TIMEOUT if a dependency wait
+ * expired (5 s). */
+ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t s);
+
+/* Configuration used by the last ofv_compute_batched call: schedule (0 =
+ * stage-major over all pairs, else group size), persistent CTAs per SM,
+ * duration of its persistent launch in ms, and whether that call tuned. */
+ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm, double *ms, int *tuned);
+
+/* Test hook for the bounded waits of the persistent launch: runs one CTA
+ * whose work unit depends on a counter nothing increments.  Expected result:
+ * OFV_ERR_TIMEOUT after about timeout_us, *error_word = 1, the device still
+ * usable. */
+ofv_status ofv_queue_selftest(int timeout_us, int *error_word);
+
+/* ---- CUDA-graph replay (live loop) -------------------------------------
+ * A live acquisition hands the estimator a new pair into the same device
+ * buffers at a fixed rate (Sec. 6, live mode).  ofv_graph_create records the
+ * whole launch sequence of ofv_compute(h, I1, I2, u, v) for those fixed
+ * buffers into a CUDA graph (after one eager run that prepares the kernels),
+ * so each new pair costs one ofv_graph_launch instead of ~PSL + L*IT + 1
+ * launches.  The graph uses the handle's workspace: the handle must outlive
+ * it, and launches of graphs and compute calls of one handle must be
+ * ordered (one stream).  Kernel timing is not recorded inside graphs. */
+typedef struct ofv_graph ofv_graph;
+ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float *u, float *v, ofv_graph **out);
+ofv_status ofv_graph_launch(ofv_graph *g, ofv_stream_t s);
+ofv_status ofv_graph_destroy(ofv_graph *g);
+
 /* Dimensions of pyramid level l (0 = full resolution). */
 ofv_status ofv_level_shape(const ofv_handle *h, int level, int *H, int *W);
 

@@ -33,7 +33,9 @@ OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED_SYMBOLS = [
     "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_compute",
-    "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_level_shape", "ofv_read_level",
+    "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_graph_create", "ofv_graph_launch",
+    "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_level_shape",
+    "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
 ]
 
@@ -68,6 +70,13 @@ def _load_library():
         "ofv_compute_host": ([P, P, P, P, P, P], I),
         "ofv_compute_sequence": ([P, I, P, Z, P, P, Z, P], I),
         "ofv_compute_noalloc": ([I, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
+        "ofv_graph_create": ([P, P, P, P, P, ctypes.POINTER(P)], I),
+        "ofv_graph_launch": ([P, P], I),
+        "ofv_graph_destroy": ([P], I),
+        "ofv_compute_batched": ([P, I, P, P], I),
+        "ofv_batch_tuning": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(I)], I),
+        "ofv_queue_selftest": ([I, ctypes.POINTER(I)], I),
         "ofv_level_shape": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "ofv_read_level": ([P, I, I, P, P], I),
         "ofv_profile_enable": ([P, I], I),
@@ -164,6 +173,58 @@ def ofv_compute_noalloc(H: int, W: int, params: Params, w25, I1, I2, u, v, strea
     array (OFV_NOALLOC_SCRATCH_BYTES).  See include/ofv.h for its limits."""
     _check(_lib.ofv_compute_noalloc(H, W, ctypes.byref(params), _addr(w25), _addr(I1), _addr(I2), _addr(u),
                                     _addr(v), _stream(stream)), "ofv_compute_noalloc")
+
+
+class Pair(ctypes.Structure):
+    """Mirror of ofv_pair (include/ofv.h)."""
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("I1", ctypes.c_void_p), ("I2", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("v", ctypes.c_void_p)]
+
+
+def ofv_compute_batched(h: int, pairs, stream=None):
+    """pairs: sequence of (I1, I2, u, v) CUDA tensors (each H x W) or Pair
+    structures; all pairs of the batch run in one persistent launch."""
+    arr = (Pair * len(pairs))()
+    for k, p in enumerate(pairs):
+        if isinstance(p, Pair):
+            arr[k] = p
+        else:
+            I1, I2, u, v = p
+            H, W = I1.shape[-2], I1.shape[-1]
+            arr[k] = Pair(H, W, _addr(I1), _addr(I2), _addr(u), _addr(v))
+    _check(_lib.ofv_compute_batched(h, len(pairs), ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
+           "ofv_compute_batched")
+
+
+def ofv_batch_tuning(h: int):
+    s, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(_lib.ofv_batch_tuning(h, ctypes.byref(s), ctypes.byref(c), ctypes.byref(ms), ctypes.byref(t)),
+           "ofv_batch_tuning")
+    return {"schedule": s.value, "ctas_per_sm": c.value, "ms": ms.value, "tuned": bool(t.value)}
+
+
+def ofv_queue_selftest(timeout_us: int):
+    """Returns (status, error_word) without raising."""
+    w = ctypes.c_int()
+    st = _lib.ofv_queue_selftest(timeout_us, ctypes.byref(w))
+    return st, w.value
+
+
+def ofv_graph_create(h: int, I1, I2, u, v) -> int:
+    """Record ofv_compute(h, I1, I2, u, v) for these fixed buffers as a CUDA
+    graph; replay it with ofv_graph_launch."""
+    g = ctypes.c_void_p()
+    _check(_lib.ofv_graph_create(h, _addr(I1), _addr(I2), _addr(u), _addr(v), ctypes.byref(g)), "ofv_graph_create")
+    return g.value
+
+
+def ofv_graph_launch(g: int, stream=None):
+    _check(_lib.ofv_graph_launch(g, _stream(stream)), "ofv_graph_launch")
+
+
+def ofv_graph_destroy(g: int):
+    _check(_lib.ofv_graph_destroy(g), "ofv_graph_destroy")
 
 
 def ofv_level_shape(h: int, level: int):

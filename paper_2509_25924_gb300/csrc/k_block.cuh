@@ -70,11 +70,36 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// V0 at (x, y) with the mode chosen at run time (uniform per launch).
+// Field load: through the read-only cache, or -- when the field was written
+// earlier in the same launch by other CTAs (persistent batched kernel) --
+// from L2 only, so no stale L1 line is read.
+template <bool COH>
+__device__ __forceinline__ float2 ld_field(const float2 *p)
+{
+    return COH ? __ldcg(p) : __ldg(p);
+}
+
+// V0 at (x, y) with the mode chosen at run time (uniform per launch):
+// zero, the same-level field, or 2 * bilinear(coarse field, x/2, y/2).
+template <bool COH>
 __device__ __forceinline__ float2 fetch_v0_rt(const IterArgs &a, int mode, int x, int y)
 {
-    if (mode == V0_SAME) return fetch_v0<V0_SAME>(a, x, y);
-    if (mode == V0_UP) return fetch_v0<V0_UP>(a, x, y);
+    if (mode == V0_SAME) return ld_field<COH>(a.V0 + (int64_t)y * a.vpitch + x);
+    if (mode == V0_UP) {
+        const int cx = x >> 1, cy = y >> 1;
+        const float fx = (x & 1) ? 0.5f : 0.f, fy = (y & 1) ? 0.5f : 0.f;
+        const int cx1 = min(cx + 1, a.Wc - 1), cy1 = min(cy + 1, a.Hc - 1);
+        const int cxa = min(cx, a.Wc - 1), cya = min(cy, a.Hc - 1);
+        const float2 v00 = ld_field<COH>(a.Vc + (int64_t)cya * a.vcpitch + cxa);
+        const float2 v01 = ld_field<COH>(a.Vc + (int64_t)cya * a.vcpitch + cx1);
+        const float2 v10 = ld_field<COH>(a.Vc + (int64_t)cy1 * a.vcpitch + cxa);
+        const float2 v11 = ld_field<COH>(a.Vc + (int64_t)cy1 * a.vcpitch + cx1);
+        const float wx0 = 1.f - fx, wy0 = 1.f - fy;
+        float2 r;
+        r.x = 2.f * (wy0 * (wx0 * v00.x + fx * v01.x) + fy * (wx0 * v10.x + fx * v11.x));
+        r.y = 2.f * (wy0 * (wx0 * v00.y + fx * v01.y) + fy * (wx0 * v10.y + fx * v11.y));
+        return r;
+    }
     return make_float2(0.f, 0.f);
 }
 
@@ -224,8 +249,8 @@ __device__ __forceinline__ void window_sums_inplace(float *line, int stride)
     if (b < TS) window_block<KR, TS, true>(line, stride, b);
 }
 
-template <typename T, int KR>
-__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __grid_constant__ BlockParams prm)
+template <typename T, int KR, bool COH>
+__device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4)
 {
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
@@ -233,15 +258,12 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __gr
     constexpr int SP = SS::SP, NV = SS::NV, VEC = SS::VEC;
     constexpr int PLANE = RW * RWP;
 
-    extern __shared__ float4 smem_f4[];
     float *prod = reinterpret_cast<float *>(smem_f4);                // [5][RW][RWP]
     T *stage = reinterpret_cast<T *>(prod + ProdFloats<KR>::v);     // [2][SH][SP]
 
-    const IterArgs &a = prm.a[blockIdx.z];
-    const int mode = prm.mode;
     const int tid = threadIdx.x;
     const int H = a.H, W = a.W, pitch = a.pitch;
-    const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int tx0 = bx * TS, ty0 = by * TS;
     const int px0 = tx0 - KR, py0 = ty0 - KR;                      // product region origin
     const int sy0 = py0 - kBlockReach - 1;                         // staged row origin
     const int sxn = px0 - kBlockReach - 1;
@@ -282,14 +304,14 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __gr
     // V0 of the thread's next pixel is loaded one iteration ahead
     float2 V0n = make_float2(0.f, 0.f);
     if (ry < RW && py0 + ry >= 0 && py0 + ry < H && px0 + rx >= 0 && px0 + rx < W)
-        V0n = fetch_v0_rt(a, mode, px0 + rx, py0 + ry);
+        V0n = fetch_v0_rt<COH>(a, mode, px0 + rx, py0 + ry);
     for (int idx = tid; idx < RW * RW; idx += NT) {
         const int gy = py0 + ry, gx = px0 + rx;
         const float2 V0c = V0n;
         int nry = ry + DY, nrx = rx + DX;
         if (nrx >= RW) { nrx -= RW; ++nry; }
         if (idx + NT < RW * RW && py0 + nry >= 0 && py0 + nry < H && px0 + nrx >= 0 && px0 + nrx < W)
-            V0n = fetch_v0_rt(a, mode, px0 + nrx, py0 + nry);
+            V0n = fetch_v0_rt<COH>(a, mode, px0 + nrx, py0 + nry);
         float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (interior || (gx > kBlockReach && gx < W - kBlockReach - 2 && gy > kBlockReach && gy < H - kBlockReach - 2)) {
             products_interior<T, SP>(stage, stage + SH * SP, sx0, sy0, a, gx, gy, V0c, p);
@@ -343,7 +365,7 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __gr
         const float det = sxx * syy - sxy * sxy;
         float2 V;
         if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr) {
-            V = fetch_v0_rt(a, mode, gx, gy);
+            V = fetch_v0_rt<COH>(a, mode, gx, gy);
         } else {
             const float inv = __frcp_rn(det);  // one correctly rounded reciprocal, two products
             V = make_float2((syy * sxr - sxy * syr) * inv, (sxx * syr - sxy * sxr) * inv);
@@ -354,6 +376,141 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __gr
         } else {
             a.Vout[(int64_t)gy * a.vpitch + gx] = V;
         }
+    }
+}
+
+// One tile per CTA; blockIdx.z selects the pair.
+template <typename T, int KR>
+__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __grid_constant__ BlockParams prm)
+{
+    extern __shared__ float4 smem_f4[];
+    block_tile<T, KR, false>(prm.a[blockIdx.z], prm.mode, blockIdx.x, blockIdx.y, smem_f4);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched launch: many pairs of unequal size, all (level,
+// iteration) stages, in one launch.  Work units (stage, pair, tile) are
+// handed out in the order of a schedule built on the host; a unit of stage
+// s waits until every tile of stage s-1 of its pair is done (a per-(stage,
+// pair) counter).  Units are claimed in schedule order by resident CTAs, so
+// every unit a CTA waits for is held by a running CTA.  The wait is bounded
+// by an iteration count and a %globaltimer deadline; on expiry the CTA
+// records an error word and leaves, and the host reports OFV_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+struct BatchPair {
+    const void *P1[16], *P2[16];  // level images of the two frames
+    int H[16], W[16], pitch[16];
+    float2 *vb[2];                // ping-pong fields (pitch vpitch)
+    float *u, *v;                 // caller's outputs
+    int vpitch;
+};
+
+struct QueueParams {
+    const BatchPair *pairs;  // [npairs]
+    const int *group_off;    // [ngroups + 1] first unit of each (stage, pair) group
+    const int2 *group;       // [ngroups] (stage, pair)
+    int ngroups, total_units, npairs;
+    int L, IT, kr;
+    float eps_rel, eps_abs;
+    int *head;               // next unclaimed unit
+    int *done;               // [stages * npairs] finished tiles
+    int *error;              // 0, or 1 + the unit whose wait expired
+    long long timeout_ns;
+    int spin_limit;
+};
+
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int TS>
+__device__ __forceinline__ int tiles_of(int H, int W) { return ((W + TS - 1) / TS) * ((H + TS - 1) / TS); }
+
+template <typename T, int KR>
+__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __grid_constant__ QueueParams q)
+{
+    constexpr int TS = BlockShape<KR>::TS;
+    extern __shared__ float4 smem_f4[];
+    __shared__ int s_unit, s_fail;
+    const int S = q.L * q.IT;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_unit = atomicAdd(q.head, 1);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const int unit = s_unit;
+        if (unit >= q.total_units) break;
+        // (stage, pair) group of the unit: binary search in the offsets
+        int lo = 0, hi = q.ngroups - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(q.group_off + mid) <= unit) lo = mid; else hi = mid - 1;
+        }
+        const int2 sp = __ldg(q.group + lo);
+        const int s = sp.x, p = sp.y;
+        const int tile = unit - __ldg(q.group_off + lo);
+        const BatchPair &bp = q.pairs[p];
+        const int l = q.L - 1 - s / q.IT, t = s % q.IT;
+        if (s > 0 && threadIdx.x == 0) {
+            const int lp = q.L - 1 - (s - 1) / q.IT;
+            const int need = tiles_of<TS>(bp.H[lp], bp.W[lp]);
+            const int *cnt = q.done + (s - 1) * q.npairs + p;
+            const long long t0 = global_ns();
+            int spins = 0;
+            while (ld_acquire(cnt) < need) {
+                if (++spins > q.spin_limit || global_ns() - t0 > q.timeout_ns) {
+                    atomicCAS(q.error, 0, 1 + unit);
+                    s_fail = 1;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        IterArgs a = {};
+        a.P1 = bp.P1[l];
+        a.P2 = bp.P2[l];
+        a.H = bp.H[l];
+        a.W = bp.W[l];
+        a.pitch = bp.pitch[l];
+        a.vpitch = bp.vpitch;
+        a.vcpitch = bp.vpitch;
+        a.kr = q.kr;
+        a.eps_rel = q.eps_rel;
+        a.eps_abs = q.eps_abs;
+        int mode = V0_ZERO;
+        if (s > 0 && t == 0) {
+            mode = V0_UP;
+            a.Vc = bp.vb[(s - 1) & 1];
+            a.Hc = bp.H[l + 1];
+            a.Wc = bp.W[l + 1];
+        } else if (s > 0) {
+            mode = V0_SAME;
+            a.V0 = bp.vb[(s - 1) & 1];
+        }
+        if (s == S - 1) {
+            a.u_out = bp.u;
+            a.v_out = bp.v;
+        } else {
+            a.Vout = bp.vb[s & 1];
+        }
+        const int ntx = (a.W + TS - 1) / TS;
+        block_tile<T, KR, true>(a, mode, tile % ntx, tile / ntx, smem_f4);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(q.done + s * q.npairs + p, 1);
     }
 }
 

@@ -42,3 +42,66 @@ cudaError_t launch_block_f16(const BlockParams &p, int kr, int npairs, cudaStrea
 }
 
 }  // namespace ofv
+
+namespace ofv {
+
+namespace {
+size_t g_qgranted_f16[64][kBlockMaxKR + 1];
+
+template <int KR>
+cudaError_t runq_f16(const QueueParams &q, int ctas, int dev, cudaStream_t s)
+{
+    constexpr size_t smem = block_smem_bytes<__half, KR>();
+    auto kern = k_iter_queue<__half, KR>;
+    if (dev < 0 || dev >= 64 || g_qgranted_f16[dev][KR] < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) g_qgranted_f16[dev][KR] = smem;
+    }
+    kern<<<ctas, BlockShape<KR>::NT, smem, s>>>(q);
+    return cudaGetLastError();
+}
+
+template <int KR>
+int occq_f16()
+{
+    constexpr size_t smem = block_smem_bytes<__half, KR>();
+    cudaFuncSetAttribute(k_iter_queue<__half, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_iter_queue<__half, KR>, BlockShape<KR>::NT, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+}  // namespace
+
+// Persistent batched launch with ctas CTAs (at most the resident count).
+cudaError_t launch_queue_f16(const QueueParams &q, int kr, int ctas, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    switch (kr) {
+#define OFV_QUEUE_CASE(K) \
+    case K: return runq_f16<K>(q, ctas, dev, s);
+    OFV_QUEUE_CASE(1) OFV_QUEUE_CASE(2) OFV_QUEUE_CASE(3) OFV_QUEUE_CASE(4) OFV_QUEUE_CASE(5)
+    OFV_QUEUE_CASE(6) OFV_QUEUE_CASE(7) OFV_QUEUE_CASE(8) OFV_QUEUE_CASE(9) OFV_QUEUE_CASE(10)
+#undef OFV_QUEUE_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Resident CTAs per SM of the persistent kernel.
+int queue_occupancy_f16(int kr)
+{
+    switch (kr) {
+#define OFV_OCC_CASE(K) \
+    case K: return occq_f16<K>();
+    OFV_OCC_CASE(1) OFV_OCC_CASE(2) OFV_OCC_CASE(3) OFV_OCC_CASE(4) OFV_OCC_CASE(5)
+    OFV_OCC_CASE(6) OFV_OCC_CASE(7) OFV_OCC_CASE(8) OFV_OCC_CASE(9) OFV_OCC_CASE(10)
+#undef OFV_OCC_CASE
+    default: return 0;
+    }
+}
+
+
+}  // namespace ofv

@@ -1,0 +1,397 @@
+// Batched entry point: many image pairs of unequal size in one persistent
+// launch (a work queue of (stage, pair, tile) units), with an autotuner that
+// picks the unit schedule and the number of persistent CTAs per batch
+// signature.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ofv.h"
+#include "k_block.cuh"
+#include "ofv_handle.h"
+
+namespace ofv {
+cudaError_t launch_queue_f32(const QueueParams &q, int kr, int ctas, cudaStream_t s);
+cudaError_t launch_queue_f16(const QueueParams &q, int kr, int ctas, cudaStream_t s);
+cudaError_t launch_queue_bf16(const QueueParams &q, int kr, int ctas, cudaStream_t s);
+int queue_occupancy_f32(int kr);
+int queue_occupancy_f16(int kr);
+int queue_occupancy_bf16(int kr);
+int block_tile_size(int kr);
+}  // namespace ofv
+
+using namespace ofv;
+
+namespace {
+
+constexpr long long kWaitTimeoutNs = 5000000000LL;  // 5 s
+constexpr int kWaitSpinLimit = 200000000;
+
+cudaError_t launch_queue(int store, const QueueParams &q, int kr, int ctas, cudaStream_t s)
+{
+    switch (store) {
+    case OFV_STORE_F16: return launch_queue_f16(q, kr, ctas, s);
+    case OFV_STORE_BF16: return launch_queue_bf16(q, kr, ctas, s);
+    default: return launch_queue_f32(q, kr, ctas, s);
+    }
+}
+
+int queue_occupancy(int store, int kr)
+{
+    switch (store) {
+    case OFV_STORE_F16: return queue_occupancy_f16(kr);
+    case OFV_STORE_BF16: return queue_occupancy_bf16(kr);
+    default: return queue_occupancy_f32(kr);
+    }
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Unit list of one schedule: groups (stage, pair) with their first unit.
+void build_schedule(int schedule, int S, int n, const std::vector<std::vector<int>> &tiles, std::vector<int2> &group,
+                    std::vector<int> &off)
+{
+    group.clear();
+    off.assign(1, 0);
+    const int chunk = schedule > 0 ? schedule : n;
+    for (int c0 = 0; c0 < n; c0 += chunk) {
+        const int c1 = std::min(n, c0 + chunk);
+        for (int s = 0; s < S; ++s)
+            for (int p = c0; p < c1; ++p) {
+                group.push_back(make_int2(s, p));
+                off.push_back(off.back() + tiles[p][s]);
+            }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t stream)
+{
+    if (!h || !pairs) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: handle or pairs is NULL");
+    if (n < 1) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: n=%d must be >= 1", n);
+    const ofv_params &p = h->p;
+    if (p.path != OFV_PATH_FUSED || p.kernel_radius > 10)
+        return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_compute_batched: needs the fused path with KR <= 10");
+    const int L = h->L, IT = p.iterations, S = L * IT, KR = p.kernel_radius;
+    const int minsz = 2 * KR + 1 > 8 ? 2 * KR + 1 : 8;
+    const int TS = block_tile_size(KR);
+    const int sb = store_bytes(p.storage);
+    std::vector<std::vector<int>> Hs(n, std::vector<int>(L)), Ws(n, std::vector<int>(L)), tiles(n, std::vector<int>(S));
+    for (int i = 0; i < n; ++i) {
+        const ofv_pair &q = pairs[i];
+        if (!q.I1 || !q.I2 || !q.u || !q.v || q.u == q.v)
+            return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: pair %d has a NULL or aliased buffer", i);
+        if (q.H < 1 || q.W < 1 || (int64_t)q.H * q.W > 2147483647LL)
+            return fail_msg(OFV_ERR_SHAPE, "ofv_compute_batched: pair %d has H=%d W=%d", i, q.H, q.W);
+        Hs[i][0] = q.H;
+        Ws[i][0] = q.W;
+        for (int l = 1; l < L; ++l) {
+            Hs[i][l] = (Hs[i][l - 1] + 1) / 2;
+            Ws[i][l] = (Ws[i][l - 1] + 1) / 2;
+        }
+        if (Hs[i][L - 1] < minsz || Ws[i][L - 1] < minsz)
+            return fail_msg(OFV_ERR_SHAPE, "ofv_compute_batched: pair %d (%dx%d): coarsest level below %d", i, q.H,
+                            q.W, minsz);
+        for (int s = 0; s < S; ++s) {
+            const int l = L - 1 - s / IT;
+            tiles[i][s] = ((Ws[i][l] + TS - 1) / TS) * ((Hs[i][l] + TS - 1) / TS);
+        }
+    }
+    DevGuard dg(h->device);
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail_msg(e, "error pending before ofv_compute_batched");
+    }
+
+    // workspace: per pair two pyramids and two fields, then the queue data
+    std::vector<size_t> lvl_off(2 * (size_t)n * L), vb_off(2 * (size_t)n), tmp_off(2 * (size_t)n, 0);
+    std::vector<int> vpitch(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int f = 0; f < 2; ++f)
+            for (int l = 0; l < L; ++l) {
+                lvl_off[((size_t)i * 2 + f) * L + l] = off;
+                off = align_up(off + (size_t)Hs[i][l] * pitch_for(Ws[i][l]) * sb, 256);
+            }
+        vpitch[i] = pitch_for(Ws[i][0]);
+        for (int k = 0; k < 2; ++k) {
+            vb_off[2 * i + k] = off;
+            off = align_up(off + (size_t)Hs[i][0] * vpitch[i] * sizeof(float2), 256);
+        }
+        if (p.prefilter)
+            for (int f = 0; f < 2; ++f) {
+                tmp_off[2 * i + f] = off;
+                off = align_up(off + (size_t)Hs[i][0] * pitch_for(Ws[i][0]) * sizeof(float), 256);
+            }
+    }
+    const size_t pairs_off = off;
+    off = align_up(off + sizeof(BatchPair) * n, 256);
+    const size_t maxgroups = (size_t)S * n;
+    const size_t goff_off = off;
+    off = align_up(off + sizeof(int) * (maxgroups + 1), 256);
+    const size_t grp_off = off;
+    off = align_up(off + sizeof(int2) * maxgroups, 256);
+    const size_t done_off = off;
+    off = align_up(off + sizeof(int) * (maxgroups + 2), 256);  // done counters, head, error
+    if (off > h->batch_bytes) {
+        if (h->batch_arena) {
+            e = cudaStreamSynchronize(cs);
+            cudaFree(h->batch_arena);
+            h->batch_arena = nullptr;
+            h->batch_bytes = 0;
+        }
+        e = cudaMalloc(&h->batch_arena, off);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->batch_arena = nullptr;
+            return fail_msg(OFV_ERR_ALLOC, "ofv_compute_batched: cudaMalloc of %zu bytes failed", off);
+        }
+        h->batch_bytes = off;
+    }
+    char *base = static_cast<char *>(h->batch_arena);
+    auto lvl = [&](int i, int f, int l) { return (void *)(base + lvl_off[((size_t)i * 2 + f) * L + l]); };
+
+    // steps 1-2: ingest and reduce, frames of equal size together
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return Hs[a][0] != Hs[b][0] ? Hs[a][0] < Hs[b][0] : Ws[a][0] < Ws[b][0];
+    });
+    for (size_t k0 = 0; k0 < order.size();) {
+        size_t k1 = k0;
+        while (k1 < order.size() && Hs[order[k1]][0] == Hs[order[k0]][0] && Ws[order[k1]][0] == Ws[order[k0]][0]) ++k1;
+        // frames of this size class, kMaxFramesPerLaunch at a time
+        std::vector<std::pair<int, int>> fr;  // (pair, frame)
+        for (size_t k = k0; k < k1; ++k) {
+            fr.push_back({order[k], 0});
+            fr.push_back({order[k], 1});
+        }
+        for (size_t c0 = 0; c0 < fr.size(); c0 += kMaxFramesPerLaunch) {
+            const int nf = (int)std::min<size_t>(kMaxFramesPerLaunch, fr.size() - c0);
+            IngestArgs ia[kMaxFramesPerLaunch];
+            for (int k = 0; k < nf; ++k) {
+                const int i = fr[c0 + k].first, f = fr[c0 + k].second;
+                IngestArgs &a = ia[k];
+                a.raw = f ? pairs[i].I2 : pairs[i].I1;
+                a.out = lvl(i, f, 0);
+                a.tmp = p.prefilter ? reinterpret_cast<float *>(base + tmp_off[2 * i + f]) : nullptr;
+                a.w25 = h->w25;
+                a.H = Hs[i][0];
+                a.W = Ws[i][0];
+                a.pitch = pitch_for(Ws[i][0]);
+                a.in_type = p.input;
+                a.bits = p.bit_depth;
+                a.nr = p.norm_radius;
+                a.eps_n = p.norm_eps;
+                a.prefilter = p.prefilter;
+            }
+            e = launch_ingest_frames(ia, nf, p.storage, cs);
+            if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: ingest launch");
+            for (int l = 1; l < L; ++l) {
+                ReduceArgs ra[kMaxFramesPerLaunch];
+                for (int k = 0; k < nf; ++k) {
+                    const int i = fr[c0 + k].first, f = fr[c0 + k].second;
+                    ReduceArgs &r = ra[k];
+                    r.src = lvl(i, f, l - 1);
+                    r.Hs = Hs[i][l - 1];
+                    r.Ws = Ws[i][l - 1];
+                    r.spitch = pitch_for(Ws[i][l - 1]);
+                    r.dst = lvl(i, f, l);
+                    r.Hd = Hs[i][l];
+                    r.Wd = Ws[i][l];
+                    r.dpitch = pitch_for(Ws[i][l]);
+                }
+                e = launch_reduce_frames(ra, nf, p.storage, cs);
+                if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: reduce launch");
+            }
+        }
+        k0 = k1;
+    }
+
+    // pair descriptors
+    std::vector<BatchPair> bp(n);
+    for (int i = 0; i < n; ++i) {
+        BatchPair &b = bp[i];
+        memset(&b, 0, sizeof b);
+        for (int l = 0; l < L; ++l) {
+            b.P1[l] = lvl(i, 0, l);
+            b.P2[l] = lvl(i, 1, l);
+            b.H[l] = Hs[i][l];
+            b.W[l] = Ws[i][l];
+            b.pitch[l] = pitch_for(Ws[i][l]);
+        }
+        b.vb[0] = reinterpret_cast<float2 *>(base + vb_off[2 * i]);
+        b.vb[1] = reinterpret_cast<float2 *>(base + vb_off[2 * i + 1]);
+        b.u = pairs[i].u;
+        b.v = pairs[i].v;
+        b.vpitch = vpitch[i];
+    }
+    e = cudaMemcpyAsync(base + pairs_off, bp.data(), sizeof(BatchPair) * n, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading pair descriptors");
+
+    int dev = h->device, sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = std::max(1, queue_occupancy(p.storage, KR));
+
+    // batch signature for the autotuner
+    std::vector<std::pair<int, int>> sizes;
+    for (int i = 0; i < n; ++i) sizes.push_back({Hs[i][0], Ws[i][0]});
+    std::sort(sizes.begin(), sizes.end());
+    std::string key = "kr" + std::to_string(KR) + "l" + std::to_string(L) + "it" + std::to_string(IT) + "s" +
+                      std::to_string(p.storage);
+    for (auto &sz : sizes) key += ":" + std::to_string(sz.first) + "x" + std::to_string(sz.second);
+
+    std::vector<BatchTune> cands;
+    auto it = h->tune.find(key);
+    const bool tuning = it == h->tune.end();
+    if (tuning) {
+        for (int sch : {0, 8})
+            for (int c : {occ, occ - 1})
+                if (c >= 1 && (sch == 0 || sch < n)) cands.push_back(BatchTune{sch, c, 0.0});
+    } else {
+        cands.push_back(it->second);
+    }
+
+    QueueParams q;
+    memset(&q, 0, sizeof q);
+    q.pairs = reinterpret_cast<const BatchPair *>(base + pairs_off);
+    q.group_off = reinterpret_cast<const int *>(base + goff_off);
+    q.group = reinterpret_cast<const int2 *>(base + grp_off);
+    q.npairs = n;
+    q.L = L;
+    q.IT = IT;
+    q.kr = KR;
+    q.eps_rel = p.det_rel_eps;
+    q.eps_abs = p.det_abs_eps;
+    q.done = reinterpret_cast<int *>(base + done_off);
+    q.head = q.done + maxgroups;
+    q.error = q.head + 1;
+    q.timeout_ns = kWaitTimeoutNs;
+    q.spin_limit = kWaitSpinLimit;
+
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (tuning) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+    }
+    std::vector<int2> group;
+    std::vector<int> goff;
+    int best = 0;
+    for (size_t c = 0; c < cands.size(); ++c) {
+        build_schedule(cands[c].schedule, S, n, tiles, group, goff);
+        q.ngroups = (int)group.size();
+        q.total_units = goff.back();
+        e = cudaMemcpyAsync(base + goff_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + grp_off, group.data(), sizeof(int2) * group.size(), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(q.done, 0, sizeof(int) * (maxgroups + 2), cs);
+        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading the schedule");
+        const int ctas = std::min(sms * cands[c].ctas_per_sm, std::max(1, q.total_units));
+        if (tuning) cudaEventRecord(e0, cs);
+        e = launch_queue(p.storage, q, KR, ctas, cs);
+        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: persistent launch");
+        if (tuning) {
+            cudaEventRecord(e1, cs);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cands[c].ms = ms;
+            if (ms < cands[best].ms) best = (int)c;
+        }
+        int err = 0;
+        e = cudaMemcpyAsync(&err, q.error, sizeof(int), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: completing the batch");
+        if (err != 0)
+            return fail_msg(OFV_ERR_TIMEOUT, "ofv_compute_batched: a dependency wait of work unit %d expired", err - 1);
+    }
+    if (tuning) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->tune[key] = cands[best];
+        // the last candidate's outputs are already in place (all compute the same fields)
+    }
+    h->last_tune = tuning ? cands[best] : cands[0];
+    h->last_tuned = tuning ? 1 : 0;
+    return OFV_OK;
+}
+
+ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm, double *ms, int *tuned)
+{
+    if (!h || !schedule || !ctas_per_sm || !ms || !tuned) return fail_msg(OFV_ERR_INVALID_ARG, "NULL argument");
+    *schedule = h->last_tune.schedule;
+    *ctas_per_sm = h->last_tune.ctas_per_sm;
+    *ms = h->last_tune.ms;
+    *tuned = h->last_tuned;
+    return OFV_OK;
+}
+
+// A persistent launch whose one work unit waits on a counter that nothing
+// increments; the wait must expire after about timeout_us and leave the
+// error word set (1 + the unit) for the host, without a fault or a hang.
+ofv_status ofv_queue_selftest(int timeout_us, int *error_word)
+{
+    if (!error_word || timeout_us < 1 || timeout_us > 10000000)
+        return fail_msg(OFV_ERR_INVALID_ARG, "ofv_queue_selftest: bad arguments");
+    *error_word = 0;
+    void *mem = nullptr;
+    const size_t bytes = 4096;
+    cudaError_t e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_queue_selftest: cudaMalloc");
+    char *b = static_cast<char *>(mem);
+    BatchPair bp;
+    memset(&bp, 0, sizeof bp);
+    bp.H[0] = bp.W[0] = bp.H[1] = bp.W[1] = 8;
+    const int goff[2] = {0, 1};
+    const int2 grp = make_int2(1, 0);  // stage 1 of pair 0: waits for stage 0, which has no units
+    e = cudaMemcpy(b, &bp, sizeof bp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + 2048, goff, sizeof goff, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + 2112, &grp, sizeof grp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b + 3072, 0, 64);
+    QueueParams q;
+    memset(&q, 0, sizeof q);
+    q.pairs = reinterpret_cast<const BatchPair *>(b);
+    q.group_off = reinterpret_cast<const int *>(b + 2048);
+    q.group = reinterpret_cast<const int2 *>(b + 2112);
+    q.ngroups = 1;
+    q.total_units = 1;
+    q.npairs = 1;
+    q.L = 2;
+    q.IT = 1;
+    q.kr = 4;
+    q.done = reinterpret_cast<int *>(b + 3072);
+    q.head = q.done + 4;
+    q.error = q.done + 5;
+    q.timeout_ns = (long long)timeout_us * 1000;
+    q.spin_limit = kWaitSpinLimit;
+    if (e == cudaSuccess) e = launch_queue(OFV_STORE_F32, q, 4, 1, nullptr);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, q.error, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_queue_selftest");
+    *error_word = err;
+    return err ? fail_msg(OFV_ERR_TIMEOUT, "ofv_queue_selftest: wait expired as intended (unit %d)", err - 1)
+               : OFV_OK;
+}
+
+}  // extern "C"

@@ -17,6 +17,7 @@
 
 #include "../../include/ofv.h"
 #include "ofv_common.cuh"
+#include "ofv_handle.h"
 
 using namespace ofv;
 
@@ -38,50 +39,7 @@ ofv_status cuda_fail(cudaError_t e, const char *where)
     return fail(OFV_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
-constexpr int kMaxLevels = 16;
-constexpr int kMaxBatch = kMaxPairsPerLaunch;
-constexpr int kMaxSlots = kMaxBatch + 1;
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-int store_bytes(int st) { return st == OFV_STORE_F32 ? 4 : 2; }
-int input_bytes(int in) { return in == OFV_IN_U8 ? 1 : (in == OFV_IN_U16 ? 2 : 4); }
-
-struct ProfRec {
-    int cls;
-    cudaEvent_t e0, e1;
-    double bytes;
-};
-
 }  // namespace
-
-struct ofv_handle {
-    int H, W;
-    ofv_params p;
-    int L;
-    int B;       // pairs per launch in sequences
-    int nslots;  // pyramid slots (B + 1)
-    int Hs[kMaxLevels], Ws[kMaxLevels], pitch[kMaxLevels];
-    int vpitch;
-    int device;
-    void *arena;
-    size_t arena_bytes;
-    void *lvl[kMaxSlots][kMaxLevels];
-    float2 *vbuf[2 * kMaxBatch];  // two ping-pong fields per pair
-    float *w25;
-    float *tmp[kMaxSlots];        // pre-filter input, one per frame of an ingest launch
-    PlainBufs plain;
-    // host-pointer entry point staging (allocated on first use)
-    void *stage;
-    size_t stage_bytes;
-    // slots of I1 and I2 of the last computed pair
-    int last_s1, last_s2;
-    // kernel timing
-    bool prof;
-    std::vector<ProfRec> recs;
-    std::vector<cudaEvent_t> pool;
-    size_t pool_next;
-};
 
 namespace {
 
@@ -306,6 +264,17 @@ ofv_status pending_error(const char *where)
 namespace ofv {
 // Record a failure message for ofv_last_error() from another translation unit.
 void set_error_message(const char *msg) { fail(OFV_OK, "%s", msg); }
+
+ofv_status fail_msg(ofv_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+ofv_status cuda_fail_msg(cudaError_t e, const char *where) { return cuda_fail(e, where); }
 }  // namespace ofv
 
 extern "C" {
@@ -449,6 +418,7 @@ ofv_status ofv_destroy(ofv_handle *h)
     if (e != cudaSuccess) st = cuda_fail(e, "synchronising before destroy");
     for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
     if (h->stage) cudaFree(h->stage);
+    if (h->batch_arena) cudaFree(h->batch_arena);
     if (h->arena) cudaFree(h->arena);
     delete h;
     return st;
@@ -565,6 +535,86 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
         h->last_s1 = s1[np - 1];
         h->last_s2 = s2[np - 1];
     }
+    return OFV_OK;
+}
+
+}  // extern "C"
+
+struct ofv_graph {
+    ofv_handle *h;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float *u, float *v, ofv_graph **out)
+{
+    if (!out) return fail(OFV_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!h || !I1 || !I2 || !u || !v || u == v)
+        return fail(OFV_ERR_INVALID_ARG, "handle, I1, I2, u, v must be non-NULL and u != v");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "creating the capture stream");
+    const bool prof = h->prof;
+    h->prof = false;
+    // one eager run sets kernel attributes outside the capture
+    ofv_status st = ofv_compute(h, I1, I2, u, v, (ofv_stream_t)cs);
+    if (st == OFV_OK) {
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "warm-up run before capture");
+    }
+    cudaGraph_t graph = nullptr;
+    if (st == OFV_OK) {
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "beginning stream capture");
+        } else {
+            st = ofv_compute(h, I1, I2, u, v, (ofv_stream_t)cs);
+            e = cudaStreamEndCapture(cs, &graph);
+            if (st == OFV_OK && e != cudaSuccess) st = cuda_fail(e, "ending stream capture");
+        }
+    }
+    h->prof = prof;
+    cudaGraphExec_t exec = nullptr;
+    if (st == OFV_OK) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "instantiating the graph");
+    }
+    cudaStreamDestroy(cs);
+    if (st != OFV_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    ofv_graph *gr = new (std::nothrow) ofv_graph{h, graph, exec};
+    if (!gr) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(OFV_ERR_ALLOC, "host allocation of the graph handle failed");
+    }
+    *out = gr;
+    return OFV_OK;
+}
+
+ofv_status ofv_graph_launch(ofv_graph *g, ofv_stream_t s)
+{
+    if (!g) return fail(OFV_ERR_INVALID_ARG, "graph is NULL");
+    DeviceGuard dg(g->h->device);
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the graph");
+    return OFV_OK;
+}
+
+ofv_status ofv_graph_destroy(ofv_graph *g)
+{
+    if (!g) return OFV_OK;
+    DeviceGuard dg(g->h->device);
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
     return OFV_OK;
 }
 

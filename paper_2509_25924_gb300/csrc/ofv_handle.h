@@ -1,0 +1,74 @@
+// The handle behind the C ABI (private to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ofv.h"
+#include "ofv_common.cuh"
+
+namespace ofv {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxBatch = kMaxPairsPerLaunch;
+constexpr int kMaxSlots = kMaxBatch + 1;
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double bytes;
+};
+
+// Configuration the batched entry point's autotuner picked for one batch
+// signature (sizes and parameters).
+struct BatchTune {
+    int schedule;     // 0: stage-major over all pairs, else pairs in groups of this many
+    int ctas_per_sm;  // persistent CTAs per SM
+    double ms;        // measured duration of the persistent launch
+};
+
+// Record a failure for ofv_last_error() (thread-local) and return st.
+ofv_status fail_msg(ofv_status st, const char *fmt, ...);
+ofv_status cuda_fail_msg(cudaError_t e, const char *where);
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int store_bytes(int st) { return st == OFV_STORE_F32 ? 4 : 2; }
+inline int input_bytes(int in) { return in == OFV_IN_U8 ? 1 : (in == OFV_IN_U16 ? 2 : 4); }
+
+}  // namespace ofv
+
+struct ofv_handle {
+    int H, W;
+    ofv_params p;
+    int L;
+    int B;       // pairs per launch in sequences
+    int nslots;  // pyramid slots (B + 1)
+    int Hs[ofv::kMaxLevels], Ws[ofv::kMaxLevels], pitch[ofv::kMaxLevels];
+    int vpitch;
+    int device;
+    void *arena;
+    size_t arena_bytes;
+    void *lvl[ofv::kMaxSlots][ofv::kMaxLevels];
+    float2 *vbuf[2 * ofv::kMaxBatch];  // two ping-pong fields per pair
+    float *w25;
+    float *tmp[ofv::kMaxSlots];        // pre-filter input, one per frame of an ingest launch
+    ofv::PlainBufs plain;
+    // host-pointer entry point staging (allocated on first use)
+    void *stage;
+    size_t stage_bytes;
+    // slots of I1 and I2 of the last computed pair
+    int last_s1, last_s2;
+    // kernel timing
+    bool prof;
+    std::vector<ofv::ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_next;
+    // batched entry point: grow-only workspace and autotuner cache
+    void *batch_arena;
+    size_t batch_bytes;
+    std::map<std::string, ofv::BatchTune> tune;
+    ofv::BatchTune last_tune;
+    int last_tuned;  // 1 if the last batched call ran the autotuner
+};

@@ -118,3 +118,11 @@ def test_oracle_and_cuda_path_share_no_code():
         text = open(f).read()
         assert not re.search(r"\boracle\b", text.replace("oracle-free", "")), f
         assert "ofv_oracle" not in text, f
+
+
+def test_batched_rejects_bad_arguments_on_the_host():
+    p = ofv.ofv_default_params()
+    lib = ctypes.CDLL(ofv.lib_path)
+    lib.ofv_compute_batched.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.ofv_compute_batched.restype = ctypes.c_int
+    assert lib.ofv_compute_batched(None, 1, None, None) == ofv.OFV_ERR_INVALID_ARG

@@ -308,6 +308,34 @@ def test_sequence_equals_pairwise_and_host_entry_point(path, batch):
         ofv.ofv_destroy(h)
 
 
+def test_graph_replay_matches_compute_and_follows_new_frames():
+    """A captured graph replays the whole pipeline on whatever the fixed input
+    buffers hold at launch time (the live-loop pattern)."""
+    F = synth.stream_frames(256, 320, 4, seed=8)
+    H, W = 256, 320
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(**PARAMS))
+    g = None
+    try:
+        b1 = torch.from_numpy(F[0]).to(DEV)
+        b2 = torch.from_numpy(F[1]).to(DEV)
+        u = torch.empty((H, W), device=DEV); v = torch.empty_like(u)
+        g = ofv.ofv_graph_create(h, b1, b2, u, v)
+        ru = torch.empty_like(u); rv = torch.empty_like(u)
+        for k in range(3):
+            b1.copy_(torch.from_numpy(F[k]).to(DEV))
+            b2.copy_(torch.from_numpy(F[k + 1]).to(DEV))
+            ofv.ofv_graph_launch(g)
+            torch.cuda.synchronize()
+            f1 = torch.from_numpy(F[k]).to(DEV); f2 = torch.from_numpy(F[k + 1]).to(DEV)
+            ofv.ofv_compute(h, f1, f2, ru, rv)
+            torch.cuda.synchronize()
+            assert torch.equal(u, ru) and torch.equal(v, rv)
+    finally:
+        if g:
+            ofv.ofv_graph_destroy(g)
+        ofv.ofv_destroy(h)
+
+
 def test_profile_counts_launches_and_bytes():
     I1, I2, _, _ = synth.rankine_pair()
     p = ofv.ofv_default_params(input=ofv.OFV_IN_F32, **PARAMS)
@@ -353,3 +381,61 @@ def test_full_21mp_wake_fp32():
     u, v = gpu_flow(I1, I2, **PARAMS)
     ou, ov, nd, _ = oracle_flow(I1, I2)
     compare(u, v, ou, ov, nd, label="21Mp wake fp32", max_masked=0.05)
+
+
+# --------------------------------------------------------------------------
+# many pairs of unequal size in one persistent launch
+# --------------------------------------------------------------------------
+def _uneven_pairs(sizes, seed0=100):
+    out = []
+    for k, (H, W) in enumerate(sizes):
+        I1, I2, _, _ = synth.turbulence_pair(H, W, seed=seed0 + k)
+        out.append((I1, I2))
+    return out
+
+
+@pytest.mark.parametrize("storage", [ofv.OFV_STORE_F32, ofv.OFV_STORE_F16])
+def test_batched_uneven_sizes_match_per_pair_compute_and_oracle(storage):
+    sizes = [(256, 256), (512, 512), (192, 320), (256, 256), (384, 512), (512, 512), (200, 232), (256, 384),
+             (512, 256), (96, 640)]
+    data = _uneven_pairs(sizes)
+    p = ofv.ofv_default_params(storage=storage, **PARAMS)
+    h = ofv.ofv_create(64, 64, p)
+    try:
+        dev_pairs, refs = [], []
+        for (I1, I2), (H, W) in zip(data, sizes):
+            t1 = torch.from_numpy(I1).to(DEV); t2 = torch.from_numpy(I2).to(DEV)
+            u = torch.full((H, W), float("nan"), device=DEV); v = torch.full((H, W), float("nan"), device=DEV)
+            dev_pairs.append((t1, t2, u, v))
+        ofv.ofv_compute_batched(h, dev_pairs)
+        tun = ofv.ofv_batch_tuning(h)
+        assert tun["tuned"] and tun["ms"] > 0
+        for (t1, t2, u, v), (H, W) in zip(dev_pairs, sizes):
+            hh = ofv.ofv_create(H, W, p)
+            ru = torch.empty((H, W), device=DEV); rv = torch.empty_like(ru)
+            ofv.ofv_compute(hh, t1, t2, ru, rv)
+            torch.cuda.synchronize()
+            ofv.ofv_destroy(hh)
+            assert torch.equal(u, ru) and torch.equal(v, rv), f"{H}x{W}"
+        # second batch of the same signature reuses the tuned configuration
+        for _, _, u, v in dev_pairs:
+            u.fill_(float("nan")); v.fill_(float("nan"))
+        ofv.ofv_compute_batched(h, dev_pairs)
+        assert not ofv.ofv_batch_tuning(h)["tuned"]
+        for (I1, I2), (t1, t2, u, v) in list(zip(data, dev_pairs))[:3]:
+            ou, ov, nd, _ = oracle_flow(I1, I2)
+            kw = dict(rms_tol=REDUCED_RMS_TOL) if storage != ofv.OFV_STORE_F32 else {}
+            compare(u.cpu().numpy(), v.cpu().numpy(), ou, ov, nd, label=f"batched {I1.shape}", **kw)
+    finally:
+        ofv.ofv_destroy(h)
+
+
+def test_batched_wait_timeout_is_reported_and_device_stays_usable():
+    """The persistent launch's dependency wait is bounded: a unit that waits
+    on a counter nothing increments gives up after the time limit, records
+    the error word, and the context keeps working."""
+    st, word = ofv.ofv_queue_selftest(2000)
+    assert st == ofv.OFV_ERR_TIMEOUT and word == 1
+    I1, I2, _, _ = synth.rankine_pair(128, 128, seed=2)
+    u, v = gpu_flow(I1, I2, **PARAMS)
+    assert np.isfinite(u).all() and np.isfinite(v).all()
