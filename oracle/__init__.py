@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ofv_oracle.c")
+_SRC_ADJ = os.path.join(_HERE, "ofv_oracle_adjoint.c")
 _HDR = os.path.join(_HERE, "ofv_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
@@ -34,10 +35,10 @@ EPS_N = 1e-2
 def build(force: bool = False) -> str:
     """Compile liboracle.so beside its source (gcc, OpenMP over rows,
     no floating-point contraction so results match across hosts)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_ADJ), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+               _SRC, _SRC_ADJ, "-o", _LIB_PATH + ".tmp", "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
     return _LIB_PATH
@@ -77,6 +78,8 @@ def _load():
             lib.orc_pyramid.restype = I
             lib.orc_flow.argtypes = [I, I, P, P, ctypes.POINTER(_Params), P, P, P, P]
             lib.orc_flow.restype = I
+            lib.orc_flow_grad.argtypes = [I, I, P, P, ctypes.POINTER(_Params), P, P, P, P, P, P, P]
+            lib.orc_flow_grad.restype = I
             _lib = lib
     return _lib
 
@@ -245,3 +248,19 @@ def flow(I1, I2, params: Params | None = None, diagnostics: bool = False):
     if diagnostics:
         return u, v, nd, g
     return u, v
+
+
+def flow_grad(I1, I2, params: Params, gu, gv):
+    """Reverse mode: for a loss L with dL/du = gu and dL/dv = gv, returns
+    (dL/dI1, dL/dI2, dL/dw25 or None, u, v).  NR must be 0."""
+    a, b = _f64(I1), _f64(I2)
+    gu, gv = _f64(gu), _f64(gv)
+    H, W = a.shape
+    g1 = np.empty((H, W)); g2 = np.empty((H, W)); u = np.empty((H, W)); v = np.empty((H, W))
+    gw = np.zeros(25)
+    c = params.c()
+    rc = _load().orc_flow_grad(H, W, _p(a), _p(b), ctypes.byref(c), _p(gu), _p(gv), _p(g1), _p(g2), _p(gw),
+                               _p(u), _p(v))
+    if rc:
+        raise RuntimeError(f"orc_flow_grad failed ({rc})")
+    return g1, g2, (gw.reshape(5, 5) if params.prefilter is not None else None), u, v

@@ -42,6 +42,10 @@ int orc_ingest(int H, int W, const double *raw, const orc_params *p, double *out
 int orc_pyramid(int H, int W, const double *raw, const orc_params *p, double *out);
 int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_params *p,
              double *u, double *v, double *ndet, unsigned char *guard0);
+/* reverse mode (ofv_oracle_adjoint.c): gw25 accumulates (zero it first) */
+int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const orc_params *p,
+                  const double *gu, const double *gv, double *g1, double *g2, double *gw25,
+                  double *u, double *v);
 
 #ifdef __cplusplus
 }
