@@ -482,8 +482,35 @@ def batched_uneven(ofv, torch, synth, dev, stream, n_pairs=64, reps=5):
     finally:
         for hh in handles.values():
             ofv.ofv_destroy(hh)
+    # reverse mode on the same pairs: dL/dI1, dL/dI2 and dL/dw of the 5x5
+    # pre-filter for random dL/du, dL/dv (forward recomputed inside)
+    bh = {c: ofv.ofv_create(*classes[c], ofv.ofv_default_params(prefilter=1)) for c in content}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    grads = {}
+    for c in content:
+        shp = classes[c]
+        grads[c] = (torch.randn(shp, device=dev, generator=gen), torch.randn(shp, device=dev, generator=gen),
+                    torch.empty(shp, device=dev), torch.empty(shp, device=dev), torch.empty(25, device=dev))
+    torch.cuda.synchronize()
+    try:
+        def bwd():
+            for c, p in zip(pick.tolist(), pairs):
+                gu, gv, g1, g2, gw = grads[c]
+                ofv.ofv_backward(bh[c], p[0], p[1], gu, gv, g1, g2, gw, stream)
+        bwd()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            bwd()
+        torch.cuda.synchronize()
+        backward = n_pairs * reps / (time.perf_counter() - t0)
+    finally:
+        for hh in bh.values():
+            ofv.ofv_destroy(hh)
     return {"pairs": n_pairs, "mpix_per_batch": mpix, "batched_fields_per_s": batched,
             "batched_mvectors_per_s": batched * mpix / n_pairs, "sequential_fields_per_s": sequential,
+            "backward_pairs_per_s": backward, "backward_mvectors_per_s": backward * mpix / n_pairs,
             "tuning": tune, "timing": "host wall clock over 5 batches (the batched call synchronises)"}
 
 

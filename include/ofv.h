@@ -134,6 +134,28 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
                                 size_t frame_stride_bytes, float *u, float *v, size_t field_stride,
                                 ofv_stream_t s);
 
+/* ---- reverse mode -------------------------------------------------------
+ * The paper defines no derivative; this is the chain rule through the steps
+ * of Sec. 2 (Eq. 2 and its Gauss-Newton linearisation, the pyramid, the
+ * up-sampling) in reverse order, for training a pre-filter or chaining the
+ * estimator inside a differentiable model.
+ *
+ * Given a loss L(u, v) and its gradients gu = dL/du, gv = dL/dv (H x W
+ * float, device), writes gI1 = dL/dI1 and gI2 = dL/dI2 (H x W float, device,
+ * gradients with respect to the raw input values) and, when gw25 is not
+ * NULL, gw25 = dL/dw (25 floats, device, row-major 5x5 pre-filter weights;
+ * zeros when params.prefilter = 0).  The forward pass is recomputed from I1
+ * and I2 with the fused kernels and each stage's fields are kept in a
+ * handle-owned workspace (grown on demand: one float2 field per stage at its
+ * level's size plus about 17 float planes of the level-0 size).  A pixel whose 2x2
+ * system was guarded keeps V0, so its gradient passes to V0 unchanged; at a
+ * bilinear cell boundary the derivative is that of the cell floor() picks.
+ * Float atomics scatter the gradients, so the last bits vary between runs.
+ * The handle's pyramid slots are overwritten (as by ofv_compute).
+ * OFV_ERR_UNSUPPORTED when local normalization is on (NR > 0). */
+ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2, const float *gu,
+                        const float *gv, float *gI1, float *gI2, float *gw25, ofv_stream_t s);
+
 /* ---- allocation-free variant -------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot call cudaMalloc: code that records work into a CUDA graph by stream

@@ -18,7 +18,8 @@ from . import build as _build
 
 __all__ = [
     "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter",
-    "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_level_shape",
+    "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_backward",
+    "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
     "Flow", "lib_path", "EXPORTED_SYMBOLS",
@@ -34,7 +35,8 @@ OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 EXPORTED_SYMBOLS = [
     "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_compute",
     "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_graph_create", "ofv_graph_launch",
-    "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_level_shape",
+    "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
+    "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
 ]
@@ -77,6 +79,7 @@ def _load_library():
         "ofv_batch_tuning": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(I)], I),
         "ofv_queue_selftest": ([I, ctypes.POINTER(I)], I),
+        "ofv_backward": ([P, P, P, P, P, P, P, P, P], I),
         "ofv_level_shape": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "ofv_read_level": ([P, I, I, P, P], I),
         "ofv_profile_enable": ([P, I], I),
@@ -173,6 +176,13 @@ def ofv_compute_noalloc(H: int, W: int, params: Params, w25, I1, I2, u, v, strea
     array (OFV_NOALLOC_SCRATCH_BYTES).  See include/ofv.h for its limits."""
     _check(_lib.ofv_compute_noalloc(H, W, ctypes.byref(params), _addr(w25), _addr(I1), _addr(I2), _addr(u),
                                     _addr(v), _stream(stream)), "ofv_compute_noalloc")
+
+
+def ofv_backward(h: int, I1, I2, gu, gv, gI1, gI2, gw25=None, stream=None):
+    """Reverse mode: gI1, gI2 (H x W float32) and gw25 (25 float32, or None)
+    receive dL/dI1, dL/dI2, dL/dw for dL/du = gu, dL/dv = gv."""
+    _check(_lib.ofv_backward(h, _addr(I1), _addr(I2), _addr(gu), _addr(gv), _addr(gI1), _addr(gI2), _addr(gw25),
+                             _stream(stream)), "ofv_backward")
 
 
 class Pair(ctypes.Structure):

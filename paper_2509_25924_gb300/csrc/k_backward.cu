@@ -1,0 +1,581 @@
+// Adjoint (reverse mode) of the estimator: gradients of a loss with respect
+// to both input frames and the 5x5 pre-filter weights, given dL/du, dL/dv.
+// The paper has no adjoint; this is the chain rule through the steps of
+// Sec. 2 in reverse order.  Per Gauss-Newton stage (level l, iteration t):
+//   forward again: products at every pixel, window sums S;
+//   solve:   V = H^-1 b  =>  lambda = H^-1 gV, gH = -lambda V^T, gb = lambda
+//            (a guarded pixel, V = V0, passes gV to V0 unchanged);
+//   sums:    the adjoint of a truncated box sum is the same box sum;
+//   products, residual r = G.V0 - It, G = (g1 + g2)/2, It = B - A:
+//            gradients of the five products to G, r, and on to the samples;
+//   samples: bilinear samples of the level images and of their central
+//            differences at p1 = k - V0/2, p2 = k + V0/2: scatter to the image
+//            taps (atomics) and differentiate with respect to the position,
+//            which gives the gradient of V0 (clamped taps: zero slope beyond
+//            the border);
+//   then the up-sampling (scatter to the coarse field), the pyramid
+//   reductions (scatter) and the pre-filter (transpose and weight
+//   gradient).  Float atomics make the summation order, and so the last bits,
+//   vary from run to run.
+#include <cstring>
+
+#include "iter_math.cuh"
+#include "ofv_handle.h"
+
+namespace ofv {
+
+struct Planes5 {
+    float *p[5];
+    int pitch;  // elements
+};
+
+// V0 of a stage written as a plane: zero, same (copy of the previous stage
+// output) or the x2 up-sampled coarse field.
+__global__ void k_bw_v0(IterArgs a, int mode, float2 *out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    float2 v = make_float2(0.f, 0.f);
+    if (mode == V0_SAME) v = fetch_v0<V0_SAME>(a, x, y);
+    else if (mode == V0_UP) v = fetch_v0<V0_UP>(a, x, y);
+    out[(int64_t)y * a.vpitch + x] = v;
+}
+
+// Forward products of a stage (V0 from a.V0, pitch a.vpitch).
+template <typename T>
+__global__ void k_bw_products(IterArgs a, Planes5 out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    float p[5];
+    pixel_products<T>(a, x, y, fetch_v0<V0_SAME>(a, x, y), p);
+    const int64_t o = (int64_t)y * out.pitch + x;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out.p[c][o] = p[c];
+}
+
+// Truncated box sums along rows (dir 0) or columns (dir 1), five planes.
+__global__ void k_bw_box(Planes5 in, Planes5 out, int H, int W, int kr, int dir)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const int64_t o = (int64_t)y * in.pitch + x;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        float s = 0.f;
+        if (dir == 0) {
+            const int j0 = max(x - kr, 0), j1 = min(x + kr, W - 1);
+            const float *row = in.p[c] + (int64_t)y * in.pitch;
+            for (int j = j0; j <= j1; ++j) s += row[j];
+        } else {
+            const int i0 = max(y - kr, 0), i1 = min(y + kr, H - 1);
+            for (int i = i0; i <= i1; ++i) s += in.p[c][(int64_t)i * in.pitch + x];
+        }
+        out.p[c][o] = s;
+    }
+}
+
+// Adjoint of the guarded 2x2 solve.  S holds the window sums; gV the
+// gradient of the stage output (pitch vpitch).  Writes gS (five planes) and
+// the direct part of the gradient of V0 (guarded pixels) into gV0.
+__global__ void k_bw_solve(Planes5 S, const float2 *gV, int vpitch, int H, int W, float eps_rel, float eps_abs,
+                           Planes5 gS, float2 *gV0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const int64_t o = (int64_t)y * S.pitch + x;
+    const int64_t ov = (int64_t)y * vpitch + x;
+    const float a = S.p[0][o], b = S.p[1][o], c = S.p[2][o], sxr = S.p[3][o], syr = S.p[4][o];
+    const float tr = a + c, det = a * c - b * b;
+    const float2 g = gV[ov];
+    float r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float2 direct = make_float2(0.f, 0.f);
+    if (!(tr > eps_abs) || det <= eps_rel * tr * tr) {
+        direct = g;
+    } else {
+        const float inv = 1.f / det;
+        const float Vx = (c * sxr - b * syr) * inv, Vy = (a * syr - b * sxr) * inv;
+        const float lx = (c * g.x - b * g.y) * inv, ly = (a * g.y - b * g.x) * inv;
+        r[0] = -lx * Vx;
+        r[1] = -(lx * Vy + ly * Vx);
+        r[2] = -ly * Vy;
+        r[3] = lx;
+        r[4] = ly;
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) gS.p[k][o] = r[k];
+    gV0[ov] = direct;
+}
+
+template <typename T>
+__device__ __forceinline__ float ldp(const T *P, int pitch, int y, int x) { return ld_store(P + (int64_t)y * pitch + x); }
+
+// Value, gradient and position derivatives of one bilinear sample at
+// (x + dx, y + dy) with clamp-to-edge taps, and the scatter of (gval, ggx,
+// ggy) into the image gradient gP (dense pitch gpitch).  Returns through
+// dpx, dpy the derivative of gval*val + ggx*gx + ggy*gy w.r.t. the position.
+template <typename T>
+__device__ void sample_adj(const T *P, int H, int W, int pitch, int x, int y, float dx, float dy, float gval, float ggx,
+                           float ggy, float *gP, int gpitch, float &dpx, float &dpy)
+{
+    const float lim_x = (float)(W + 4), lim_y = (float)(H + 4);
+    dx = fminf(fmaxf(dx, -lim_x), lim_x);
+    dy = fminf(fmaxf(dy, -lim_y), lim_y);
+    const float flx = floorf(dx), fly = floorf(dy);
+    const float fx = dx - flx, fy = dy - fly;
+    const int x0 = x + (int)flx, y0 = y + (int)fly;
+    const int xa = clampi(x0, 0, W - 1), xb = clampi(x0 + 1, 0, W - 1);
+    const int ya = clampi(y0, 0, H - 1), yb = clampi(y0 + 1, 0, H - 1);
+    const int xam = clampi(xa - 1, 0, W - 1), xap = clampi(xa + 1, 0, W - 1);
+    const int xbm = clampi(xb - 1, 0, W - 1), xbp = clampi(xb + 1, 0, W - 1);
+    const int yam = clampi(ya - 1, 0, H - 1), yap = clampi(ya + 1, 0, H - 1);
+    const int ybm = clampi(yb - 1, 0, H - 1), ybp = clampi(yb + 1, 0, H - 1);
+    const float p00 = ldp(P, pitch, ya, xa), p01 = ldp(P, pitch, ya, xb);
+    const float p10 = ldp(P, pitch, yb, xa), p11 = ldp(P, pitch, yb, xb);
+    const float dx00 = 0.5f * (ldp(P, pitch, ya, xap) - ldp(P, pitch, ya, xam));
+    const float dx01 = 0.5f * (ldp(P, pitch, ya, xbp) - ldp(P, pitch, ya, xbm));
+    const float dx10 = 0.5f * (ldp(P, pitch, yb, xap) - ldp(P, pitch, yb, xam));
+    const float dx11 = 0.5f * (ldp(P, pitch, yb, xbp) - ldp(P, pitch, yb, xbm));
+    const float dy00 = 0.5f * (ldp(P, pitch, yap, xa) - ldp(P, pitch, yam, xa));
+    const float dy01 = 0.5f * (ldp(P, pitch, yap, xb) - ldp(P, pitch, yam, xb));
+    const float dy10 = 0.5f * (ldp(P, pitch, ybp, xa) - ldp(P, pitch, ybm, xa));
+    const float dy11 = 0.5f * (ldp(P, pitch, ybp, xb) - ldp(P, pitch, ybm, xb));
+    const float wx0 = 1.f - fx, wy0 = 1.f - fy;
+    auto ddx = [&](float q00, float q01, float q10, float q11) { return wy0 * (q01 - q00) + fy * (q11 - q10); };
+    auto ddy = [&](float q00, float q01, float q10, float q11) {
+        return (wx0 * q10 + fx * q11) - (wx0 * q00 + fx * q01);
+    };
+    dpx = gval * ddx(p00, p01, p10, p11) + ggx * ddx(dx00, dx01, dx10, dx11) + ggy * ddx(dy00, dy01, dy10, dy11);
+    dpy = gval * ddy(p00, p01, p10, p11) + ggx * ddy(dx00, dx01, dx10, dx11) + ggy * ddy(dy00, dy01, dy10, dy11);
+    const float w[4] = {wx0 * wy0, fx * wy0, wx0 * fy, fx * fy};
+    const int ty[4] = {ya, ya, yb, yb}, tx[4] = {xa, xb, xa, xb};
+    const int txm[4] = {xam, xbm, xam, xbm}, txp[4] = {xap, xbp, xap, xbp};
+    const int tym[4] = {yam, yam, ybm, ybm}, typ[4] = {yap, yap, ybp, ybp};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (gval != 0.f) atomicAdd(gP + (int64_t)ty[k] * gpitch + tx[k], gval * w[k]);
+        const float gdx = 0.5f * ggx * w[k], gdy = 0.5f * ggy * w[k];
+        if (gdx != 0.f) {
+            atomicAdd(gP + (int64_t)ty[k] * gpitch + txp[k], gdx);
+            atomicAdd(gP + (int64_t)ty[k] * gpitch + txm[k], -gdx);
+        }
+        if (gdy != 0.f) {
+            atomicAdd(gP + (int64_t)typ[k] * gpitch + tx[k], gdy);
+            atomicAdd(gP + (int64_t)tym[k] * gpitch + tx[k], -gdy);
+        }
+    }
+}
+
+// Adjoint of the products, the residual, the averaged gradient and the two
+// warped samples at every pixel k; adds into gV0 and the level-image
+// gradients gP1, gP2 (dense, pitch gpitch).
+template <typename T>
+__global__ void k_bw_samples(IterArgs a, Planes5 gprod, float2 *gV0, float *gP1, float *gP2, int gpitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const T *P1 = static_cast<const T *>(a.P1);
+    const T *P2 = static_cast<const T *>(a.P2);
+    const float2 V0 = fetch_v0<V0_SAME>(a, x, y);
+    const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
+    const Sample s1 = sample_level(P1, a.H, a.W, a.pitch, x, y, -hx, -hy);
+    const Sample s2 = sample_level(P2, a.H, a.W, a.pitch, x, y, hx, hy);
+    const float Gx = 0.5f * (s1.gx + s2.gx), Gy = 0.5f * (s1.gy + s2.gy);
+    const float It = s2.val - s1.val;
+    const float r = Gx * V0.x + Gy * V0.y - It;
+    const int64_t o = (int64_t)y * gprod.pitch + x;
+    const float q0 = gprod.p[0][o], q1 = gprod.p[1][o], q2 = gprod.p[2][o], q3 = gprod.p[3][o], q4 = gprod.p[4][o];
+    const float gr = Gx * q3 + Gy * q4;
+    const float gGx = 2.f * Gx * q0 + Gy * q1 + r * q3 + V0.x * gr;
+    const float gGy = Gx * q1 + 2.f * Gy * q2 + r * q4 + V0.y * gr;
+    const float gA = gr, gB = -gr;  // It = B - A, gIt = -gr
+    float d1x, d1y, d2x, d2y;
+    sample_adj(P1, a.H, a.W, a.pitch, x, y, -hx, -hy, gA, 0.5f * gGx, 0.5f * gGy, gP1, gpitch, d1x, d1y);
+    sample_adj(P2, a.H, a.W, a.pitch, x, y, hx, hy, gB, 0.5f * gGx, 0.5f * gGy, gP2, gpitch, d2x, d2y);
+    float2 g = gV0[(int64_t)y * a.vpitch + x];
+    g.x += Gx * gr - 0.5f * d1x + 0.5f * d2x;
+    g.y += Gy * gr - 0.5f * d1y + 0.5f * d2y;
+    gV0[(int64_t)y * a.vpitch + x] = g;
+}
+
+// Transpose of the x2 up-sampling: scatter 2 * w * gV0(fine) to the coarse
+// taps (gc zeroed beforehand).
+__global__ void k_bw_upsample_T(const float2 *gV0, int vpitch, int H, int W, float2 *gc, int cpitch, int Hc, int Wc)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const float2 g = gV0[(int64_t)y * vpitch + x];
+    const int cx = x >> 1, cy = y >> 1;
+    const float fx = (x & 1) ? 0.5f : 0.f, fy = (y & 1) ? 0.5f : 0.f;
+    const int xa = min(cx, Wc - 1), xb = min(cx + 1, Wc - 1), ya = min(cy, Hc - 1), yb = min(cy + 1, Hc - 1);
+    const float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+    const int ty[4] = {ya, ya, yb, yb}, tx[4] = {xa, xb, xa, xb};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (w[k] == 0.f) continue;
+        float *p = reinterpret_cast<float *>(gc + (int64_t)ty[k] * cpitch + tx[k]);
+        atomicAdd(p, 2.f * w[k] * g.x);
+        atomicAdd(p + 1, 2.f * w[k] * g.y);
+    }
+}
+
+// Transpose of one pyramid reduction: level l+1 gradient (Hc x Wc) added
+// into level l (H x W), both dense with their pitches.
+__global__ void k_bw_reduce_T(const float *gc, int cpitch, int Hc, int Wc, float *g, int pitch, int H, int W)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= Hc || j >= Wc) return;
+    const float c[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+    const float v = gc[(int64_t)i * cpitch + j];
+    if (v == 0.f) return;
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+            atomicAdd(g + (int64_t)clampi(2 * i + a - 2, 0, H - 1) * pitch + clampi(2 * j + b - 2, 0, W - 1),
+                      c[a] * c[b] * v);
+}
+
+// Pre-filter transpose and weight gradient, then the input scaling:
+// gI(src) += w[a][b] * gJ(i,j) for src = clamp(i+a, j+b); gw[a][b] +=
+// gJ(i,j) * I(src).  The frame values I come from the raw input (scaled).
+template <typename TI>
+__device__ __forceinline__ float ld_raw(const TI *p) { return (float)__ldg(p); }
+
+template <typename TI>
+__global__ void k_bw_prefilter(const float *gJ, int pitch, int H, int W, const TI *raw, float scale, const float *w25,
+                               float *gI, float *gw)
+{
+    __shared__ float sw[25][8];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    const int lane = threadIdx.x + threadIdx.y * blockDim.x;
+    float acc[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) acc[k] = 0.f;
+    if (i < H && j < W) {
+        const float g = gJ[(int64_t)i * pitch + j];
+        if (g != 0.f) {
+#pragma unroll
+            for (int a = 0; a < 5; ++a)
+#pragma unroll
+                for (int b = 0; b < 5; ++b) {
+                    const int64_t src = (int64_t)clampi(i + a - 2, 0, H - 1) * W + clampi(j + b - 2, 0, W - 1);
+                    atomicAdd(gI + src, __ldg(w25 + a * 5 + b) * g * scale);
+                    acc[a * 5 + b] = g * ld_raw(raw + src) * scale;
+                }
+        }
+    }
+    // block reduction of the weight gradient: warp shuffles, then one atomic per warp
+#pragma unroll
+    for (int k = 0; k < 25; ++k) {
+        float v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((lane & 31) == 0) sw[k][lane >> 5] = v;
+    }
+    __syncthreads();
+    if (lane < 25) {
+        float s = 0.f;
+        for (int k = 0; k < (int)(blockDim.x * blockDim.y + 31) / 32; ++k) s += sw[lane][k];
+        atomicAdd(gw + lane, s);
+    }
+}
+
+// Without a pre-filter: gI = scale * gJ (dense output).
+__global__ void k_bw_copy_scaled(const float *gJ, int pitch, int H, int W, float scale, float *gI)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= H || j >= W) return;
+    gI[(int64_t)i * W + j] = scale * gJ[(int64_t)i * pitch + j];
+}
+
+// Dense planar (gu, gv) into an interleaved field of pitch vpitch.
+__global__ void k_bw_pack(const float *gu, const float *gv, int H, int W, float2 *out, int vpitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const int64_t i = (int64_t)y * W + x;
+    out[(int64_t)y * vpitch + x] = make_float2(__ldg(gu + i), __ldg(gv + i));
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static dim3 grid2(int W, int H) { return dim3((W + 31) / 32, (H + 7) / 8); }
+
+cudaError_t bw_pack(const float *gu, const float *gv, int H, int W, float2 *out, int vpitch, cudaStream_t s)
+{
+    k_bw_pack<<<grid2(W, H), dim3(32, 8), 0, s>>>(gu, gv, H, W, out, vpitch);
+    return cudaGetLastError();
+}
+
+cudaError_t bw_v0(const IterArgs &a, int mode, float2 *out, cudaStream_t s)
+{
+    k_bw_v0<<<grid2(a.W, a.H), dim3(32, 8), 0, s>>>(a, mode, out);
+    return cudaGetLastError();
+}
+
+cudaError_t bw_stage(const IterArgs &a, int store, Planes5 A, Planes5 B, const float2 *gV, float2 *gV0, float *gP1,
+                     float *gP2, int gpitch, cudaStream_t s)
+{
+    const dim3 g = grid2(a.W, a.H), b(32, 8);
+    switch (store) {
+    case ST_F16: k_bw_products<__half><<<g, b, 0, s>>>(a, A); break;
+    case ST_BF16: k_bw_products<__nv_bfloat16><<<g, b, 0, s>>>(a, A); break;
+    default: k_bw_products<float><<<g, b, 0, s>>>(a, A); break;
+    }
+    k_bw_box<<<g, b, 0, s>>>(A, B, a.H, a.W, a.kr, 0);
+    k_bw_box<<<g, b, 0, s>>>(B, A, a.H, a.W, a.kr, 1);
+    k_bw_solve<<<g, b, 0, s>>>(A, gV, a.vpitch, a.H, a.W, a.eps_rel, a.eps_abs, B, gV0);
+    k_bw_box<<<g, b, 0, s>>>(B, A, a.H, a.W, a.kr, 0);
+    k_bw_box<<<g, b, 0, s>>>(A, B, a.H, a.W, a.kr, 1);
+    switch (store) {
+    case ST_F16: k_bw_samples<__half><<<g, b, 0, s>>>(a, B, gV0, gP1, gP2, gpitch); break;
+    case ST_BF16: k_bw_samples<__nv_bfloat16><<<g, b, 0, s>>>(a, B, gV0, gP1, gP2, gpitch); break;
+    default: k_bw_samples<float><<<g, b, 0, s>>>(a, B, gV0, gP1, gP2, gpitch); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t bw_upsample_T(const float2 *gV0, int vpitch, int H, int W, float2 *gc, int cpitch, int Hc, int Wc,
+                          cudaStream_t s)
+{
+    k_bw_upsample_T<<<grid2(W, H), dim3(32, 8), 0, s>>>(gV0, vpitch, H, W, gc, cpitch, Hc, Wc);
+    return cudaGetLastError();
+}
+
+cudaError_t bw_reduce_T(const float *gc, int cpitch, int Hc, int Wc, float *g, int pitch, int H, int W, cudaStream_t s)
+{
+    k_bw_reduce_T<<<grid2(Wc, Hc), dim3(32, 8), 0, s>>>(gc, cpitch, Hc, Wc, g, pitch, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t bw_input(const float *gJ, int pitch, int H, int W, const void *raw, int in_type, float scale,
+                     const float *w25, int prefilter, float *gI, float *gw, cudaStream_t s)
+{
+    const dim3 g = grid2(W, H), b(32, 8);
+    if (!prefilter) {
+        k_bw_copy_scaled<<<g, b, 0, s>>>(gJ, pitch, H, W, scale, gI);
+        return cudaGetLastError();
+    }
+    switch (in_type) {
+    case IN_U8: k_bw_prefilter<uint8_t><<<g, b, 0, s>>>(gJ, pitch, H, W, static_cast<const uint8_t *>(raw), scale, w25, gI, gw); break;
+    case IN_U16: k_bw_prefilter<uint16_t><<<g, b, 0, s>>>(gJ, pitch, H, W, static_cast<const uint16_t *>(raw), scale, w25, gI, gw); break;
+    default: k_bw_prefilter<float><<<g, b, 0, s>>>(gJ, pitch, H, W, static_cast<const float *>(raw), scale, w25, gI, gw); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ofv
+
+namespace {
+
+using namespace ofv;
+
+struct BwDevGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit BwDevGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~BwDevGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Carve the reverse-mode workspace; returns its size (nothing written when
+// base is null).
+struct BwLayout {
+    float2 *Vst[kMaxLevels * 64];
+    float2 *V0in[kMaxLevels];
+    Planes5 A, B;
+    float2 *gV, *gV0;
+    float *gP1[kMaxLevels], *gP2[kMaxLevels];
+    float *gw_scratch;
+};
+
+size_t bw_layout(const ofv_handle *h, char *base, BwLayout *o)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    const int L = h->L, IT = h->p.iterations;
+    for (int s = 0; s < L * IT; ++s) {
+        const int l = L - 1 - s / IT;
+        o->Vst[s] = reinterpret_cast<float2 *>(take((size_t)h->Hs[l] * h->pitch[l] * sizeof(float2)));
+    }
+    for (int l = 0; l < L; ++l)
+        o->V0in[l] = reinterpret_cast<float2 *>(take((size_t)h->Hs[l] * h->pitch[l] * sizeof(float2)));
+    const size_t plane = (size_t)h->Hs[0] * h->pitch[0];
+    for (int c = 0; c < 5; ++c) {
+        o->A.p[c] = reinterpret_cast<float *>(take(plane * sizeof(float)));
+        o->B.p[c] = reinterpret_cast<float *>(take(plane * sizeof(float)));
+    }
+    o->gV = reinterpret_cast<float2 *>(take(plane * sizeof(float2)));
+    o->gV0 = reinterpret_cast<float2 *>(take(plane * sizeof(float2)));
+    for (int l = 0; l < L; ++l) {
+        o->gP1[l] = reinterpret_cast<float *>(take((size_t)h->Hs[l] * h->pitch[l] * sizeof(float)));
+        o->gP2[l] = reinterpret_cast<float *>(take((size_t)h->Hs[l] * h->pitch[l] * sizeof(float)));
+    }
+    o->gw_scratch = reinterpret_cast<float *>(take(32 * sizeof(float)));
+    return off;
+}
+
+#define BW_TRY(expr, what)                                 \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_fail_msg(e_, what); \
+    } while (0)
+
+}  // namespace
+
+extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2, const float *gu, const float *gv,
+                                   float *gI1, float *gI2, float *gw25, ofv_stream_t stream)
+{
+    if (!h) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_backward: handle is NULL");
+    if (!I1 || !I2 || !gu || !gv || !gI1 || !gI2)
+        return fail_msg(OFV_ERR_INVALID_ARG, "ofv_backward: I1, I2, gu, gv, gI1 and gI2 must be non-NULL");
+    if (gI1 == gI2) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_backward: gI1 and gI2 must be distinct buffers");
+    const ofv_params &p = h->p;
+    if (p.norm_radius > 0)
+        return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_backward: local normalization (NR=%d) has no adjoint", p.norm_radius);
+    if (p.iterations * h->L > kMaxLevels * 64)
+        return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_backward: too many stages");
+    BwDevGuard g(h->device);
+    if (!g.ok) return fail_msg(OFV_ERR_CUDA, "ofv_backward: cannot select the handle's device");
+    {
+        cudaError_t e = cudaPeekAtLastError();
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail_msg(e, "error pending before ofv_backward");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BwLayout w;
+    const size_t need = bw_layout(h, nullptr, &w);
+    if (need > h->bw_bytes) {
+        if (h->bw_arena) {
+            BW_TRY(cudaStreamSynchronize(s), "ofv_backward: waiting before growing the workspace");
+            cudaFree(h->bw_arena);
+            h->bw_arena = nullptr;
+            h->bw_bytes = 0;
+        }
+        if (cudaMalloc(&h->bw_arena, need) != cudaSuccess) {
+            cudaGetLastError();
+            h->bw_arena = nullptr;
+            return fail_msg(OFV_ERR_ALLOC, "ofv_backward: cudaMalloc of %zu bytes failed", need);
+        }
+        h->bw_bytes = need;
+    }
+    bw_layout(h, static_cast<char *>(h->bw_arena), &w);
+
+    // forward again (steps 1-5), keeping every stage's input and output field
+    const void *fr[2] = {I1, I2};
+    const int slots[2] = {0, 1};
+    ofv_status st = handle_pyramids(h, fr, slots, 2, s);
+    if (st != OFV_OK) return st;
+    h->last_s1 = 0;
+    h->last_s2 = 1;
+    const int L = h->L, IT = p.iterations, S = L * IT;
+    auto stage_args = [&](int sidx) {
+        const int l = L - 1 - sidx / IT, t = sidx % IT;
+        IterArgs a;
+        memset(&a, 0, sizeof a);
+        a.P1 = h->lvl[0][l];
+        a.P2 = h->lvl[1][l];
+        a.H = h->Hs[l];
+        a.W = h->Ws[l];
+        a.pitch = h->pitch[l];
+        a.vpitch = h->pitch[l];
+        a.kr = p.kernel_radius;
+        a.eps_rel = p.det_rel_eps;
+        a.eps_abs = p.det_abs_eps;
+        a.V0 = t == 0 ? w.V0in[l] : w.Vst[sidx - 1];
+        return a;
+    };
+    for (int sidx = 0; sidx < S; ++sidx) {
+        const int l = L - 1 - sidx / IT, t = sidx % IT;
+        IterArgs a = stage_args(sidx);
+        if (t == 0) {
+            IterArgs b = a;
+            int mode = V0_ZERO;
+            if (sidx > 0) {
+                mode = V0_UP;
+                b.Vc = w.Vst[sidx - 1];
+                b.Hc = h->Hs[l + 1];
+                b.Wc = h->Ws[l + 1];
+                b.vcpitch = h->pitch[l + 1];
+            }
+            BW_TRY(bw_v0(b, mode, w.V0in[l], s), "ofv_backward: stage input field");
+        }
+        a.Vout = w.Vst[sidx];
+        cudaError_t e = block_supports(p.kernel_radius) ? launch_iter_block(&a, 1, p.storage, V0_SAME, s)
+                                                        : launch_iter_fused(a, p.storage, V0_SAME, s);
+        BW_TRY(e, "ofv_backward: forward iteration");
+    }
+
+    // reverse
+    for (int l = 0; l < L; ++l) {
+        BW_TRY(cudaMemsetAsync(w.gP1[l], 0, (size_t)h->Hs[l] * h->pitch[l] * sizeof(float), s), "ofv_backward: memset");
+        BW_TRY(cudaMemsetAsync(w.gP2[l], 0, (size_t)h->Hs[l] * h->pitch[l] * sizeof(float), s), "ofv_backward: memset");
+    }
+    BW_TRY(bw_pack(gu, gv, h->H, h->W, w.gV, h->pitch[0], s), "ofv_backward: packing dL/dV");
+    float2 *gV = w.gV, *gV0 = w.gV0;
+    for (int sidx = S - 1; sidx >= 0; --sidx) {
+        const int l = L - 1 - sidx / IT, t = sidx % IT;
+        IterArgs a = stage_args(sidx);
+        Planes5 A = w.A, B = w.B;
+        A.pitch = B.pitch = h->pitch[l];
+        BW_TRY(bw_stage(a, p.storage, A, B, gV, gV0, w.gP1[l], w.gP2[l], h->pitch[l], s), "ofv_backward: stage adjoint");
+        if (sidx == 0) break;
+        if (t > 0) {
+            float2 *tmp = gV;
+            gV = gV0;
+            gV0 = tmp;
+        } else {
+            BW_TRY(cudaMemsetAsync(gV, 0, (size_t)h->Hs[l + 1] * h->pitch[l + 1] * sizeof(float2), s),
+                   "ofv_backward: memset");
+            BW_TRY(bw_upsample_T(gV0, h->pitch[l], h->Hs[l], h->Ws[l], gV, h->pitch[l + 1], h->Hs[l + 1], h->Ws[l + 1], s),
+                   "ofv_backward: up-sampling adjoint");
+        }
+    }
+    for (int l = L - 1; l >= 1; --l) {
+        BW_TRY(bw_reduce_T(w.gP1[l], h->pitch[l], h->Hs[l], h->Ws[l], w.gP1[l - 1], h->pitch[l - 1], h->Hs[l - 1],
+                           h->Ws[l - 1], s),
+               "ofv_backward: reduce adjoint");
+        BW_TRY(bw_reduce_T(w.gP2[l], h->pitch[l], h->Hs[l], h->Ws[l], w.gP2[l - 1], h->pitch[l - 1], h->Hs[l - 1],
+                           h->Ws[l - 1], s),
+               "ofv_backward: reduce adjoint");
+    }
+    const float scale = p.input == OFV_IN_F32 ? 1.0f : 1.0f / (float)((1u << p.bit_depth) - 1u);
+    float *gw = gw25 ? gw25 : w.gw_scratch;
+    const size_t nbytes = (size_t)h->H * h->W * sizeof(float);
+    if (p.prefilter) {
+        BW_TRY(cudaMemsetAsync(gI1, 0, nbytes, s), "ofv_backward: memset");
+        BW_TRY(cudaMemsetAsync(gI2, 0, nbytes, s), "ofv_backward: memset");
+        BW_TRY(cudaMemsetAsync(gw, 0, 25 * sizeof(float), s), "ofv_backward: memset");
+    } else if (gw25) {
+        BW_TRY(cudaMemsetAsync(gw25, 0, 25 * sizeof(float), s), "ofv_backward: memset");
+    }
+    BW_TRY(bw_input(w.gP1[0], h->pitch[0], h->H, h->W, I1, p.input, scale, h->w25, p.prefilter, gI1, gw, s),
+           "ofv_backward: input adjoint");
+    BW_TRY(bw_input(w.gP2[0], h->pitch[0], h->H, h->W, I2, p.input, scale, h->w25, p.prefilter, gI2, gw, s),
+           "ofv_backward: input adjoint");
+    return OFV_OK;
+}

@@ -275,6 +275,11 @@ ofv_status fail_msg(ofv_status st, const char *fmt, ...)
 }
 
 ofv_status cuda_fail_msg(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+
+ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s)
+{
+    return build_pyramids(h, frames, slots, nf, s);
+}
 }  // namespace ofv
 
 extern "C" {
@@ -419,6 +424,7 @@ ofv_status ofv_destroy(ofv_handle *h)
     for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
     if (h->stage) cudaFree(h->stage);
     if (h->batch_arena) cudaFree(h->batch_arena);
+    if (h->bw_arena) cudaFree(h->bw_arena);
     if (h->arena) cudaFree(h->arena);
     delete h;
     return st;

@@ -71,4 +71,12 @@ struct ofv_handle {
     std::map<std::string, ofv::BatchTune> tune;
     ofv::BatchTune last_tune;
     int last_tuned;  // 1 if the last batched call ran the autotuner
+    // reverse mode: grow-only workspace (stage fields, sums, gradients)
+    void *bw_arena;
+    size_t bw_bytes;
 };
+
+namespace ofv {
+// Steps 1-2 into the handle's pyramid slots (defined with the C ABI).
+ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s);
+}  // namespace ofv

@@ -1,0 +1,194 @@
+"""GPU parity of the reverse mode: ofv_backward through the C ABI, and the
+torch.autograd wrapper, vs the FP64 oracle's reverse mode on the same seeded
+inputs.
+
+Tolerance (written here): relative L2 error of each gradient
+||g_gpu - g_oracle|| / ||g_oracle|| <= 2e-3 for FP32 storage on smooth
+textured pairs, 3e-2 on particle images and 5e-2 for FP16 level storage.
+The gradient multiplies FP32 round-off by the condition number of each 2x2
+system and by the slopes of the bilinear cells, so it is compared in the
+aggregate rather than element by element; float atomics make the last bits
+vary between runs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2509_25924_gb300 as ofv  # noqa: E402
+from paper_2509_25924_gb300.autograd import flow_fn  # noqa: E402
+import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+_IN = {np.dtype(np.float32): ofv.OFV_IN_F32, np.dtype(np.uint16): ofv.OFV_IN_U16,
+       np.dtype(np.uint8): ofv.OFV_IN_U8}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def gpu_grad(I1, I2, gu, gv, w25=None, bits=12, **kw):
+    H, W = I1.shape
+    kw.setdefault("input", _IN[I1.dtype])
+    kw.setdefault("bit_depth", bits)
+    if w25 is not None:
+        kw["prefilter"] = 1
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(**kw))
+    try:
+        t1 = torch.from_numpy(np.ascontiguousarray(I1)).to(DEV)
+        t2 = torch.from_numpy(np.ascontiguousarray(I2)).to(DEV)
+        if w25 is not None:
+            ofv.ofv_set_prefilter(h, torch.tensor(np.asarray(w25, np.float32).reshape(25), device=DEV))
+        tgu = torch.from_numpy(gu.astype(np.float32)).to(DEV)
+        tgv = torch.from_numpy(gv.astype(np.float32)).to(DEV)
+        g1 = torch.empty((H, W), dtype=torch.float32, device=DEV)
+        g2 = torch.empty_like(g1)
+        gw = torch.empty(25, dtype=torch.float32, device=DEV)
+        ofv.ofv_backward(h, t1, t2, tgu, tgv, g1, g2, gw)
+        torch.cuda.synchronize()
+        return g1.cpu().numpy(), g2.cpu().numpy(), gw.cpu().numpy().reshape(5, 5)
+    finally:
+        ofv.ofv_destroy(h)
+
+
+def oracle_grad(I1, I2, gu, gv, w25=None, bits=12, psl=2, kr=4, it=3):
+    b = bits if I1.dtype != np.float32 else 0
+    p = oracle.Params(psl=psl, kr=kr, it=it, bits=b, prefilter=w25)
+    g1, g2, gw, _, _ = oracle.flow_grad(I1.astype(np.float64), I2.astype(np.float64), p, gu, gv)
+    return g1, g2, gw
+
+
+def _smooth(H, W, seed, shift=(0.8, -0.5)):
+    I1, I2 = synth.smooth_pair(H, W, shift, seed=seed)
+    rng = np.random.default_rng(seed)
+    return (I1.astype(np.float32), I2.astype(np.float32),
+            rng.standard_normal((H, W)), rng.standard_normal((H, W)))
+
+
+@pytest.mark.parametrize("H,W,psl,kr,it", [(64, 72, 1, 2, 2), (97, 83, 2, 4, 3), (48, 48, 0, 3, 1),
+                                           (80, 96, 1, 12, 2)])
+def test_frame_gradients_match_oracle(H, W, psl, kr, it):
+    I1, I2, gu, gv = _smooth(H, W, seed=H + W)
+    g1, g2, _ = gpu_grad(I1, I2, gu, gv, levels_psl=psl, kernel_radius=kr, iterations=it)
+    o1, o2, _ = oracle_grad(I1, I2, gu, gv, psl=psl, kr=kr, it=it)
+    assert _rel(g1, o1) <= 2e-3, _rel(g1, o1)
+    assert _rel(g2, o2) <= 2e-3, _rel(g2, o2)
+
+
+def test_prefilter_weight_gradient_matches_oracle():
+    H, W = 70, 66
+    I1, I2, gu, gv = _smooth(H, W, seed=4)
+    rng = np.random.default_rng(4)
+    w = np.zeros((5, 5))
+    w[2, 2] = 0.6
+    w[1:4, 1:4] += 0.05
+    w = (w + 0.01 * rng.standard_normal((5, 5))).astype(np.float32)
+    g1, g2, gw = gpu_grad(I1, I2, gu, gv, w25=w, levels_psl=1, kernel_radius=3, iterations=2)
+    o1, o2, ow = oracle_grad(I1, I2, gu, gv, w25=w.astype(np.float64), psl=1, kr=3, it=2)
+    assert _rel(gw, ow) <= 2e-3, _rel(gw, ow)
+    assert _rel(g1, o1) <= 2e-3 and _rel(g2, o2) <= 2e-3
+
+
+@pytest.mark.parametrize("dtype,bits", [(np.uint16, 12), (np.uint8, 8)])
+def test_particle_images_counts_input(dtype, bits):
+    kind = synth.OUT_U16 if dtype == np.uint16 else synth.OUT_U8
+    I1, I2 = synth.particle_pair(160, 176, synth.rankine_field(160, 176), ppp=0.05, dmin=2.5, dmax=2.5, seed=6,
+                                 noise=0.01, kind=kind, bits=bits, field_max=3.0)
+    assert I1.dtype == dtype
+    rng = np.random.default_rng(6)
+    gu, gv = rng.standard_normal(I1.shape), rng.standard_normal(I1.shape)
+    g1, g2, _ = gpu_grad(I1, I2, gu, gv, bits=bits)
+    o1, o2, _ = oracle_grad(I1, I2, gu, gv, bits=bits)
+    assert _rel(g1, o1) <= 3e-2, _rel(g1, o1)
+    assert _rel(g2, o2) <= 3e-2, _rel(g2, o2)
+
+
+def test_fp16_storage_gradient():
+    I1, I2, gu, gv = _smooth(64, 80, seed=9)
+    g1, g2, _ = gpu_grad(I1, I2, gu, gv, storage=ofv.OFV_STORE_F16, levels_psl=1, kernel_radius=3, iterations=2)
+    o1, o2, _ = oracle_grad(I1, I2, gu, gv, psl=1, kr=3, it=2)
+    assert _rel(g1, o1) <= 5e-2 and _rel(g2, o2) <= 5e-2
+
+
+def test_zero_output_gradient_gives_zero():
+    I1, I2, _, _ = _smooth(48, 56, seed=2)
+    z = np.zeros(I1.shape)
+    g1, g2, gw = gpu_grad(I1, I2, z, z, w25=np.full((5, 5), 0.04, np.float32), levels_psl=1, kernel_radius=2,
+                          iterations=2)
+    assert not g1.any() and not g2.any() and not gw.any()
+
+
+def test_normalization_is_unsupported():
+    H, W = 64, 64
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(norm_radius=3, input=ofv.OFV_IN_F32))
+    try:
+        t = torch.zeros((H, W), dtype=torch.float32, device=DEV)
+        g = torch.empty_like(t)
+        g2 = torch.empty_like(t)
+        with pytest.raises(ofv.OfvError) as e:
+            ofv.ofv_backward(h, t, t, t, t, g, g2)
+        assert e.value.status == ofv.OFV_ERR_UNSUPPORTED
+    finally:
+        ofv.ofv_destroy(h)
+
+
+def test_autograd_function_matches_c_abi_and_oracle():
+    H, W = 72, 80
+    I1, I2, gu, gv = _smooth(H, W, seed=12)
+    w = np.zeros((5, 5), np.float32)
+    w[2, 2] = 0.7
+    w[1:4, 1:4] += 0.03
+    flow = ofv.Flow(H, W, input=ofv.OFV_IN_F32, prefilter=1, levels_psl=1, kernel_radius=3, iterations=2)
+    try:
+        t1 = torch.from_numpy(I1).to(DEV).requires_grad_(True)
+        t2 = torch.from_numpy(I2).to(DEV).requires_grad_(True)
+        tw = torch.from_numpy(w).to(DEV).requires_grad_(True)
+        u, v = flow_fn(flow, t1, t2, tw)
+        loss = (u * torch.from_numpy(gu.astype(np.float32)).to(DEV)).sum() + \
+               (v * torch.from_numpy(gv.astype(np.float32)).to(DEV)).sum()
+        loss.backward()
+        o1, o2, ow = oracle_grad(I1, I2, gu, gv, w25=w.astype(np.float64), psl=1, kr=3, it=2)
+        assert _rel(t1.grad.cpu().numpy(), o1) <= 2e-3
+        assert _rel(t2.grad.cpu().numpy(), o2) <= 2e-3
+        assert _rel(tw.grad.cpu().numpy(), ow) <= 2e-3
+        # forward of the autograd node is the plain estimator
+        ou, ov = oracle.flow(I1.astype(np.float64), I2.astype(np.float64),
+                             oracle.Params(psl=1, kr=3, it=2, prefilter=w.astype(np.float64)))
+        assert np.max(np.abs(u.detach().cpu().numpy() - ou)) < 1e-3
+    finally:
+        flow.close()
+
+
+def test_prefilter_training_step_lowers_the_loss():
+    # a few gradient steps on the pre-filter weights against a known field
+    H, W = 96, 96
+    d = (1.3, -0.6)
+    I1, I2 = synth.smooth_pair(H, W, d, seed=31)
+    I1, I2 = I1.astype(np.float32), I2.astype(np.float32)
+    flow = ofv.Flow(H, W, input=ofv.OFV_IN_F32, prefilter=1, levels_psl=1, kernel_radius=4, iterations=1)
+    try:
+        t1 = torch.from_numpy(I1).to(DEV)
+        t2 = torch.from_numpy(I2).to(DEV)
+        w = torch.zeros((5, 5), device=DEV)
+        w[2, 2] = 1.0
+        w[0, 0] = 0.3  # a bad start: the ideal filter is symmetric
+        w.requires_grad_(True)
+        opt = torch.optim.SGD([w], lr=5e-2)
+        losses = []
+        for _ in range(6):
+            opt.zero_grad()
+            u, v = flow_fn(flow, t1, t2, w)
+            loss = ((u - d[0]) ** 2).mean() + ((v - d[1]) ** 2).mean()
+            loss.backward()
+            losses.append(float(loss))
+            opt.step()
+        # FP64 reverse mode with the same steps: 0.00993 -> 0.00911
+        assert losses[-1] < 0.97 * losses[0], losses
+    finally:
+        flow.close()
