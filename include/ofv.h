@@ -134,6 +134,18 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
                                 size_t frame_stride_bytes, float *u, float *v, size_t field_stride,
                                 ofv_stream_t s);
 
+/* As ofv_compute_sequence, but frames, u and v are HOST pointers (use
+   page-locked memory for the copies to overlap).  The sequence runs in
+   groups of the handle's pairs-per-launch; each frame is uploaded once, and
+   the upload of the next group and the download of the previous group's
+   fields run on two library-owned copy streams while the current group
+   computes on s.  A device ring of 3 groups (frames and fields) is
+   allocated on first use and kept.  Work queued on s before the call runs
+   first; the host outputs are valid once s has been synchronised. */
+ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *frames,
+                                     size_t frame_stride_bytes, float *u, float *v,
+                                     size_t field_stride, ofv_stream_t s);
+
 /* ---- reverse mode -------------------------------------------------------
  * The paper defines no derivative; this is the chain rule through the steps
  * of Sec. 2 (Eq. 2 and its Gauss-Newton linearisation, the pyramid, the

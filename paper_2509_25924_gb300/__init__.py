@@ -18,8 +18,8 @@ from . import build as _build
 
 __all__ = [
     "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter",
-    "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_backward",
-    "ofv_level_shape",
+    "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host",
+    "ofv_compute_noalloc", "ofv_backward", "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
     "Flow", "lib_path", "EXPORTED_SYMBOLS",
@@ -34,7 +34,8 @@ OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED_SYMBOLS = [
     "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_compute",
-    "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_noalloc", "ofv_graph_create", "ofv_graph_launch",
+    "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host", "ofv_compute_noalloc",
+    "ofv_graph_create", "ofv_graph_launch",
     "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
     "ofv_level_shape",
     "ofv_read_level",
@@ -71,6 +72,7 @@ def _load_library():
         "ofv_compute": ([P, P, P, P, P, P], I),
         "ofv_compute_host": ([P, P, P, P, P, P], I),
         "ofv_compute_sequence": ([P, I, P, Z, P, P, Z, P], I),
+        "ofv_compute_sequence_host": ([P, I, P, Z, P, P, Z, P], I),
         "ofv_compute_noalloc": ([I, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
         "ofv_graph_create": ([P, P, P, P, P, ctypes.POINTER(P)], I),
         "ofv_graph_launch": ([P, P], I),
@@ -168,6 +170,13 @@ def ofv_compute_sequence(h: int, n_frames: int, frames, frame_stride_bytes: int,
                          stream=None):
     _check(_lib.ofv_compute_sequence(h, n_frames, _addr(frames), frame_stride_bytes, _addr(u), _addr(v),
                                      field_stride, _stream(stream)), "ofv_compute_sequence")
+
+
+def ofv_compute_sequence_host(h: int, n_frames: int, frames, frame_stride_bytes: int, u, v, field_stride: int,
+                              stream=None):
+    """frames, u, v are host buffers (pinned torch tensors or numpy arrays)."""
+    _check(_lib.ofv_compute_sequence_host(h, n_frames, _addr(frames), frame_stride_bytes, _addr(u), _addr(v),
+                                          field_stride, _stream(stream)), "ofv_compute_sequence_host")
 
 
 def ofv_compute_noalloc(H: int, W: int, params: Params, w25, I1, I2, u, v, stream=None):

@@ -425,6 +425,13 @@ ofv_status ofv_destroy(ofv_handle *h)
     if (h->stage) cudaFree(h->stage);
     if (h->batch_arena) cudaFree(h->batch_arena);
     if (h->bw_arena) cudaFree(h->bw_arena);
+    if (h->hs_stage) cudaFree(h->hs_stage);
+    if (h->hs_ready) {
+        for (int r = 0; r < kHostRing; ++r)
+            for (int k = 0; k < 3; ++k) cudaEventDestroy(h->hs_ev[r][k]);
+        cudaStreamDestroy(h->hs_stream[0]);
+        cudaStreamDestroy(h->hs_stream[1]);
+    }
     if (h->arena) cudaFree(h->arena);
     delete h;
     return st;
@@ -541,6 +548,135 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
         h->last_s1 = s1[np - 1];
         h->last_s2 = s2[np - 1];
     }
+    return OFV_OK;
+}
+
+ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *frames, size_t frame_stride_bytes,
+                                     float *u, float *v, size_t field_stride, ofv_stream_t s)
+{
+    if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
+    if (!frames || !u || !v) return fail(OFV_ERR_INVALID_ARG, "frames, u and v must be non-NULL");
+    if (u == v) return fail(OFV_ERR_INVALID_ARG, "u and v must be distinct buffers");
+    if (n_frames < 2) return fail(OFV_ERR_INVALID_ARG, "n_frames=%d must be >= 2", n_frames);
+    const size_t N = (size_t)h->H * h->W;
+    const size_t fb = N * input_bytes(h->p.input);
+    if (frame_stride_bytes < fb)
+        return fail(OFV_ERR_INVALID_ARG, "frame_stride_bytes=%zu is smaller than one frame", frame_stride_bytes);
+    if (field_stride < N) return fail(OFV_ERR_INVALID_ARG, "field_stride=%zu is smaller than one field", field_stride);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    ofv_status st = pending_error("error pending before ofv_compute_sequence_host");
+    if (st != OFV_OK) return st;
+    cudaStream_t cs = (cudaStream_t)s;
+    const int B = h->B, NS = h->nslots;
+    // device ring: per slot B+1 frames and B fields (u and v)
+    const size_t in_b = align_up(fb * (size_t)(B + 1), 256);
+    const size_t out_b = align_up(N * sizeof(float) * (size_t)B, 256);
+    const size_t slot_b = in_b + 2 * out_b;
+    const size_t need = slot_b * kHostRing;
+    if (!h->hs_ready) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->hs_stream[0], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->hs_stream[1], cudaStreamNonBlocking);
+        for (int r = 0; r < kHostRing && e == cudaSuccess; ++r)
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+                e = cudaEventCreateWithFlags(&h->hs_ev[r][k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "creating the copy streams");
+        h->hs_ready = 1;
+    }
+    if (need > h->hs_bytes) {
+        if (h->hs_stage) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "waiting before growing the host pipeline ring");
+            cudaFree(h->hs_stage);
+            h->hs_stage = nullptr;
+            h->hs_bytes = 0;
+        }
+        if (cudaMalloc(&h->hs_stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            h->hs_stage = nullptr;
+            return fail(OFV_ERR_ALLOC, "cudaMalloc of %zu ring bytes failed", need);
+        }
+        h->hs_bytes = need;
+    }
+    cudaStream_t up = h->hs_stream[0], down = h->hs_stream[1];
+    const char *hf = static_cast<const char *>(frames);
+    const int npairs = n_frames - 1;
+    // The copy streams start after the work already queued on s.
+    cudaError_t e = cudaEventRecord(h->hs_ev[0][1], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(up, h->hs_ev[0][1], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(down, h->hs_ev[0][1], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering the copy streams");
+    // Group c (pairs c*B .. c*B+np-1) uses ring slot c mod kHostRing: its
+    // new frames go up on stream `up`, the group runs on s, its fields come
+    // down on stream `down`.  A slot is reused once the group that last used
+    // it has finished on s (frames) and gone down (fields).
+    int c = 0;
+    for (int f0 = 0; f0 < npairs; f0 += B, ++c) {
+        const int r = c % kHostRing;
+        const int np = npairs - f0 < B ? npairs - f0 : B;
+        char *slot = static_cast<char *>(h->hs_stage) + (size_t)r * slot_b;
+        float *du = reinterpret_cast<float *>(slot + in_b), *dv = reinterpret_cast<float *>(slot + in_b + out_b);
+        const int fa = f0 == 0 ? 0 : f0 + 1, fz = f0 + np;  // frames to ingest
+        if (c >= kHostRing) {
+            e = cudaStreamWaitEvent(up, h->hs_ev[r][1], 0);  // group c - kHostRing done on s
+            if (e != cudaSuccess) return cuda_fail(e, "ordering the frame upload");
+        }
+        if (frame_stride_bytes == fb) {
+            e = cudaMemcpyAsync(slot, hf + (size_t)fa * fb, fb * (size_t)(fz - fa + 1), cudaMemcpyHostToDevice, up);
+        } else {
+            for (int f = fa; f <= fz && e == cudaSuccess; ++f)
+                e = cudaMemcpyAsync(slot + (size_t)(f - fa) * fb, hf + (size_t)f * frame_stride_bytes, fb,
+                                    cudaMemcpyHostToDevice, up);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->hs_ev[r][0], up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->hs_ev[r][0], 0);
+        if (e == cudaSuccess && c >= kHostRing) e = cudaStreamWaitEvent(cs, h->hs_ev[r][2], 0);  // fields gone down
+        if (e != cudaSuccess) return cuda_fail(e, "uploading frames");
+        const void *fr[kMaxSlots];
+        int slots[kMaxSlots];
+        int nf = 0;
+        for (int f = fa; f <= fz; ++f) {
+            fr[nf] = slot + (size_t)(f - fa) * fb;
+            slots[nf] = f % NS;
+            ++nf;
+        }
+        st = build_pyramids(h, fr, slots, nf, cs);
+        if (st != OFV_OK) return st;
+        int s1[kMaxBatch], s2[kMaxBatch];
+        float *uu[kMaxBatch], *vv[kMaxBatch];
+        for (int k = 0; k < np; ++k) {
+            s1[k] = (f0 + k) % NS;
+            s2[k] = (f0 + k + 1) % NS;
+            uu[k] = du + (size_t)k * N;
+            vv[k] = dv + (size_t)k * N;
+        }
+        st = run_levels(h, np, s1, s2, uu, vv, cs);
+        if (st != OFV_OK) return st;
+        h->last_s1 = s1[np - 1];
+        h->last_s2 = s2[np - 1];
+        e = cudaEventRecord(h->hs_ev[r][1], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(down, h->hs_ev[r][1], 0);
+        if (e == cudaSuccess) {
+            if (field_stride == N) {
+                e = cudaMemcpyAsync(u + (size_t)f0 * N, du, N * sizeof(float) * np, cudaMemcpyDeviceToHost, down);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(v + (size_t)f0 * N, dv, N * sizeof(float) * np, cudaMemcpyDeviceToHost, down);
+            } else {
+                for (int k = 0; k < np && e == cudaSuccess; ++k) {
+                    e = cudaMemcpyAsync(u + (size_t)(f0 + k) * field_stride, du + (size_t)k * N, N * sizeof(float),
+                                        cudaMemcpyDeviceToHost, down);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(v + (size_t)(f0 + k) * field_stride, dv + (size_t)k * N,
+                                            N * sizeof(float), cudaMemcpyDeviceToHost, down);
+                }
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->hs_ev[r][2], down);
+        if (e != cudaSuccess) return cuda_fail(e, "downloading fields");
+    }
+    // s reaches its end only after the last fields are in host memory
+    e = cudaStreamWaitEvent(cs, h->hs_ev[(c - 1) % kHostRing][2], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "joining the copy streams");
     return OFV_OK;
 }
 

@@ -14,6 +14,7 @@ namespace ofv {
 constexpr int kMaxLevels = 16;
 constexpr int kMaxBatch = kMaxPairsPerLaunch;
 constexpr int kMaxSlots = kMaxBatch + 1;
+constexpr int kHostRing = 3;  // device ring slots of the host-memory sequence pipeline
 
 struct ProfRec {
     int cls;
@@ -74,6 +75,12 @@ struct ofv_handle {
     // reverse mode: grow-only workspace (stage fields, sums, gradients)
     void *bw_arena;
     size_t bw_bytes;
+    // host-memory sequence pipeline: copy streams, ring events, device ring
+    cudaStream_t hs_stream[2];            // [0] host-to-device, [1] device-to-host
+    cudaEvent_t hs_ev[ofv::kHostRing][3];  // per ring slot: frames in, fields ready, fields out
+    int hs_ready;
+    void *hs_stage;
+    size_t hs_bytes;
 };
 
 namespace ofv {

@@ -308,6 +308,44 @@ def test_sequence_equals_pairwise_and_host_entry_point(path, batch):
         ofv.ofv_destroy(h)
 
 
+@pytest.mark.parametrize("batch,strided,pinned", [(3, False, True), (2, True, True), (8, False, False),
+                                                  (1, True, False)])
+def test_host_sequence_pipeline_equals_device_sequence(batch, strided, pinned):
+    """The host-memory sequence (uploads and downloads on their own streams,
+    a 3-group device ring that wraps several times) gives bitwise the fields
+    of the device sequence, for dense and strided host layouts."""
+    n, H, W = 23, 96, 136
+    F = synth.stream_frames(H, W, n, seed=4)
+    p = ofv.ofv_default_params(max_batch=batch, **PARAMS)
+    h = ofv.ofv_create(H, W, p)
+    try:
+        N = H * W
+        fr = torch.from_numpy(F).to(DEV)
+        us = torch.empty((n - 1, H, W), device=DEV); vs = torch.empty_like(us)
+        ofv.ofv_compute_sequence(h, n, fr, N * 2, us, vs, N)
+        fpad = 40 if strided else 0   # extra elements after each frame / field
+        opad = 24 if strided else 0
+        hf = torch.zeros((n, N + fpad), dtype=torch.int16)
+        hf[:, :N] = torch.from_numpy(F.reshape(n, N).view(np.int16))
+        hu = torch.full((n - 1, N + opad), -7.0)
+        hv = torch.full((n - 1, N + opad), -7.0)
+        if pinned:
+            hf, hu, hv = hf.pin_memory(), hu.pin_memory(), hv.pin_memory()
+        ofv.ofv_compute_sequence_host(h, n, hf, (N + fpad) * 2, hu, hv, N + opad)
+        torch.cuda.synchronize()
+        assert torch.equal(hu[:, :N].reshape(n - 1, H, W), us.cpu())
+        assert torch.equal(hv[:, :N].reshape(n - 1, H, W), vs.cpu())
+        if opad:
+            assert bool((hu[:, N:] == -7.0).all()) and bool((hv[:, N:] == -7.0).all())
+        # a second call reuses the ring and the copy streams
+        hu.fill_(0.0)
+        ofv.ofv_compute_sequence_host(h, n, hf, (N + fpad) * 2, hu, hv, N + opad)
+        torch.cuda.synchronize()
+        assert torch.equal(hu[:, :N].reshape(n - 1, H, W), us.cpu())
+    finally:
+        ofv.ofv_destroy(h)
+
+
 def test_graph_replay_matches_compute_and_follows_new_frames():
     """A captured graph replays the whole pipeline on whatever the fixed input
     buffers hold at launch time (the live-loop pattern)."""
