@@ -4,9 +4,11 @@
 // One CTA owns a TS x TS tile of output pixels (TS = 48 for KR <= 5, else
 // 32) and works entirely on chip in five phases:
 //   0. stage the two level images over the tile, its KR window halo, a
-//      REACH px warp margin and the gradient stencil into shared memory
-//      (clamp-to-edge applied while staging, 16-byte cp.async rows away from
-//      the image border);
+//      REACH px warp margin and the gradient stencil into shared memory:
+//      a tile whose staged box lies inside the image takes two TMA tensor
+//      copies (cp.async.bulk.tensor, completion on an mbarrier) when the
+//      launch carries tensor maps; otherwise 16-byte cp.async rows, with
+//      clamp-to-edge applied element by element at the image border;
 //   1. the five products of every pixel of tile + halo (bilinear value and
 //      central-difference gradient of both frames at k -/+ V0/2) into
 //      shared memory; taps farther than REACH px come from global memory;
@@ -20,6 +22,8 @@
 // Products of pixels outside the image are zero, which truncates the
 // windows at the border.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded on the host)
+
 #include "iter_math.cuh"
 
 namespace ofv {
@@ -31,6 +35,9 @@ constexpr int kBlockMaxBatch = kMaxPairsPerLaunch;
 struct BlockParams {
     IterArgs a[kBlockMaxBatch];  // one per pair (blockIdx.z)
     int mode;                    // V0Mode, uniform per launch
+    int use_tma;                 // 1: tm[k] maps the two level images of pair k
+    int *err;                    // error word (set to 1 when a TMA wait expires), or null
+    CUtensorMap tm[kBlockMaxBatch][2];
 };
 
 template <int KR> struct BlockShape {
@@ -46,18 +53,20 @@ template <typename T, int KR> struct StageShape {
     static constexpr int SW = BlockShape<KR>::RW + 2 * kBlockReach + 3 + VEC - 1;  // incl. alignment slack
     static constexpr int NV = (SW + VEC - 1) / VEC;                               // 16-byte vectors per row
     static constexpr int SP = NV * VEC;                                           // staged row pitch
+    // elements per staged frame, rounded so the second frame starts 128-byte aligned
+    static constexpr int STG = (BlockShape<KR>::SH * SP * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
 };
 
 // floats of the five product planes, rounded up so the staged images that
-// follow start 16-byte aligned
+// follow start 128-byte aligned (TMA destinations)
 template <int KR> struct ProdFloats {
-    static constexpr int v = (5 * BlockShape<KR>::RW * BlockShape<KR>::RWP + 3) / 4 * 4;
+    static constexpr int v = (5 * BlockShape<KR>::RW * BlockShape<KR>::RWP + 31) / 32 * 32;
 };
 
 template <typename T, int KR>
 constexpr size_t block_smem_bytes()
 {
-    return sizeof(float) * ProdFloats<KR>::v + sizeof(T) * 2 * BlockShape<KR>::SH * StageShape<T, KR>::SP;
+    return sizeof(float) * ProdFloats<KR>::v + sizeof(T) * 2 * StageShape<T, KR>::STG;
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -68,6 +77,61 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// mbarrier and TMA (bulk tensor copy) primitives, CTA scope.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 2-D tiled copy of the box at element (x, y) of the tensor map into shared
+// memory; x * sizeof(element) must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Wait for phase `parity` of the barrier, at most ~timeout_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long timeout_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    for (int i = 0; i < (1 << 22); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && global_ns() - t0 > timeout_ns) return false;
+    }
+    return false;
 }
 
 // Field load: through the read-only cache, or -- when the field was written
@@ -101,6 +165,14 @@ __device__ __forceinline__ float2 fetch_v0_rt(const IterArgs &a, int mode, int x
         return r;
     }
     return make_float2(0.f, 0.f);
+}
+
+// V0 with the mode fixed at compile time, for pixels inside the image.
+template <bool COH, int MODE>
+__device__ __forceinline__ float2 fetch_v0_ct(const IterArgs &a, int x, int y)
+{
+    if (MODE == V0_ZERO) return make_float2(0.f, 0.f);
+    return fetch_v0_rt<COH>(a, MODE, x, y);
 }
 
 // Global-memory sampler for warps beyond the staged margin (rare).
@@ -212,6 +284,43 @@ __device__ __forceinline__ void products_interior(const T *__restrict__ st1, con
     p[4] = Gy * r;
 }
 
+// Phase 1 of a tile whose staged box lies inside the image: every pixel of
+// the product region is inside the image and takes the staged fast path, so
+// the loop needs no bounds or border checks; the V0 mode is a template
+// parameter.  V0 of the thread's next pixel is loaded one iteration ahead.
+template <typename T, int KR, bool COH, int MODE, int SP>
+__device__ __forceinline__ void products_tile_interior(const IterArgs &a, const T *__restrict__ st1,
+                                                       const T *__restrict__ st2, int sx0, int sy0, int px0, int py0,
+                                                       float *prod)
+{
+    using BS = BlockShape<KR>;
+    constexpr int NT = BS::NT, RW = BS::RW, RWP = BS::RWP, PLANE = RW * RWP;
+    constexpr int DY = NT / RW, DX = NT % RW;
+    const int tid = threadIdx.x;
+    int ry = tid / RW, rx = tid - (tid / RW) * RW;
+    float2 V0n = make_float2(0.f, 0.f);
+    if (ry < RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
+    for (int idx = tid; idx < RW * RW; idx += NT) {
+        const float2 V0c = V0n;
+        const int gx = px0 + rx, gy = py0 + ry;
+        float *q = prod + ry * RWP + rx;
+        rx += DX;
+        ry += DY;
+        if (rx >= RW) {
+            rx -= RW;
+            ++ry;
+        }
+        if (idx + NT < RW * RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
+        float p[5];
+        products_interior<T, SP>(st1, st2, sx0, sy0, a, gx, gy, V0c, p);
+        q[0] = p[0];
+        q[PLANE] = p[1];
+        q[2 * PLANE] = p[2];
+        q[3 * PLANE] = p[3];
+        q[4 * PLANE] = p[4];
+    }
+}
+
 // Window sums of one line of the product planes, in place: for outputs
 // o = 0 .. TS-1, line[o*stride] <- sum_{j=0}^{2KR} line[(o+j)*stride].
 // Outputs are formed block by block (blocks of WIN = 2KR+1): the sums of a
@@ -250,16 +359,18 @@ __device__ __forceinline__ void window_sums_inplace(float *line, int stride)
 }
 
 template <typename T, int KR, bool COH>
-__device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4)
+__device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4,
+                                           const CUtensorMap *tm1 = nullptr, const CUtensorMap *tm2 = nullptr,
+                                           int *err = nullptr)
 {
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
     constexpr int TS = BS::TS, NT = BS::NT, RW = BS::RW, RWP = BS::RWP, SH = BS::SH;
-    constexpr int SP = SS::SP, NV = SS::NV, VEC = SS::VEC;
+    constexpr int SP = SS::SP, NV = SS::NV, VEC = SS::VEC, STG = SS::STG;
     constexpr int PLANE = RW * RWP;
 
     float *prod = reinterpret_cast<float *>(smem_f4);                // [5][RW][RWP]
-    T *stage = reinterpret_cast<T *>(prod + ProdFloats<KR>::v);     // [2][SH][SP]
+    T *stage = reinterpret_cast<T *>(prod + ProdFloats<KR>::v);     // [2][STG]: SH rows of SP
 
     const int tid = threadIdx.x;
     const int H = a.H, W = a.W, pitch = a.pitch;
@@ -271,72 +382,102 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
     const T *P1 = static_cast<const T *>(a.P1);
     const T *P2 = static_cast<const T *>(a.P2);
 
-    // phase 0: stage both frames (rows sy0 .. sy0+SH-1, columns sx0 .. sx0+SP-1)
-    // 16-byte chunks inside the image rows are copied asynchronously; chunks
-    // that straddle the left or right border are filled element by element
-    // with clamped columns.  Rows are clamped as a whole.
+    // phase 0: stage both frames (rows sy0 .. sy0+SH-1, columns sx0 .. sx0+SP-1).
+    // A box inside the image: two TMA copies.  Otherwise 16-byte chunks
+    // inside the image rows are copied asynchronously; chunks that straddle
+    // the left or right border are filled element by element with clamped
+    // columns.  Rows are clamped as a whole.
     const bool vec_ok = sx0 >= 0 && sx0 + SP <= W;
-    for (int t = tid; t < 2 * SH * NV; t += NT) {
-        const int f = t >= SH * NV ? 1 : 0;
-        const int r = t - f * SH * NV;
-        const int row = r / NV, v = r - row * NV;
-        const int gy = min(max(sy0 + row, 0), H - 1);
-        const int gx0 = sx0 + v * VEC;
-        const T *src = (f ? P2 : P1) + (int64_t)gy * pitch;
-        T *dst = stage + (f * SH + row) * SP + v * VEC;
-        if (gx0 >= 0 && gx0 + VEC <= W) {
-            cp_async16(dst, src + gx0);
-        } else {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) dst[e] = src[min(max(gx0 + e, 0), W - 1)];
+    const bool interior = vec_ok && sy0 >= 0 && sy0 + SH <= H;
+    if (tm1 != nullptr && interior && (smem_u32(stage) & 127u) == 0) {
+        __shared__ __align__(8) uint64_t s_bar;
+        if (tid == 0) mbar_init(&s_bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(&s_bar, (unsigned)(2 * SH * SP * sizeof(T)));
+            tma_load_2d(stage, tm1, sx0, sy0, &s_bar);
+            tma_load_2d(stage + STG, tm2, sx0, sy0, &s_bar);
         }
+        const bool ok = mbar_wait_bounded(&s_bar, 0, 2000000000LL);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not complete in 2 s: report, give the copies one
+            // more bounded wait, and leave the tile unwritten
+            if (tid == 0 && err) atomicExch(err, 1);
+            mbar_wait_bounded(&s_bar, 0, 1000000000LL);
+            return;
+        }
+    } else {
+        for (int t = tid; t < 2 * SH * NV; t += NT) {
+            const int f = t >= SH * NV ? 1 : 0;
+            const int r = t - f * SH * NV;
+            const int row = r / NV, v = r - row * NV;
+            const int gy = min(max(sy0 + row, 0), H - 1);
+            const int gx0 = sx0 + v * VEC;
+            const T *src = (f ? P2 : P1) + (int64_t)gy * pitch;
+            T *dst = stage + f * STG + row * SP + v * VEC;
+            if (gx0 >= 0 && gx0 + VEC <= W) {
+                cp_async16(dst, src + gx0);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) dst[e] = src[min(max(gx0 + e, 0), W - 1)];
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
     }
-    cp_async_wait_all();
-    __syncthreads();
 
     // phase 1: products on tile + halo.  A tile whose staged rows and columns
     // all lie inside the image needs no clamping or border remap.
     // Pixels at least REACH+1 px from every border take the same fast path
     // inside border tiles too (their taps never clamp or remap).
-    const bool interior = vec_ok && sy0 >= 0 && sy0 + SH <= H;
-    constexpr int DY = NT / RW, DX = NT % RW;  // index step in rows and columns
-    int ry = tid / RW, rx = tid - (tid / RW) * RW;
-    // V0 of the thread's next pixel is loaded one iteration ahead
-    float2 V0n = make_float2(0.f, 0.f);
-    if (ry < RW && py0 + ry >= 0 && py0 + ry < H && px0 + rx >= 0 && px0 + rx < W)
-        V0n = fetch_v0_rt<COH>(a, mode, px0 + rx, py0 + ry);
-    for (int idx = tid; idx < RW * RW; idx += NT) {
-        const int gy = py0 + ry, gx = px0 + rx;
-        const float2 V0c = V0n;
-        int nry = ry + DY, nrx = rx + DX;
-        if (nrx >= RW) { nrx -= RW; ++nry; }
-        if (idx + NT < RW * RW && py0 + nry >= 0 && py0 + nry < H && px0 + nrx >= 0 && px0 + nrx < W)
-            V0n = fetch_v0_rt<COH>(a, mode, px0 + nrx, py0 + nry);
-        float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (interior || (gx > kBlockReach && gx < W - kBlockReach - 2 && gy > kBlockReach && gy < H - kBlockReach - 2)) {
-            products_interior<T, SP>(stage, stage + SH * SP, sx0, sy0, a, gx, gy, V0c, p);
-        } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            const float2 V0 = V0c;
-            const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
-            const Sample s1 = sample_staged<T, SP>(stage, sx0, sy0, P1, H, W, pitch, gx, gy, -hx, -hy);
-            const Sample s2 = sample_staged<T, SP>(stage + SH * SP, sx0, sy0, P2, H, W, pitch, gx, gy, hx, hy);
-            const float Gx = 0.5f * (s1.gx + s2.gx), Gy = 0.5f * (s1.gy + s2.gy);
-            const float It = s2.val - s1.val;
-            const float r = Gx * V0.x + Gy * V0.y - It;
-            p[0] = Gx * Gx;
-            p[1] = Gx * Gy;
-            p[2] = Gy * Gy;
-            p[3] = Gx * r;
-            p[4] = Gy * r;
+    if (interior) {
+        const T *st2 = stage + STG;
+        if (mode == V0_SAME)
+            products_tile_interior<T, KR, COH, V0_SAME, SP>(a, stage, st2, sx0, sy0, px0, py0, prod);
+        else if (mode == V0_UP)
+            products_tile_interior<T, KR, COH, V0_UP, SP>(a, stage, st2, sx0, sy0, px0, py0, prod);
+        else
+            products_tile_interior<T, KR, COH, V0_ZERO, SP>(a, stage, st2, sx0, sy0, px0, py0, prod);
+    } else {
+        constexpr int DY = NT / RW, DX = NT % RW;  // index step in rows and columns
+        int ry = tid / RW, rx = tid - (tid / RW) * RW;
+        // V0 of the thread's next pixel is loaded one iteration ahead
+        float2 V0n = make_float2(0.f, 0.f);
+        if (ry < RW && py0 + ry >= 0 && py0 + ry < H && px0 + rx >= 0 && px0 + rx < W)
+            V0n = fetch_v0_rt<COH>(a, mode, px0 + rx, py0 + ry);
+        for (int idx = tid; idx < RW * RW; idx += NT) {
+            const int gy = py0 + ry, gx = px0 + rx;
+            const float2 V0c = V0n;
+            int nry = ry + DY, nrx = rx + DX;
+            if (nrx >= RW) { nrx -= RW; ++nry; }
+            if (idx + NT < RW * RW && py0 + nry >= 0 && py0 + nry < H && px0 + nrx >= 0 && px0 + nrx < W)
+                V0n = fetch_v0_rt<COH>(a, mode, px0 + nrx, py0 + nry);
+            float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            if (gx > kBlockReach && gx < W - kBlockReach - 2 && gy > kBlockReach && gy < H - kBlockReach - 2) {
+                products_interior<T, SP>(stage, stage + STG, sx0, sy0, a, gx, gy, V0c, p);
+            } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                const float2 V0 = V0c;
+                const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
+                const Sample s1 = sample_staged<T, SP>(stage, sx0, sy0, P1, H, W, pitch, gx, gy, -hx, -hy);
+                const Sample s2 = sample_staged<T, SP>(stage + STG, sx0, sy0, P2, H, W, pitch, gx, gy, hx, hy);
+                const float Gx = 0.5f * (s1.gx + s2.gx), Gy = 0.5f * (s1.gy + s2.gy);
+                const float It = s2.val - s1.val;
+                const float r = Gx * V0.x + Gy * V0.y - It;
+                p[0] = Gx * Gx;
+                p[1] = Gx * Gy;
+                p[2] = Gy * Gy;
+                p[3] = Gx * r;
+                p[4] = Gy * r;
+            }
+            float *q = prod + ry * RWP + rx;
+            q[0] = p[0];
+            q[PLANE] = p[1];
+            q[2 * PLANE] = p[2];
+            q[3 * PLANE] = p[3];
+            q[4 * PLANE] = p[4];
+            ry = nry;
+            rx = nrx;
         }
-        float *q = prod + ry * RWP + rx;
-        q[0] = p[0];
-        q[PLANE] = p[1];
-        q[2 * PLANE] = p[2];
-        q[3 * PLANE] = p[3];
-        q[4 * PLANE] = p[4];
-        ry = nry;
-        rx = nrx;
     }
     __syncthreads();
 
@@ -383,8 +524,13 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
 template <typename T, int KR>
 __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __grid_constant__ BlockParams prm)
 {
-    extern __shared__ float4 smem_f4[];
-    block_tile<T, KR, false>(prm.a[blockIdx.z], prm.mode, blockIdx.x, blockIdx.y, smem_f4);
+    extern __shared__ __align__(128) float4 smem_f4[];
+    const int z = blockIdx.z;
+    if (prm.use_tma)
+        block_tile<T, KR, false>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4, &prm.tm[z][0], &prm.tm[z][1],
+                                 prm.err);
+    else
+        block_tile<T, KR, false>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,13 +565,6 @@ struct QueueParams {
     int spin_limit;
 };
 
-__device__ __forceinline__ long long global_ns()
-{
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ __forceinline__ int ld_acquire(const int *p)
 {
     int v;
@@ -440,7 +579,7 @@ template <typename T, int KR>
 __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __grid_constant__ QueueParams q)
 {
     constexpr int TS = BlockShape<KR>::TS;
-    extern __shared__ float4 smem_f4[];
+    extern __shared__ __align__(128) float4 smem_f4[];
     __shared__ int s_unit, s_fail;
     const int S = q.L * q.IT;
     for (;;) {

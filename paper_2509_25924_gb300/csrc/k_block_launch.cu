@@ -1,4 +1,6 @@
 // Host launcher of the block-tiled iteration kernel.
+#include <cstring>
+
 #include "k_block.cuh"
 
 namespace ofv {
@@ -9,16 +11,58 @@ cudaError_t launch_block_bf16(const BlockParams &p, int kr, int npairs, cudaStre
 
 bool block_supports(int kr) { return kr >= 1 && kr <= kBlockMaxKR; }
 
-cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s)
+cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s,
+                              const CUtensorMap *const *tm, int *err)
 {
     if (npairs < 1 || npairs > kBlockMaxBatch || !block_supports(a[0].kr)) return cudaErrorInvalidValue;
     BlockParams p;
+    memset(&p, 0, sizeof p);
     for (int k = 0; k < npairs; ++k) p.a[k] = a[k];
     p.mode = mode;
+    p.err = err;
+    p.use_tma = 0;
+    if (tm) {
+        p.use_tma = 1;
+        for (int k = 0; k < npairs; ++k) {
+            if (!tm[2 * k] || !tm[2 * k + 1]) {
+                p.use_tma = 0;
+                break;
+            }
+            p.tm[k][0] = *tm[2 * k];
+            p.tm[k][1] = *tm[2 * k + 1];
+        }
+    }
     switch (store) {
     case ST_F16: return launch_block_f16(p, a[0].kr, npairs, s);
     case ST_BF16: return launch_block_bf16(p, a[0].kr, npairs, s);
     default: return launch_block_f32(p, a[0].kr, npairs, s);
+    }
+}
+
+namespace {
+template <typename T>
+void box_of(int kr, int *cols, int *rows)
+{
+    switch (kr) {
+#define OFV_BOX_CASE(K)                       \
+    case K:                                   \
+        *cols = StageShape<T, K>::SP;         \
+        *rows = BlockShape<K>::SH;            \
+        return;
+    OFV_BOX_CASE(1) OFV_BOX_CASE(2) OFV_BOX_CASE(3) OFV_BOX_CASE(4) OFV_BOX_CASE(5)
+    OFV_BOX_CASE(6) OFV_BOX_CASE(7) OFV_BOX_CASE(8) OFV_BOX_CASE(9) OFV_BOX_CASE(10)
+#undef OFV_BOX_CASE
+    default: *cols = *rows = 0;
+    }
+}
+}  // namespace
+
+void block_stage_box(int store, int kr, int *cols, int *rows)
+{
+    switch (store) {
+    case ST_F16: box_of<__half>(kr, cols, rows); break;
+    case ST_BF16: box_of<__nv_bfloat16>(kr, cols, rows); break;
+    default: box_of<float>(kr, cols, rows); break;
     }
 }
 

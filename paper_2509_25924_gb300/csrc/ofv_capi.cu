@@ -7,6 +7,7 @@
 // iteration) of the fused path is one launch over all of them, which keeps
 // the coarse levels from leaving the GPU idle.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -132,6 +133,55 @@ struct ProfScope {
     }
 };
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to
+// the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor maps of the level images for the block kernel's staged box: 2-D,
+// W x H elements, row stride pitch * element bytes, no swizzle.  Levels
+// smaller than the box never have an interior tile and keep cp.async.
+void encode_tensor_maps(ofv_handle *h)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    int cols = 0, rows = 0;
+    block_stage_box(h->p.storage, h->p.kernel_radius, &cols, &rows);
+    const CUtensorMapDataType dt = h->p.storage == OFV_STORE_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : h->p.storage == OFV_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const int sb = store_bytes(h->p.storage);
+    for (int l = 0; l < h->L; ++l) {
+        h->tma_ok[l] = 0;
+        if (!enc || cols < 1 || h->Ws[l] < cols || h->Hs[l] < rows) continue;
+        bool ok = true;
+        for (int f = 0; f < h->nslots && ok; ++f) {
+            const cuuint64_t dim[2] = {(cuuint64_t)h->Ws[l], (cuuint64_t)h->Hs[l]};
+            const cuuint64_t stride[1] = {(cuuint64_t)h->pitch[l] * sb};
+            const cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)rows};
+            const cuuint32_t estr[2] = {1, 1};
+            ok = enc(&h->tmap[f][l], dt, 2, h->lvl[f][l], dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        h->tma_ok[l] = ok ? 1 : 0;
+    }
+}
+
 // Steps 1-2: ingest nf frames (frames[k] into pyramid slot slots[k]) and
 // reduce them, nf frames per launch.
 ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s)
@@ -234,7 +284,13 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
             ProfScope ps(h, s, OFV_K_ITERATE, bytes);
             cudaError_t e = cudaSuccess;
             if (p.path == OFV_PATH_FUSED && block_supports(p.kernel_radius)) {
-                e = launch_iter_block(a, np, p.storage, mode, s);
+                const CUtensorMap *tm[2 * kMaxBatch];
+                for (int k = 0; k < np; ++k) {
+                    tm[2 * k] = &h->tmap[s1[k]][l];
+                    tm[2 * k + 1] = &h->tmap[s2[k]][l];
+                }
+                const bool use = h->tma_ok[l] && h->tma_err_d;
+                e = launch_iter_block(a, np, p.storage, mode, s, use ? tm : nullptr, h->tma_err_d);
             } else {
                 for (int k = 0; k < np && e == cudaSuccess; ++k)
                     e = p.path == OFV_PATH_PLAIN ? launch_iter_plain(a[k], h->plain, p.storage, mode, s)
@@ -249,8 +305,10 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
     return OFV_OK;
 }
 
-ofv_status pending_error(const char *where)
+ofv_status pending_error(const ofv_handle *h, const char *where)
 {
+    if (h->tma_err_h && *static_cast<volatile int *>(h->tma_err_h))
+        return fail(OFV_ERR_TIMEOUT, "%s: a TMA copy of an earlier launch did not complete", where);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -410,6 +468,19 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
     }
     h->last_s1 = 0;
     h->last_s2 = 1;
+    if (p->path == OFV_PATH_FUSED && block_supports(p->kernel_radius)) {
+        // TMA staging of interior tiles: the error word and one tensor map
+        // per (slot, level); a level whose map cannot be made keeps cp.async
+        if (cudaHostAlloc(reinterpret_cast<void **>(&h->tma_err_h), sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->tma_err_d), h->tma_err_h, 0) == cudaSuccess) {
+            *h->tma_err_h = 0;
+            encode_tensor_maps(h);
+        } else {
+            cudaGetLastError();
+            if (h->tma_err_h) cudaFreeHost(h->tma_err_h);
+            h->tma_err_h = h->tma_err_d = nullptr;
+        }
+    }
     *out = h;
     return OFV_OK;
 }
@@ -425,6 +496,7 @@ ofv_status ofv_destroy(ofv_handle *h)
     if (h->stage) cudaFree(h->stage);
     if (h->batch_arena) cudaFree(h->batch_arena);
     if (h->bw_arena) cudaFree(h->bw_arena);
+    if (h->tma_err_h) cudaFreeHost(h->tma_err_h);
     if (h->hs_stage) cudaFree(h->hs_stage);
     if (h->hs_ready) {
         for (int r = 0; r < kHostRing; ++r)
@@ -453,7 +525,7 @@ ofv_status ofv_compute(ofv_handle *h, const void *I1, const void *I2, float *u, 
     if (u == v) return fail(OFV_ERR_INVALID_ARG, "u and v must be distinct buffers");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
-    ofv_status st = pending_error("error pending before ofv_compute");
+    ofv_status st = pending_error(h, "error pending before ofv_compute");
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
     const void *fr[2] = {I1, I2};
@@ -514,7 +586,7 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
     if (field_stride < N) return fail(OFV_ERR_INVALID_ARG, "field_stride=%zu is smaller than one field", field_stride);
     DeviceGuard g(h->device);
     if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
-    ofv_status st = pending_error("error pending before ofv_compute_sequence");
+    ofv_status st = pending_error(h, "error pending before ofv_compute_sequence");
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
     const char *fb = static_cast<const char *>(frames);
@@ -565,7 +637,7 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
     if (field_stride < N) return fail(OFV_ERR_INVALID_ARG, "field_stride=%zu is smaller than one field", field_stride);
     DeviceGuard g(h->device);
     if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
-    ofv_status st = pending_error("error pending before ofv_compute_sequence_host");
+    ofv_status st = pending_error(h, "error pending before ofv_compute_sequence_host");
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
     const int B = h->B, NS = h->nslots;

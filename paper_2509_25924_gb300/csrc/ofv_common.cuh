@@ -1,6 +1,7 @@
 // Shared device helpers and launch descriptors of the OFV CUDA path.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -60,8 +61,15 @@ struct IterArgs {
 // Tile kernel: one CTA per 32x32 output tile, products staged in shared memory.
 cudaError_t launch_iter_fused(const IterArgs &a, int store, int mode, cudaStream_t s);
 // Block-tiled kernel (KR 1..10): npairs pairs of equal level size in one launch.
+// tm (optional): 2 * npairs tensor maps (frame 1 and frame 2 of pair k at
+// 2k, 2k+1) of the level images with the box of block_stage_box; tiles whose
+// staged box lies inside the image are then loaded by TMA.  err (optional):
+// device-visible word set to 1 if a TMA wait expires.
 bool block_supports(int kr);
-cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s);
+cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s,
+                              const CUtensorMap *const *tm = nullptr, int *err = nullptr);
+// Staged box (columns, rows) of the block kernel for this storage and radius.
+void block_stage_box(int store, int kr, int *cols, int *rows);
 
 struct PlainBufs {
     float *prod;  // 5 planes, each H x pitch floats

@@ -75,6 +75,12 @@ struct ofv_handle {
     // reverse mode: grow-only workspace (stage fields, sums, gradients)
     void *bw_arena;
     size_t bw_bytes;
+    // TMA tensor maps of every (slot, level) image for the block kernel's
+    // staged box, and the word a kernel sets when a TMA wait expires
+    // (page-locked host memory mapped into the device)
+    CUtensorMap tmap[ofv::kMaxSlots][ofv::kMaxLevels];
+    int tma_ok[ofv::kMaxLevels];
+    int *tma_err_h, *tma_err_d;
     // host-memory sequence pipeline: copy streams, ring events, device ring
     cudaStream_t hs_stream[2];            // [0] host-to-device, [1] device-to-host
     cudaEvent_t hs_ev[ofv::kHostRing][3];  // per ring slot: frames in, fields ready, fields out
