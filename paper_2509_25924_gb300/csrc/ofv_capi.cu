@@ -184,7 +184,8 @@ void encode_tensor_maps(ofv_handle *h)
 
 // Steps 1-2: ingest nf frames (frames[k] into pyramid slot slots[k]) and
 // reduce them, nf frames per launch.
-ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s)
+ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s,
+                          int tset = 0)
 {
     const ofv_params &p = h->p;
     const int sb = store_bytes(p.storage), ib = input_bytes(p.input);
@@ -193,7 +194,7 @@ ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *s
         IngestArgs &a = ia[k];
         a.raw = frames[k];
         a.out = h->lvl[slots[k]][0];
-        a.tmp = h->tmp[k];
+        a.tmp = h->tmp[tset * kMaxFramesPerLaunch + k];
         a.w25 = h->w25;
         a.H = h->H;
         a.W = h->W;
@@ -234,10 +235,11 @@ ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *s
 // Steps 3-6 for np pairs: pair k uses pyramid slots s1[k], s2[k], field
 // buffers vbuf[2k], vbuf[2k+1], and writes u[k], v[k].
 ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float *const *u, float *const *v,
-                      cudaStream_t s)
+                      cudaStream_t s, int vset = 0)
 {
     const ofv_params &p = h->p;
     const int sb = store_bytes(p.storage);
+    float2 *const *vbuf = h->vbuf + 2 * h->B * vset;
     int cur = 0;  // vbuf[2k + cur] holds the latest field of pair k
     bool have = false;
     for (int l = h->L - 1; l >= 0; --l) {
@@ -263,17 +265,17 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
                 x.eps_rel = p.det_rel_eps;
                 x.eps_abs = p.det_abs_eps;
                 if (mode == V0_UP) {
-                    x.Vc = h->vbuf[2 * k + cur];
+                    x.Vc = vbuf[2 * k + cur];
                     x.Hc = h->Hs[l + 1];
                     x.Wc = h->Ws[l + 1];
                 } else if (mode == V0_SAME) {
-                    x.V0 = h->vbuf[2 * k + cur];
+                    x.V0 = vbuf[2 * k + cur];
                 }
                 if (last) {
                     x.u_out = u[k];
                     x.v_out = v[k];
                 } else {
-                    x.Vout = h->vbuf[2 * k + nxt];
+                    x.Vout = vbuf[2 * k + nxt];
                 }
             }
             const double Nl = (double)h->Hs[l] * h->Ws[l];
@@ -304,6 +306,89 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
     }
     return OFV_OK;
 }
+
+// The groups of a time-resolved sequence: group g holds pairs f0 .. f0+np-1
+// (frames f0 .. f0+np, f0 = g B).  Frame f lives in pyramid slot f mod NS;
+// group g ingests its frames except f0, whose pyramid group g-1 built.
+//
+// With two group streams (NS = 2B + 1), group g runs on stream g mod 2 with
+// field buffers and pre-filter scratch of that stream, so the coarse levels
+// of one group overlap the fine levels of the other.  Group g waits for the
+// pyramids of group g-1 (frame f0) before its iterations, and before
+// ingesting for group g-3, whose frames' slots it reuses (group g-2 ran
+// before it on its own stream).  One stream: everything in order on the
+// caller's stream (also while kernel timing is on, so that launch events
+// time single kernels).
+struct GroupRunner {
+    ofv_handle *h;
+    cudaStream_t s;
+    bool two;
+    int last = -1;
+    GroupRunner(ofv_handle *h_, cudaStream_t s_) : h(h_), s(s_), two(h_->nstreams == 2 && !h_->prof) {}
+
+    cudaStream_t stream_of(int g) const { return two ? h->gs[g & 1] : s; }
+
+    ofv_status begin()
+    {
+        if (!two) return OFV_OK;
+        cudaError_t e = cudaEventRecord(h->gstart, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gs[0], h->gstart, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gs[1], h->gstart, 0);
+        return e == cudaSuccess ? OFV_OK : cuda_fail(e, "ordering the group streams");
+    }
+
+    // fr[k] = frame f0 + k (k = 0 .. np), device pointers; before_ingest
+    // (optional) is an event the group's stream waits for first
+    ofv_status group(int g, int f0, int np, const void *const *fr, float *const *uu, float *const *vv,
+                     cudaEvent_t before_ingest = nullptr)
+    {
+        const int NS = h->nslots;
+        cudaStream_t cs = stream_of(g);
+        cudaError_t e = cudaSuccess;
+        if (two && g >= 3) e = cudaStreamWaitEvent(cs, h->gev[(g - 3) & 3][1], 0);
+        if (e == cudaSuccess && before_ingest) e = cudaStreamWaitEvent(cs, before_ingest, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
+        const void *nfr[kMaxSlots];
+        int slots[kMaxSlots];
+        int nf = 0;
+        for (int f = (f0 == 0 ? 0 : f0 + 1); f <= f0 + np; ++f) {
+            nfr[nf] = fr[f - f0];
+            slots[nf] = f % NS;
+            ++nf;
+        }
+        ofv_status st = build_pyramids(h, nfr, slots, nf, cs, two ? (g & 1) : 0);
+        if (st != OFV_OK) return st;
+        if (two) {
+            e = cudaEventRecord(h->gev[g & 3][0], cs);
+            if (e == cudaSuccess && g >= 1) e = cudaStreamWaitEvent(cs, h->gev[(g - 1) & 3][0], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
+        }
+        int s1[kMaxBatch], s2[kMaxBatch];
+        for (int k = 0; k < np; ++k) {
+            s1[k] = (f0 + k) % NS;
+            s2[k] = (f0 + k + 1) % NS;
+        }
+        st = run_levels(h, np, s1, s2, uu, vv, cs, two ? (g & 1) : 0);
+        if (st != OFV_OK) return st;
+        if (two) {
+            e = cudaEventRecord(h->gev[g & 3][1], cs);
+            if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
+        }
+        h->last_s1 = s1[np - 1];
+        h->last_s2 = s2[np - 1];
+        last = g;
+        return OFV_OK;
+    }
+
+    // the caller's stream waits for the last two groups
+    ofv_status end()
+    {
+        if (!two || last < 0) return OFV_OK;
+        cudaError_t e = cudaStreamWaitEvent(s, h->gev[last & 3][1], 0);
+        if (e == cudaSuccess && last >= 1) e = cudaStreamWaitEvent(s, h->gev[(last - 1) & 3][1], 0);
+        return e == cudaSuccess ? OFV_OK : cuda_fail(e, "joining the group streams");
+    }
+};
 
 ofv_status pending_error(const ofv_handle *h, const char *where)
 {
@@ -395,7 +480,10 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
         const long long b = (16LL << 20) / ((long long)H * W);
         h->B = (int)(b < 1 ? 1 : (b > kMaxBatch ? kMaxBatch : b));
     }
-    h->nslots = h->B + 1;
+    // two streams for the groups of a sequence (fused path): the coarse
+    // levels of one group overlap the finer levels of the other
+    h->nstreams = p->path == OFV_PATH_FUSED ? 2 : 1;
+    h->nslots = h->nstreams == 2 ? 2 * h->B + 1 : h->B + 1;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return fail(OFV_ERR_CUDA, "cudaGetDevice failed");
@@ -416,16 +504,16 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
             lvl_off[f][l] = off;
             off = align_up(off + (size_t)Hs[l] * h->pitch[l] * sb, 256);
         }
-    size_t vb_off[2 * kMaxBatch];
-    for (int k = 0; k < 2 * h->B; ++k) {
+    size_t vb_off[4 * kMaxBatch];
+    for (int k = 0; k < 2 * h->B * h->nstreams; ++k) {
         vb_off[k] = off;
         off = align_up(off + (size_t)H * h->vpitch * sizeof(float2), 256);
     }
     const size_t w_off = off;
     off = align_up(off + 25 * sizeof(float), 256);
-    size_t tmp_off[kMaxSlots] = {};
+    size_t tmp_off[2 * kMaxFramesPerLaunch] = {};
     if (p->prefilter)
-        for (int k = 0; k < h->nslots; ++k) {
+        for (int k = 0; k < (h->B + 1) * h->nstreams; ++k) {
             tmp_off[k] = off;
             off = align_up(off + (size_t)H * h->pitch[0] * sizeof(float), 256);
         }
@@ -449,9 +537,12 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
     char *base = static_cast<char *>(h->arena);
     for (int f = 0; f < h->nslots; ++f)
         for (int l = 0; l < L; ++l) h->lvl[f][l] = base + lvl_off[f][l];
-    for (int k = 0; k < 2 * h->B; ++k) h->vbuf[k] = reinterpret_cast<float2 *>(base + vb_off[k]);
+    for (int k = 0; k < 2 * h->B * h->nstreams; ++k) h->vbuf[k] = reinterpret_cast<float2 *>(base + vb_off[k]);
     h->w25 = reinterpret_cast<float *>(base + w_off);
-    for (int k = 0; k < h->nslots; ++k) h->tmp[k] = p->prefilter ? reinterpret_cast<float *>(base + tmp_off[k]) : nullptr;
+    for (int t = 0; t < h->nstreams; ++t)
+        for (int k = 0; k <= h->B; ++k)
+            h->tmp[t * kMaxFramesPerLaunch + k] =
+                p->prefilter ? reinterpret_cast<float *>(base + tmp_off[t * (h->B + 1) + k]) : nullptr;
     if (p->path == OFV_PATH_PLAIN) {
         h->plain.prod = reinterpret_cast<float *>(base + prod_off);
         h->plain.hsum = reinterpret_cast<float *>(base + hsum_off);
@@ -468,6 +559,19 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
     }
     h->last_s1 = 0;
     h->last_s2 = 1;
+    if (h->nstreams == 2) {
+        e = cudaStreamCreateWithFlags(&h->gs[0], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gs[1], cudaStreamNonBlocking);
+        for (int r = 0; r < 4 && e == cudaSuccess; ++r)
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+                e = cudaEventCreateWithFlags(&h->gev[r][k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gstart, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ofv_destroy(h);  // frees what was made
+            return fail(OFV_ERR_CUDA, "creating the group streams");
+        }
+    }
     if (p->path == OFV_PATH_FUSED && block_supports(p->kernel_radius)) {
         // TMA staging of interior tiles: the error word and one tensor map
         // per (slot, level); a level whose map cannot be made keeps cp.async
@@ -497,6 +601,12 @@ ofv_status ofv_destroy(ofv_handle *h)
     if (h->batch_arena) cudaFree(h->batch_arena);
     if (h->bw_arena) cudaFree(h->bw_arena);
     if (h->tma_err_h) cudaFreeHost(h->tma_err_h);
+    for (int k = 0; k < 2; ++k)
+        if (h->gs[k]) cudaStreamDestroy(h->gs[k]);
+    for (int r = 0; r < 4; ++r)
+        for (int k = 0; k < 2; ++k)
+            if (h->gev[r][k]) cudaEventDestroy(h->gev[r][k]);
+    if (h->gstart) cudaEventDestroy(h->gstart);
     if (h->hs_stage) cudaFree(h->hs_stage);
     if (h->hs_ready) {
         for (int r = 0; r < kHostRing; ++r)
@@ -590,37 +700,21 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
     const char *fb = static_cast<const char *>(frames);
-    const int B = h->B, NS = h->nslots;
     const int npairs = n_frames - 1;
-    // Frame f lives in slot f mod (B+1).  A group of up to B pairs (frames
-    // f0 .. f0+np) reuses the pyramid of its first frame, which the previous
-    // group built; the other slots held frames of the previous group only.
-    for (int f0 = 0; f0 < npairs; f0 += B) {
-        const int np = npairs - f0 < B ? npairs - f0 : B;
+    GroupRunner gr(h, cs);
+    if ((st = gr.begin()) != OFV_OK) return st;
+    for (int f0 = 0, g = 0; f0 < npairs; f0 += h->B, ++g) {
+        const int np = npairs - f0 < h->B ? npairs - f0 : h->B;
         const void *fr[kMaxSlots];
-        int slots[kMaxSlots];
-        int nf = 0;
-        for (int f = (f0 == 0 ? 0 : f0 + 1); f <= f0 + np; ++f) {
-            fr[nf] = fb + (size_t)f * frame_stride_bytes;
-            slots[nf] = f % NS;
-            ++nf;
-        }
-        st = build_pyramids(h, fr, slots, nf, cs);
-        if (st != OFV_OK) return st;
-        int s1[kMaxBatch], s2[kMaxBatch];
+        for (int f = f0; f <= f0 + np; ++f) fr[f - f0] = fb + (size_t)f * frame_stride_bytes;
         float *uu[kMaxBatch], *vv[kMaxBatch];
         for (int k = 0; k < np; ++k) {
-            s1[k] = (f0 + k) % NS;
-            s2[k] = (f0 + k + 1) % NS;
             uu[k] = u + (size_t)(f0 + k) * field_stride;
             vv[k] = v + (size_t)(f0 + k) * field_stride;
         }
-        st = run_levels(h, np, s1, s2, uu, vv, cs);
-        if (st != OFV_OK) return st;
-        h->last_s1 = s1[np - 1];
-        h->last_s2 = s2[np - 1];
+        if ((st = gr.group(g, f0, np, fr, uu, vv)) != OFV_OK) return st;
     }
-    return OFV_OK;
+    return gr.end();
 }
 
 ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *frames, size_t frame_stride_bytes,
@@ -640,7 +734,7 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
     ofv_status st = pending_error(h, "error pending before ofv_compute_sequence_host");
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
-    const int B = h->B, NS = h->nslots;
+    const int B = h->B;
     // device ring: per slot B+1 frames and B fields (u and v)
     const size_t in_b = align_up(fb * (size_t)(B + 1), 256);
     const size_t out_b = align_up(N * sizeof(float) * (size_t)B, 256);
@@ -679,9 +773,12 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
     if (e == cudaSuccess) e = cudaStreamWaitEvent(down, h->hs_ev[0][1], 0);
     if (e != cudaSuccess) return cuda_fail(e, "ordering the copy streams");
     // Group c (pairs c*B .. c*B+np-1) uses ring slot c mod kHostRing: its
-    // new frames go up on stream `up`, the group runs on s, its fields come
-    // down on stream `down`.  A slot is reused once the group that last used
-    // it has finished on s (frames) and gone down (fields).
+    // new frames go up on stream `up`, the group runs on its group stream
+    // (GroupRunner), its fields come down on stream `down`.  A slot is
+    // reused once the group that last used it has finished (frames) and
+    // gone down (fields).
+    GroupRunner gr(h, cs);
+    if ((st = gr.begin()) != OFV_OK) return st;
     int c = 0;
     for (int f0 = 0; f0 < npairs; f0 += B, ++c) {
         const int r = c % kHostRing;
@@ -690,7 +787,7 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
         float *du = reinterpret_cast<float *>(slot + in_b), *dv = reinterpret_cast<float *>(slot + in_b + out_b);
         const int fa = f0 == 0 ? 0 : f0 + 1, fz = f0 + np;  // frames to ingest
         if (c >= kHostRing) {
-            e = cudaStreamWaitEvent(up, h->hs_ev[r][1], 0);  // group c - kHostRing done on s
+            e = cudaStreamWaitEvent(up, h->hs_ev[r][1], 0);  // group c - kHostRing done
             if (e != cudaSuccess) return cuda_fail(e, "ordering the frame upload");
         }
         if (frame_stride_bytes == fb) {
@@ -700,33 +797,21 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
                 e = cudaMemcpyAsync(slot + (size_t)(f - fa) * fb, hf + (size_t)f * frame_stride_bytes, fb,
                                     cudaMemcpyHostToDevice, up);
         }
+        cudaStream_t gsc = gr.stream_of(c);
         if (e == cudaSuccess) e = cudaEventRecord(h->hs_ev[r][0], up);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->hs_ev[r][0], 0);
-        if (e == cudaSuccess && c >= kHostRing) e = cudaStreamWaitEvent(cs, h->hs_ev[r][2], 0);  // fields gone down
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(gsc, h->hs_ev[r][0], 0);
+        if (e == cudaSuccess && c >= kHostRing) e = cudaStreamWaitEvent(gsc, h->hs_ev[r][2], 0);  // fields gone down
         if (e != cudaSuccess) return cuda_fail(e, "uploading frames");
         const void *fr[kMaxSlots];
-        int slots[kMaxSlots];
-        int nf = 0;
-        for (int f = fa; f <= fz; ++f) {
-            fr[nf] = slot + (size_t)(f - fa) * fb;
-            slots[nf] = f % NS;
-            ++nf;
-        }
-        st = build_pyramids(h, fr, slots, nf, cs);
-        if (st != OFV_OK) return st;
-        int s1[kMaxBatch], s2[kMaxBatch];
+        fr[0] = nullptr;  // frame f0 > 0 is already in its pyramid slot
+        for (int f = fa; f <= fz; ++f) fr[f - f0] = slot + (size_t)(f - fa) * fb;
         float *uu[kMaxBatch], *vv[kMaxBatch];
         for (int k = 0; k < np; ++k) {
-            s1[k] = (f0 + k) % NS;
-            s2[k] = (f0 + k + 1) % NS;
             uu[k] = du + (size_t)k * N;
             vv[k] = dv + (size_t)k * N;
         }
-        st = run_levels(h, np, s1, s2, uu, vv, cs);
-        if (st != OFV_OK) return st;
-        h->last_s1 = s1[np - 1];
-        h->last_s2 = s2[np - 1];
-        e = cudaEventRecord(h->hs_ev[r][1], cs);
+        if ((st = gr.group(c, f0, np, fr, uu, vv)) != OFV_OK) return st;
+        e = cudaEventRecord(h->hs_ev[r][1], gsc);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(down, h->hs_ev[r][1], 0);
         if (e == cudaSuccess) {
             if (field_stride == N) {
@@ -747,6 +832,7 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
         if (e != cudaSuccess) return cuda_fail(e, "downloading fields");
     }
     // s reaches its end only after the last fields are in host memory
+    if ((st = gr.end()) != OFV_OK) return st;
     e = cudaStreamWaitEvent(cs, h->hs_ev[(c - 1) % kHostRing][2], 0);
     if (e != cudaSuccess) return cuda_fail(e, "joining the copy streams");
     return OFV_OK;
