@@ -85,8 +85,8 @@ typedef struct {
     float det_abs_eps;  /* guard: keep V0 where Sxx + Syy <= eps (default 1e-20) */
     float norm_eps;     /* normalization floor: (I - mu) / sqrt(var + eps^2) (default 1e-2) */
     int max_batch;      /* pairs of a sequence per iteration launch, 0..8; 0 = auto (as many as keep
-                           about 16 Mp per launch).  Each costs one more pyramid and two fields of
-                           workspace. */
+                           about 16 Mp per launch).  Each costs three more pyramids and six fields
+                           of workspace (three groups of a sequence are in flight). */
 } ofv_params;
 
 typedef struct ofv_handle ofv_handle;
@@ -129,7 +129,11 @@ ofv_status ofv_compute_host(ofv_handle *h, const void *I1, const void *I2, float
    frames + k * frame_stride_bytes (device), give n_frames - 1 fields, pair
    k = (F_k, F_{k+1}), written to u + k * field_stride and v + k * field_stride
    (elements).  Each frame is normalized and reduced once and its pyramid is
-   reused by the two pairs it belongs to. */
+   reused by the two pairs it belongs to.  Pairs run in groups of the
+   handle's pairs-per-launch; with the fused path consecutive groups run on
+   library-owned streams so that one group's coarse levels overlap another's
+   fine levels.  Work queued on s before the call runs first, and s reaches
+   the end of the call only when every field is written. */
 ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
                                 size_t frame_stride_bytes, float *u, float *v, size_t field_stride,
                                 ofv_stream_t s);
@@ -138,9 +142,9 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
    page-locked memory for the copies to overlap).  The sequence runs in
    groups of the handle's pairs-per-launch; each frame is uploaded once, and
    the upload of the next group and the download of the previous group's
-   fields run on two library-owned copy streams while the current group
-   computes on s.  A device ring of 3 groups (frames and fields) is
-   allocated on first use and kept.  Work queued on s before the call runs
+   fields run on two library-owned copy streams while the groups compute
+   (as in ofv_compute_sequence).  A device ring of groups (frames and
+   fields) is allocated on first use and kept.  Work queued on s before the call runs
    first; the host outputs are valid once s has been synchronised. */
 ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *frames,
                                      size_t frame_stride_bytes, float *u, float *v,

@@ -311,29 +311,29 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
 // (frames f0 .. f0+np, f0 = g B).  Frame f lives in pyramid slot f mod NS;
 // group g ingests its frames except f0, whose pyramid group g-1 built.
 //
-// With two group streams (NS = 2B + 1), group g runs on stream g mod 2 with
+// With K group streams (NS = K B + 1), group g runs on stream g mod K with
 // field buffers and pre-filter scratch of that stream, so the coarse levels
-// of one group overlap the fine levels of the other.  Group g waits for the
-// pyramids of group g-1 (frame f0) before its iterations, and before
-// ingesting for group g-3, whose frames' slots it reuses (group g-2 ran
-// before it on its own stream).  One stream: everything in order on the
-// caller's stream (also while kernel timing is on, so that launch events
-// time single kernels).
+// of one group overlap the fine levels of the others.  Group g waits for
+// the pyramids of group g-1 (frame f0) before its iterations, and before
+// ingesting for group g-K-1, whose last frame's slot it reuses (the other
+// reused slots belong to group g-K, which ran before it on its own stream).
+// One stream: everything in order on the caller's stream (also while kernel
+// timing is on, so that launch events time single kernels).
 struct GroupRunner {
     ofv_handle *h;
     cudaStream_t s;
-    bool two;
+    int K;  // group streams in use (1: the caller's stream)
     int last = -1;
-    GroupRunner(ofv_handle *h_, cudaStream_t s_) : h(h_), s(s_), two(h_->nstreams == 2 && !h_->prof) {}
+    GroupRunner(ofv_handle *h_, cudaStream_t s_) : h(h_), s(s_), K(h_->prof ? 1 : h_->nstreams) {}
 
-    cudaStream_t stream_of(int g) const { return two ? h->gs[g & 1] : s; }
+    cudaStream_t stream_of(int g) const { return K > 1 ? h->gs[g % K] : s; }
+    static int ev(int g) { return g & (kGroupEvents - 1); }
 
     ofv_status begin()
     {
-        if (!two) return OFV_OK;
+        if (K == 1) return OFV_OK;
         cudaError_t e = cudaEventRecord(h->gstart, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gs[0], h->gstart, 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gs[1], h->gstart, 0);
+        for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(h->gs[k], h->gstart, 0);
         return e == cudaSuccess ? OFV_OK : cuda_fail(e, "ordering the group streams");
     }
 
@@ -345,7 +345,7 @@ struct GroupRunner {
         const int NS = h->nslots;
         cudaStream_t cs = stream_of(g);
         cudaError_t e = cudaSuccess;
-        if (two && g >= 3) e = cudaStreamWaitEvent(cs, h->gev[(g - 3) & 3][1], 0);
+        if (K > 1 && g >= K + 1) e = cudaStreamWaitEvent(cs, h->gev[ev(g - K - 1)][1], 0);
         if (e == cudaSuccess && before_ingest) e = cudaStreamWaitEvent(cs, before_ingest, 0);
         if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
         const void *nfr[kMaxSlots];
@@ -356,11 +356,11 @@ struct GroupRunner {
             slots[nf] = f % NS;
             ++nf;
         }
-        ofv_status st = build_pyramids(h, nfr, slots, nf, cs, two ? (g & 1) : 0);
+        ofv_status st = build_pyramids(h, nfr, slots, nf, cs, g % K);
         if (st != OFV_OK) return st;
-        if (two) {
-            e = cudaEventRecord(h->gev[g & 3][0], cs);
-            if (e == cudaSuccess && g >= 1) e = cudaStreamWaitEvent(cs, h->gev[(g - 1) & 3][0], 0);
+        if (K > 1) {
+            e = cudaEventRecord(h->gev[ev(g)][0], cs);
+            if (e == cudaSuccess && g >= 1) e = cudaStreamWaitEvent(cs, h->gev[ev(g - 1)][0], 0);
             if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
         }
         int s1[kMaxBatch], s2[kMaxBatch];
@@ -368,10 +368,10 @@ struct GroupRunner {
             s1[k] = (f0 + k) % NS;
             s2[k] = (f0 + k + 1) % NS;
         }
-        st = run_levels(h, np, s1, s2, uu, vv, cs, two ? (g & 1) : 0);
+        st = run_levels(h, np, s1, s2, uu, vv, cs, g % K);
         if (st != OFV_OK) return st;
-        if (two) {
-            e = cudaEventRecord(h->gev[g & 3][1], cs);
+        if (K > 1) {
+            e = cudaEventRecord(h->gev[ev(g)][1], cs);
             if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
         }
         h->last_s1 = s1[np - 1];
@@ -380,12 +380,13 @@ struct GroupRunner {
         return OFV_OK;
     }
 
-    // the caller's stream waits for the last two groups
+    // the caller's stream waits for the last K groups
     ofv_status end()
     {
-        if (!two || last < 0) return OFV_OK;
-        cudaError_t e = cudaStreamWaitEvent(s, h->gev[last & 3][1], 0);
-        if (e == cudaSuccess && last >= 1) e = cudaStreamWaitEvent(s, h->gev[(last - 1) & 3][1], 0);
+        if (K == 1 || last < 0) return OFV_OK;
+        cudaError_t e = cudaSuccess;
+        for (int g = last; g >= 0 && g > last - K && e == cudaSuccess; --g)
+            e = cudaStreamWaitEvent(s, h->gev[ev(g)][1], 0);
         return e == cudaSuccess ? OFV_OK : cuda_fail(e, "joining the group streams");
     }
 };
@@ -480,10 +481,10 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
         const long long b = (16LL << 20) / ((long long)H * W);
         h->B = (int)(b < 1 ? 1 : (b > kMaxBatch ? kMaxBatch : b));
     }
-    // two streams for the groups of a sequence (fused path): the coarse
-    // levels of one group overlap the finer levels of the other
-    h->nstreams = p->path == OFV_PATH_FUSED ? 2 : 1;
-    h->nslots = h->nstreams == 2 ? 2 * h->B + 1 : h->B + 1;
+    // several streams for the groups of a sequence (fused path): the coarse
+    // levels of one group overlap the finer levels of the others
+    h->nstreams = p->path == OFV_PATH_FUSED ? kGroupStreams : 1;
+    h->nslots = h->nstreams * h->B + 1;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return fail(OFV_ERR_CUDA, "cudaGetDevice failed");
@@ -504,14 +505,14 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
             lvl_off[f][l] = off;
             off = align_up(off + (size_t)Hs[l] * h->pitch[l] * sb, 256);
         }
-    size_t vb_off[4 * kMaxBatch];
+    size_t vb_off[2 * kGroupStreams * kMaxBatch];
     for (int k = 0; k < 2 * h->B * h->nstreams; ++k) {
         vb_off[k] = off;
         off = align_up(off + (size_t)H * h->vpitch * sizeof(float2), 256);
     }
     const size_t w_off = off;
     off = align_up(off + 25 * sizeof(float), 256);
-    size_t tmp_off[2 * kMaxFramesPerLaunch] = {};
+    size_t tmp_off[kGroupStreams * kMaxFramesPerLaunch] = {};
     if (p->prefilter)
         for (int k = 0; k < (h->B + 1) * h->nstreams; ++k) {
             tmp_off[k] = off;
@@ -559,10 +560,10 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
     }
     h->last_s1 = 0;
     h->last_s2 = 1;
-    if (h->nstreams == 2) {
-        e = cudaStreamCreateWithFlags(&h->gs[0], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gs[1], cudaStreamNonBlocking);
-        for (int r = 0; r < 4 && e == cudaSuccess; ++r)
+    if (h->nstreams > 1) {
+        for (int k = 0; k < h->nstreams && e == cudaSuccess; ++k)
+            e = cudaStreamCreateWithFlags(&h->gs[k], cudaStreamNonBlocking);
+        for (int r = 0; r < kGroupEvents && e == cudaSuccess; ++r)
             for (int k = 0; k < 2 && e == cudaSuccess; ++k)
                 e = cudaEventCreateWithFlags(&h->gev[r][k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gstart, cudaEventDisableTiming);
@@ -601,9 +602,9 @@ ofv_status ofv_destroy(ofv_handle *h)
     if (h->batch_arena) cudaFree(h->batch_arena);
     if (h->bw_arena) cudaFree(h->bw_arena);
     if (h->tma_err_h) cudaFreeHost(h->tma_err_h);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < kGroupStreams; ++k)
         if (h->gs[k]) cudaStreamDestroy(h->gs[k]);
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < kGroupEvents; ++r)
         for (int k = 0; k < 2; ++k)
             if (h->gev[r][k]) cudaEventDestroy(h->gev[r][k]);
     if (h->gstart) cudaEventDestroy(h->gstart);

@@ -13,8 +13,10 @@ namespace ofv {
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxBatch = kMaxPairsPerLaunch;
-constexpr int kMaxSlots = 2 * kMaxBatch + 1;  // pyramid slots: two groups of a sequence in flight
-constexpr int kHostRing = 3;  // device ring slots of the host-memory sequence pipeline
+constexpr int kGroupStreams = 3;                  // groups of a sequence in flight
+constexpr int kGroupEvents = 8;                    // event ring (power of 2, > kGroupStreams + 1)
+constexpr int kMaxSlots = kGroupStreams * kMaxBatch + 1;  // pyramid slots
+constexpr int kHostRing = kGroupStreams + 1;  // device ring slots of the host-memory sequence pipeline
 
 struct ProfRec {
     int cls;
@@ -45,21 +47,21 @@ struct ofv_handle {
     ofv_params p;
     int L;
     int B;         // pairs per launch in sequences
-    int nslots;    // pyramid slots (2B + 1 with two group streams, else B + 1)
-    int nstreams;  // 2: consecutive groups of a sequence run on two streams
+    int nslots;    // pyramid slots (nstreams B + 1)
+    int nstreams;  // consecutive groups of a sequence run on this many streams
     int Hs[ofv::kMaxLevels], Ws[ofv::kMaxLevels], pitch[ofv::kMaxLevels];
     int vpitch;
     int device;
     void *arena;
     size_t arena_bytes;
     void *lvl[ofv::kMaxSlots][ofv::kMaxLevels];
-    float2 *vbuf[4 * ofv::kMaxBatch];  // per group stream, two ping-pong fields per pair
+    float2 *vbuf[2 * ofv::kGroupStreams * ofv::kMaxBatch];  // per group stream, two ping-pong fields per pair
     float *w25;
-    float *tmp[2 * ofv::kMaxFramesPerLaunch];  // pre-filter input, per group stream and frame of an ingest launch
+    float *tmp[ofv::kGroupStreams * ofv::kMaxFramesPerLaunch];  // pre-filter input, per group stream and frame
     // group streams of the sequence entry points, and a ring of events:
-    // gev[g % 4][0] = pyramids of group g built, [1] = group g done
-    cudaStream_t gs[2];
-    cudaEvent_t gev[4][2];
+    // gev[g % kGroupEvents][0] = pyramids of group g built, [1] = group g done
+    cudaStream_t gs[ofv::kGroupStreams];
+    cudaEvent_t gev[ofv::kGroupEvents][2];
     cudaEvent_t gstart;
     ofv::PlainBufs plain;
     // host-pointer entry point staging (allocated on first use)
