@@ -187,6 +187,23 @@ def ncu_traffic(workload: str):
     return None
 
 
+def reduce_max(x: float, dist=None, device="cpu") -> float:
+    """Max of a per-rank value over all ranks (the job's time is the slowest
+    rank's); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, seconds_max: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling:
+    every rank runs its own stream of the same size)."""
+    return ws * units_per_rank / seconds_max
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2509_25924_gb300 as ofv
@@ -205,11 +222,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, dev)
 
     stream = torch.cuda.current_stream()
     nframes = args.frames
@@ -243,8 +256,7 @@ def run_ours(args, ws, rank, local):
     clocks = sampler.stop()
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
-    fields_total = ws * npairs * args.steps
-    value = fields_total / (ms_total / 1e3)
+    value = whole_job_rate(npairs * args.steps, ws, ms_total / 1e3)
 
     # dominant kernel: per-launch timing on the same stream over one step
     ofv.ofv_profile_enable(h, True)
@@ -291,6 +303,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_sizes:
         line["sizes"] = sizes(ofv, torch, synth, dev, stream, frames, u, v)
         line["live_21Mp"] = live_loop(ofv, torch, synth, dev, stream)
+        line["paper_perf_set"] = paper_perf_set(ofv, torch, synth, dev, stream)
         line["batched_64_uneven"] = batched_uneven(ofv, torch, synth, dev, stream)
 
     ofv.ofv_destroy(h)
@@ -354,16 +367,16 @@ def e2e(args, ofv, torch, h, frames_h, dev, stream, barrier, max_over_ranks, ws)
     return out
 
 
-def time_sequence(ofv, torch, h, frames, n_frames, H, W, u, v, stream, reps):
+def time_sequence(ofv, torch, h, frames, n_frames, H, W, u, v, stream, reps, in_bytes=2):
     N = H * W
     npairs = n_frames - 1
-    ofv.ofv_compute_sequence(h, n_frames, frames, N * 2, u, v, N, stream)
+    ofv.ofv_compute_sequence(h, n_frames, frames, N * in_bytes, u, v, N, stream)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        ofv.ofv_compute_sequence(h, n_frames, frames, N * 2, u, v, N, stream)
+        ofv.ofv_compute_sequence(h, n_frames, frames, N * in_bytes, u, v, N, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     return npairs * reps / (e0.elapsed_time(e1) / 1e3)
@@ -382,7 +395,7 @@ def sizes(ofv, torch, synth, dev, stream, frames1, u1, v1):
                 fr = synth.stream_frames(H, W, nf, seed=3, ppp=0.1, field=fld, field_max=8.0)
             else:
                 fld, inside = synth.wake_field(H, W)
-                nf, reps = 6, 5
+                nf, reps = 9, 4
                 fr = synth.stream_frames(H, W, nf, seed=4, ppp=0.1, field=fld, field_max=8.0, exclude=inside)
             frames = torch.from_numpy(fr).to(dev)
             u = torch.empty((nf - 1, H, W), dtype=torch.float32, device=dev)
@@ -411,6 +424,33 @@ def sizes(ofv, torch, synth, dev, stream, frames1, u1, v1):
         if kind is not None:
             del frames, u, v
             torch.cuda.empty_cache()
+    return out
+
+
+def paper_perf_set(ofv, torch, synth, dev, stream):
+    """The paper's own benchmark parameters (8-bit input, NR 2, KR 10, IT 3,
+    PSL 0/1/2) on synthetic 8-bit particle streams at 1, 4 and 21 Mp, for
+    context beside its published rates (other hardware)."""
+    out = {}
+    for name, H, W, nf in (("1Mp", 1024, 1024, 41), ("4Mp", 2048, 2048, 17), ("21Mp", 4096, 5120, 9)):
+        fr = synth.stream_frames(H, W, nf, seed=7, ppp=0.05, bits=8).astype(np.uint8)
+        frames = torch.from_numpy(fr).to(dev)
+        u = torch.empty((nf - 1, H, W), dtype=torch.float32, device=dev)
+        v = torch.empty_like(u)
+        res = {}
+        for psl in (0, 1, 2):
+            p = ofv.ofv_default_params(input=ofv.OFV_IN_U8, bit_depth=8, norm_radius=2, kernel_radius=10,
+                                       iterations=3, levels_psl=psl)
+            h = ofv.ofv_create(H, W, p)
+            try:
+                res[f"psl{psl}_fields_per_s"] = time_sequence(ofv, torch, h, frames, nf, H, W, u, v, stream, 3,
+                                                              in_bytes=1)
+            finally:
+                ofv.ofv_destroy(h)
+        out[name] = res
+        del frames, u, v
+        torch.cuda.empty_cache()
+    out["params"] = "u8 input, NR 2, KR 10, IT 3, PSL 0/1/2, FP32 storage, fused path, ofv_compute_sequence"
     return out
 
 
