@@ -10,14 +10,14 @@ Workload recipes (particle images shaped like the paper's workloads):
 
 * ``rankine_pair``   -- 256x256 float32, Gaussian particles of FWHM 2.5 px at
   0.05 particles/px, peak intensity U[0.5, 1], Rankine vortex of core radius
-  32 px and peak displacement 3 px at the image centre (Sec. 3.1).
+  32 px and peak displacement 3 px at the image centre (Sec. 4.1).
 * ``stream_frames``  -- time-resolved 12-bit uint16 sequence (frames F_0..F_n,
   pair i = (F_i, F_{i+1})), 0.08 ppp, FWHM U[2, 3] px, 1 % noise, Rankine
   vortex plus a uniform (1.3, -0.7) px shift.
 * ``turbulence_pair`` -- 12-bit uint16, 0.1 ppp, displacement from a
   divergence-free random-Fourier-mode stream function with a k^-5/3 energy
   spectrum over wavelengths 8..1024 px, scaled to 2 px rms (stands in for
-  the Madrid HIT DNS planes of Sec. 3.2, which are not available here).
+  the Madrid HIT DNS planes of Sec. 4.2, which are not available here).
 * ``wake_pair``      -- 12-bit uint16, 0.1 ppp, potential flow round a
   cylinder of diameter 400 px plus a street of Lamb-Oseen vortices, scaled to
   a 4 px maximum (stands in for the cylinder-wake experiment of Sec. 7).
@@ -116,7 +116,7 @@ class Field:
 
     def rankine(self, cx: float, cy: float, R: float, dmax: float) -> "Field":
         """Rankine vortex: azimuthal displacement dmax*r/R inside the core and
-        dmax*R/r outside (Sec. 3.1 box, peak dmax at r = R); the two frames hold
+        dmax*R/r outside (Sec. 4.1 box, peak dmax at r = R); the two frames hold
         a particle rotated by -phi/2 and +phi/2 about the centre, phi = u_theta/r."""
         s = self._s
         s.rk_cx, s.rk_cy, s.rk_R, s.rk_dmax = cx, cy, R, dmax

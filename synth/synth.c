@@ -81,7 +81,7 @@ typedef struct {
     /* uniform translation */
     double ux, uy;
     /* Rankine vortex: centre, core radius R, peak azimuthal displacement
-       dmax reached at r = R (Sec. 3.1 box: u_theta = G/(2 pi M R) * {r/R, R/r},
+       dmax reached at r = R (Sec. 4.1 box: u_theta = G/(2 pi M R) * {r/R, R/r},
        with G/(2 pi M R) chosen equal to dmax).  Off when R <= 0. */
     double rk_cx, rk_cy, rk_R, rk_dmax;
     /* stream-function turbulence psi = sum_n A_n cos(k_n . x + phi_n);
