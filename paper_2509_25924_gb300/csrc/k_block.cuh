@@ -5,10 +5,12 @@
 // 32) and works entirely on chip in five phases:
 //   0. stage the two level images over the tile, its KR window halo, a
 //      REACH px warp margin and the gradient stencil into shared memory:
-//      a tile whose staged box lies inside the image takes two TMA tensor
-//      copies (cp.async.bulk.tensor, completion on an mbarrier) when the
-//      launch carries tensor maps; otherwise 16-byte cp.async rows, with
-//      clamp-to-edge applied element by element at the image border;
+//      a tile whose staged box lies inside the image takes TMA tensor
+//      copies (cp.async.bulk.tensor) in three row bands, each completing on
+//      its own mbarrier, when the launch carries tensor maps -- phase 1
+//      waits for a band only when it reaches rows that need it; otherwise
+//      16-byte cp.async rows, with clamp-to-edge applied element by element
+//      at the image border;
 //   1. the five products of every pixel of tile + halo (bilinear value and
 //      central-difference gradient of both frames at k -/+ V0/2) into
 //      shared memory; taps farther than REACH px come from global memory;
@@ -48,13 +50,26 @@ template <int KR> struct BlockShape {
     static constexpr int SH = RW + 2 * kBlockReach + 3;   // staged rows
 };
 
+// Rows of one TMA band: at least a third of the staged rows, and a whole
+// number of 128-byte units so that every band starts 128-byte aligned.
+__host__ __device__ constexpr int band_rows(int rows, int row_bytes)
+{
+    int b = (rows + 2) / 3;
+    while ((b * row_bytes) % 128 != 0) ++b;
+    return b;
+}
+
 template <typename T, int KR> struct StageShape {
     static constexpr int VEC = 16 / (int)sizeof(T);
     static constexpr int SW = BlockShape<KR>::RW + 2 * kBlockReach + 3 + VEC - 1;  // incl. alignment slack
     static constexpr int NV = (SW + VEC - 1) / VEC;                               // 16-byte vectors per row
     static constexpr int SP = NV * VEC;                                           // staged row pitch
+    // staged rows: three bands of SHB rows, at least the SH rows the tile needs
+    static constexpr int NBAND = 3;
+    static constexpr int SHB = band_rows(BlockShape<KR>::SH, SP * (int)sizeof(T));
+    static constexpr int SHT = NBAND * SHB;
     // elements per staged frame, rounded so the second frame starts 128-byte aligned
-    static constexpr int STG = (BlockShape<KR>::SH * SP * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
+    static constexpr int STG = (SHT * SP * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
 };
 
 // floats of the five product planes, rounded up so the staged images that
@@ -237,8 +252,10 @@ __device__ __forceinline__ Sample bilin_staged(const T *__restrict__ rm, float f
     const float da0 = q02 - q00, db0 = q03 - q01, da1 = q12 - q10, db1 = q13 - q11;
     const float gx0 = fmaf(fx, db0 - da0, da0), gx1 = fmaf(fx, db1 - da1, da1);
     s.gx = fmaf(fy, gx1 - gx0, gx0);
-    const float ea0 = q11 - e0, eb0 = q12 - e1, ea1 = e2 - q01, eb1 = e3 - q02;
-    const float gy0 = fmaf(fx, eb0 - ea0, ea0), gy1 = fmaf(fx, eb1 - ea1, ea1);
+    // row-interpolated values above and below: the row interpolation of the
+    // column differences equals the difference of row interpolations
+    const float vm = fmaf(fx, e1 - e0, e0), vp = fmaf(fx, e3 - e2, e2);
+    const float gy0 = v1 - vm, gy1 = vp - v0;
     s.gy = fmaf(fy, gy1 - gy0, gy0);
     return s;
 }
@@ -288,19 +305,45 @@ __device__ __forceinline__ void products_interior(const T *__restrict__ st1, con
 // the product region is inside the image and takes the staged fast path, so
 // the loop needs no bounds or border checks; the V0 mode is a template
 // parameter.  V0 of the thread's next pixel is loaded one iteration ahead.
+// First iteration of the phase-1 loop (pixel idx = tid + i NT of the
+// RW x RW product region) that may touch staged band b: the last row of
+// iteration i is (i + 1) NT - 1 over RW, and product row r reads staged rows
+// r .. r + 2 REACH + 3.
+template <int KR, int SHB>
+__host__ __device__ constexpr int first_iter_of_band(int b)
+{
+    constexpr int NT = BlockShape<KR>::NT, RW = BlockShape<KR>::RW;
+    int i = 0;
+    while (i * NT < RW * RW && ((i + 1) * NT - 1) / RW + 2 * kBlockReach + 3 < b * SHB) ++i;
+    return i;
+}
+
+// With bars (TMA staging in three bands), the loop waits for band b just
+// before the first iteration that can touch it, so the first rows of
+// products overlap the copies of the later bands.
 template <typename T, int KR, bool COH, int MODE, int SP>
 __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const T *__restrict__ st1,
                                                        const T *__restrict__ st2, int sx0, int sy0, int px0, int py0,
-                                                       float *prod)
+                                                       float *prod, uint64_t *bars, int *err)
 {
     using BS = BlockShape<KR>;
+    using SS = StageShape<T, KR>;
+    static_assert(SS::NBAND == 3, "three staging bands");
     constexpr int NT = BS::NT, RW = BS::RW, RWP = BS::RWP, PLANE = RW * RWP;
     constexpr int DY = NT / RW, DX = NT % RW;
+    constexpr int I1 = first_iter_of_band<KR, SS::SHB>(1), I2 = first_iter_of_band<KR, SS::SHB>(2);
     const int tid = threadIdx.x;
     int ry = tid / RW, rx = tid - (tid / RW) * RW;
     float2 V0n = make_float2(0.f, 0.f);
     if (ry < RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
-    for (int idx = tid; idx < RW * RW; idx += NT) {
+    auto wait_band = [&](int b) {
+        if (bars && !mbar_wait_bounded(bars + b, 0, 2000000000LL)) {
+            // report; the tile's results are then undefined
+            if (err) atomicExch(err, 1);
+            mbar_wait_bounded(bars + b, 0, 1000000000LL);
+        }
+    };
+    auto pixel = [&](int idx) {
         const float2 V0c = V0n;
         const int gx = px0 + rx, gy = py0 + ry;
         float *q = prod + ry * RWP + rx;
@@ -318,44 +361,57 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
         q[2 * PLANE] = p[2];
         q[3 * PLANE] = p[3];
         q[4 * PLANE] = p[4];
-    }
+    };
+    int idx = tid;
+    wait_band(0);
+    for (; idx < RW * RW && idx < I1 * NT; idx += NT) pixel(idx);
+    wait_band(1);
+    for (; idx < RW * RW && idx < I2 * NT; idx += NT) pixel(idx);
+    wait_band(2);
+    for (; idx < RW * RW; idx += NT) pixel(idx);
 }
 
 // Window sums of one line of the product planes, in place: for outputs
 // o = 0 .. TS-1, line[o*stride] <- sum_{j=0}^{2KR} line[(o+j)*stride].
 // Outputs are formed block by block (blocks of WIN = 2KR+1): the sums of a
 // block are suffix sums of its own values plus prefix sums of the next 2KR
-// values.  A block's writes land on its own outputs only, which later
-// blocks no longer read.
+// values.  Each value is loaded once and kept in registers from the step
+// that reads it as the "next" block to the step that uses it as the current
+// one; a step writes only its own block's outputs, whose values are already
+// in registers, so the line can be overwritten in place.
 template <int KR, int TS, bool TAIL>
-__device__ __forceinline__ void window_block(float *line, int stride, int b)
+__device__ __forceinline__ void window_step(float *line, int stride, int b0, float (&cur)[2 * KR + 1])
 {
-    constexpr int WIN = 2 * KR + 1;
-    float v[2 * WIN - 1];
+    constexpr int WIN = 2 * KR + 1, N = TS + 2 * KR;
+    float nxt[WIN];
 #pragma unroll
-    for (int j = 0; j < 2 * WIN - 1; ++j) v[j] = (!TAIL || b + j < TS + 2 * KR) ? line[(b + j) * stride] : 0.f;
-    float s[WIN];
-    s[WIN - 1] = v[WIN - 1];
+    for (int i = 0; i < WIN; ++i) nxt[i] = (!TAIL || b0 + WIN + i < N) ? line[(b0 + WIN + i) * stride] : 0.f;
 #pragma unroll
-    for (int i = WIN - 2; i >= 0; --i) s[i] = v[i] + s[i + 1];
-    line[b * stride] = s[0];
+    for (int i = WIN - 2; i >= 0; --i) cur[i] += cur[i + 1];  // suffix sums
+    line[b0 * stride] = cur[0];
     float pre = 0.f;
 #pragma unroll
     for (int i = 1; i < WIN; ++i) {
-        pre += v[WIN + i - 1];
-        if (!TAIL || b + i < TS) line[(b + i) * stride] = s[i] + pre;
+        pre += nxt[i - 1];
+        if (!TAIL || b0 + i < TS) line[(b0 + i) * stride] = cur[i] + pre;
     }
+#pragma unroll
+    for (int i = 0; i < WIN; ++i) cur[i] = nxt[i];
 }
 
 template <int KR, int TS>
 __device__ __forceinline__ void window_sums_inplace(float *line, int stride)
 {
-    constexpr int WIN = 2 * KR + 1;
-    constexpr int NFULL = TS / WIN;  // blocks whose outputs and inputs are all in range
+    constexpr int WIN = 2 * KR + 1, N = TS + 2 * KR;
+    constexpr int NFULL = (N - WIN) / WIN;  // steps whose next block lies wholly inside the line
+    constexpr int NB = (TS + WIN - 1) / WIN;
+    float cur[WIN];
+#pragma unroll
+    for (int i = 0; i < WIN; ++i) cur[i] = line[i * stride];
     int b = 0;
 #pragma unroll 1
-    for (int k = 0; k < NFULL; ++k, b += WIN) window_block<KR, TS, false>(line, stride, b);
-    if (b < TS) window_block<KR, TS, true>(line, stride, b);
+    for (; b < NFULL && b < NB; ++b) window_step<KR, TS, false>(line, stride, b * WIN, cur);
+    for (; b < NB; ++b) window_step<KR, TS, true>(line, stride, b * WIN, cur);
 }
 
 template <typename T, int KR, bool COH>
@@ -365,12 +421,15 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
 {
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
-    constexpr int TS = BS::TS, NT = BS::NT, RW = BS::RW, RWP = BS::RWP, SH = BS::SH;
+    constexpr int TS = BS::TS, NT = BS::NT, RW = BS::RW, RWP = BS::RWP, SH = SS::SHT;
     constexpr int SP = SS::SP, NV = SS::NV, VEC = SS::VEC, STG = SS::STG;
+    constexpr int NBAND = SS::NBAND, SHB = SS::SHB;
     constexpr int PLANE = RW * RWP;
 
     float *prod = reinterpret_cast<float *>(smem_f4);                // [5][RW][RWP]
     T *stage = reinterpret_cast<T *>(prod + ProdFloats<KR>::v);     // [2][STG]: SH rows of SP
+    __shared__ __align__(8) uint64_t s_bar[NBAND];
+    uint64_t *bars = nullptr;                                      // set when staged by TMA
 
     const int tid = threadIdx.x;
     const int H = a.H, W = a.W, pitch = a.pitch;
@@ -390,22 +449,17 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
     const bool vec_ok = sx0 >= 0 && sx0 + SP <= W;
     const bool interior = vec_ok && sy0 >= 0 && sy0 + SH <= H;
     if (tm1 != nullptr && interior && (smem_u32(stage) & 127u) == 0) {
-        __shared__ __align__(8) uint64_t s_bar;
-        if (tid == 0) mbar_init(&s_bar, 1);
-        __syncthreads();
+        // NBAND bands of SHB rows per frame, band b of both frames on barrier b
         if (tid == 0) {
-            mbar_expect_tx(&s_bar, (unsigned)(2 * SH * SP * sizeof(T)));
-            tma_load_2d(stage, tm1, sx0, sy0, &s_bar);
-            tma_load_2d(stage + STG, tm2, sx0, sy0, &s_bar);
+            for (int b = 0; b < NBAND; ++b) mbar_init(&s_bar[b], 1);
+            for (int b = 0; b < NBAND; ++b) {
+                mbar_expect_tx(&s_bar[b], (unsigned)(2 * SHB * SP * sizeof(T)));
+                tma_load_2d(stage + b * SHB * SP, tm1, sx0, sy0 + b * SHB, &s_bar[b]);
+                tma_load_2d(stage + STG + b * SHB * SP, tm2, sx0, sy0 + b * SHB, &s_bar[b]);
+            }
         }
-        const bool ok = mbar_wait_bounded(&s_bar, 0, 2000000000LL);
-        if (__syncthreads_or(!ok)) {
-            // a copy did not complete in 2 s: report, give the copies one
-            // more bounded wait, and leave the tile unwritten
-            if (tid == 0 && err) atomicExch(err, 1);
-            mbar_wait_bounded(&s_bar, 0, 1000000000LL);
-            return;
-        }
+        __syncthreads();  // barriers initialised before anyone waits on them
+        bars = s_bar;
     } else {
         for (int t = tid; t < 2 * SH * NV; t += NT) {
             const int f = t >= SH * NV ? 1 : 0;
@@ -433,11 +487,14 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
     if (interior) {
         const T *st2 = stage + STG;
         if (mode == V0_SAME)
-            products_tile_interior<T, KR, COH, V0_SAME, SP>(a, stage, st2, sx0, sy0, px0, py0, prod);
+            products_tile_interior<T, KR, COH, V0_SAME, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, err);
         else if (mode == V0_UP)
-            products_tile_interior<T, KR, COH, V0_UP, SP>(a, stage, st2, sx0, sy0, px0, py0, prod);
+            products_tile_interior<T, KR, COH, V0_UP, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, err);
         else
-            products_tile_interior<T, KR, COH, V0_ZERO, SP>(a, stage, st2, sx0, sy0, px0, py0, prod);
+            products_tile_interior<T, KR, COH, V0_ZERO, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, err);
+        // every band has landed before the CTA can finish (no copy in flight at exit)
+        if (bars && tid == 0)
+            for (int b = 0; b < NBAND; ++b) mbar_wait_bounded(&s_bar[b], 0, 1000000000LL);
     } else {
         constexpr int DY = NT / RW, DX = NT % RW;  // index step in rows and columns
         int ry = tid / RW, rx = tid - (tid / RW) * RW;

@@ -47,7 +47,7 @@ void box_of(int kr, int *cols, int *rows)
 #define OFV_BOX_CASE(K)                       \
     case K:                                   \
         *cols = StageShape<T, K>::SP;         \
-        *rows = BlockShape<K>::SH;            \
+        *rows = StageShape<T, K>::SHB;        \
         return;
     OFV_BOX_CASE(1) OFV_BOX_CASE(2) OFV_BOX_CASE(3) OFV_BOX_CASE(4) OFV_BOX_CASE(5)
     OFV_BOX_CASE(6) OFV_BOX_CASE(7) OFV_BOX_CASE(8) OFV_BOX_CASE(9) OFV_BOX_CASE(10)

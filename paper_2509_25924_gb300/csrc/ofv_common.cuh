@@ -68,7 +68,8 @@ cudaError_t launch_iter_fused(const IterArgs &a, int store, int mode, cudaStream
 bool block_supports(int kr);
 cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s,
                               const CUtensorMap *const *tm = nullptr, int *err = nullptr);
-// Staged box (columns, rows) of the block kernel for this storage and radius.
+// TMA box of the block kernel's staging (columns, rows of one band) for this
+// storage and radius.
 void block_stage_box(int store, int kr, int *cols, int *rows);
 
 struct PlainBufs {
