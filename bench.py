@@ -303,6 +303,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_sizes:
         line["sizes"] = sizes(ofv, torch, synth, dev, stream, frames, u, v)
         line["live_21Mp"] = live_loop(ofv, torch, synth, dev, stream)
+        line["live_21Mp_3lanes"] = live_loop(ofv, torch, synth, dev, stream, ring=9, lanes=3)
         line["paper_perf_set"] = paper_perf_set(ofv, torch, synth, dev, stream)
         line["batched_64_uneven"] = batched_uneven(ofv, torch, synth, dev, stream)
 
@@ -454,40 +455,58 @@ def paper_perf_set(ofv, torch, synth, dev, stream):
     return out
 
 
-def live_loop(ofv, torch, synth, dev, stream, n_pairs=2000, ring=8):
+def live_loop(ofv, torch, synth, dev, stream, n_pairs=2000, ring=8, lanes=1):
     """21 Mp live analogue: a device ring of `ring` pre-generated pairs of
     the cylinder-wake stream (5120x4096 u16), one CUDA graph per ring pair,
-    replayed back to back for n_pairs fields; per-field device time from
-    CUDA events between graph launches."""
+    replayed for n_pairs fields.  lanes = 1: one handle, graphs back to back
+    on one stream.  lanes > 1: pair i runs on handle and stream i mod lanes,
+    so consecutive fields overlap (each handle owns its workspace).  Per-field
+    latency: CUDA events around each graph launch on its stream."""
     H, W = 4096, 5120
     fld, inside = synth.wake_field(H, W)
     fr = synth.stream_frames(H, W, ring + 1, seed=4, ppp=0.1, field=fld, field_max=8.0, exclude=inside)
     frames = torch.from_numpy(fr).to(dev)
-    u = torch.empty((2, H, W), dtype=torch.float32, device=dev)
+    u = torch.empty((2 * lanes, H, W), dtype=torch.float32, device=dev)
     v = torch.empty_like(u)
-    h = ofv.ofv_create(H, W, ofv.ofv_default_params())
+    hs = [ofv.ofv_create(H, W, ofv.ofv_default_params()) for _ in range(lanes)]
+    streams = [stream] if lanes == 1 else [torch.cuda.Stream(device=dev) for _ in range(lanes)]
     graphs = []
     try:
+        # graph of ring pair k on lane k mod lanes (ring is a multiple of lanes)
         for k in range(ring):
-            graphs.append(ofv.ofv_graph_create(h, frames[k], frames[k + 1], u[k % 2], v[k % 2]))
+            ln = k % lanes
+            graphs.append(ofv.ofv_graph_create(hs[ln], frames[k], frames[k + 1], u[2 * ln + (k // lanes) % 2],
+                                               v[2 * ln + (k // lanes) % 2]))
         for k in range(ring):
-            ofv.ofv_graph_launch(graphs[k], stream)
+            ofv.ofv_graph_launch(graphs[k], streams[k % lanes])
         torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_pairs + 1)]
-        ev[0].record(stream)
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_pairs)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_pairs)]
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for st in streams:
+            st.wait_event(start)
         for i in range(n_pairs):
-            ofv.ofv_graph_launch(graphs[i % ring], stream)
-            ev[i + 1].record(stream)
+            st = streams[i % lanes]
+            e0[i].record(st)
+            ofv.ofv_graph_launch(graphs[i % ring], st)
+            e1[i].record(st)
+        for st in streams:
+            stream.wait_stream(st)
+        end.record(stream)
         torch.cuda.synchronize()
-        per = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(n_pairs)])
-        total = ev[0].elapsed_time(ev[-1])
+        per = np.array([e0[i].elapsed_time(e1[i]) for i in range(n_pairs)])
+        total = start.elapsed_time(end)
     finally:
         for g in graphs:
             ofv.ofv_graph_destroy(g)
-        ofv.ofv_destroy(h)
+        for h in hs:
+            ofv.ofv_destroy(h)
     del frames, u, v
     torch.cuda.empty_cache()
-    return {"workload": "5120x4096 u16 cylinder-wake stream, ring of 8 pairs, one CUDA graph per pair",
+    return {"workload": f"5120x4096 u16 cylinder-wake stream, ring of {ring} pairs, one CUDA graph per pair, "
+                        f"{lanes} handle/stream lane(s)",
             "pairs": n_pairs, "hz": n_pairs / (total / 1e3), "p50_ms": float(np.percentile(per, 50)),
             "p99_ms": float(np.percentile(per, 99)), "max_ms": float(per.max())}
 

@@ -20,14 +20,10 @@
 #include <cstring>
 
 #include "iter_math.cuh"
+#include "k_bw_block.cuh"
 #include "ofv_handle.h"
 
 namespace ofv {
-
-struct Planes5 {
-    float *p[5];
-    int pitch;  // elements
-};
 
 // V0 of a stage written as a plane: zero, same (copy of the previous stage
 // output) or the x2 up-sampled coarse field.
@@ -114,13 +110,22 @@ __global__ void k_bw_solve(Planes5 S, const float2 *gV, int vpitch, int H, int W
 template <typename T>
 __device__ __forceinline__ float ldp(const T *P, int pitch, int y, int x) { return ld_store(P + (int64_t)y * pitch + x); }
 
+// Image-gradient scatter straight to global memory (float atomics).
+struct ScatterGlobal {
+    float *g;
+    int pitch;
+    __device__ __forceinline__ void operator()(int y, int x, float v) const { atomicAdd(g + (int64_t)y * pitch + x, v); }
+};
+
 // Value, gradient and position derivatives of one bilinear sample at
 // (x + dx, y + dy) with clamp-to-edge taps, and the scatter of (gval, ggx,
-// ggy) into the image gradient gP (dense pitch gpitch).  Returns through
-// dpx, dpy the derivative of gval*val + ggx*gx + ggy*gy w.r.t. the position.
-template <typename T>
-__device__ void sample_adj(const T *P, int H, int W, int pitch, int x, int y, float dx, float dy, float gval, float ggx,
-                           float ggy, float *gP, int gpitch, float &dpx, float &dpy)
+// ggy) into the image gradient through add(row, column, value).  Returns
+// through dpx, dpy the derivative of gval*val + ggx*gx + ggy*gy w.r.t. the
+// position.
+template <typename T, typename Scatter>
+__device__ __forceinline__ void sample_adj(const T *P, int H, int W, int pitch, int x, int y, float dx, float dy,
+                                           float gval, float ggx, float ggy, const Scatter &add, float &dpx,
+                                           float &dpy)
 {
     const float lim_x = (float)(W + 4), lim_y = (float)(H + 4);
     dx = fminf(fmaxf(dx, -lim_x), lim_x);
@@ -157,28 +162,26 @@ __device__ void sample_adj(const T *P, int H, int W, int pitch, int x, int y, fl
     const int tym[4] = {yam, yam, ybm, ybm}, typ[4] = {yap, yap, ybp, ybp};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (gval != 0.f) atomicAdd(gP + (int64_t)ty[k] * gpitch + tx[k], gval * w[k]);
+        if (gval != 0.f) add(ty[k], tx[k], gval * w[k]);
         const float gdx = 0.5f * ggx * w[k], gdy = 0.5f * ggy * w[k];
         if (gdx != 0.f) {
-            atomicAdd(gP + (int64_t)ty[k] * gpitch + txp[k], gdx);
-            atomicAdd(gP + (int64_t)ty[k] * gpitch + txm[k], -gdx);
+            add(ty[k], txp[k], gdx);
+            add(ty[k], txm[k], -gdx);
         }
         if (gdy != 0.f) {
-            atomicAdd(gP + (int64_t)typ[k] * gpitch + tx[k], gdy);
-            atomicAdd(gP + (int64_t)tym[k] * gpitch + tx[k], -gdy);
+            add(typ[k], tx[k], gdy);
+            add(tym[k], tx[k], -gdy);
         }
     }
 }
 
 // Adjoint of the products, the residual, the averaged gradient and the two
-// warped samples at every pixel k; adds into gV0 and the level-image
-// gradients gP1, gP2 (dense, pitch gpitch).
-template <typename T>
-__global__ void k_bw_samples(IterArgs a, Planes5 gprod, float2 *gV0, float *gP1, float *gP2, int gpitch)
+// warped samples at pixel (x, y); adds into gV0 and, through add1 and add2,
+// into the level-image gradients.
+template <typename T, typename Scatter>
+__device__ __forceinline__ void samples_adjoint_pixel(const IterArgs &a, const Planes5 &gprod, float2 *gV0, int x,
+                                                      int y, const Scatter &add1, const Scatter &add2)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.W || y >= a.H) return;
     const T *P1 = static_cast<const T *>(a.P1);
     const T *P2 = static_cast<const T *>(a.P2);
     const float2 V0 = fetch_v0<V0_SAME>(a, x, y);
@@ -195,12 +198,70 @@ __global__ void k_bw_samples(IterArgs a, Planes5 gprod, float2 *gV0, float *gP1,
     const float gGy = Gx * q1 + 2.f * Gy * q2 + r * q4 + V0.y * gr;
     const float gA = gr, gB = -gr;  // It = B - A, gIt = -gr
     float d1x, d1y, d2x, d2y;
-    sample_adj(P1, a.H, a.W, a.pitch, x, y, -hx, -hy, gA, 0.5f * gGx, 0.5f * gGy, gP1, gpitch, d1x, d1y);
-    sample_adj(P2, a.H, a.W, a.pitch, x, y, hx, hy, gB, 0.5f * gGx, 0.5f * gGy, gP2, gpitch, d2x, d2y);
+    sample_adj(P1, a.H, a.W, a.pitch, x, y, -hx, -hy, gA, 0.5f * gGx, 0.5f * gGy, add1, d1x, d1y);
+    sample_adj(P2, a.H, a.W, a.pitch, x, y, hx, hy, gB, 0.5f * gGx, 0.5f * gGy, add2, d2x, d2y);
     float2 g = gV0[(int64_t)y * a.vpitch + x];
     g.x += Gx * gr - 0.5f * d1x + 0.5f * d2x;
     g.y += Gy * gr - 0.5f * d1y + 0.5f * d2y;
     gV0[(int64_t)y * a.vpitch + x] = g;
+}
+
+// One pixel per thread, scatter to global memory (window radii > 10).
+template <typename T>
+__global__ void k_bw_samples(IterArgs a, Planes5 gprod, float2 *gV0, float *gP1, float *gP2, int gpitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    samples_adjoint_pixel<T>(a, gprod, gV0, x, y, ScatterGlobal{gP1, gpitch}, ScatterGlobal{gP2, gpitch});
+}
+
+// A 32 x 32 tile of pixels per CTA.  The image-gradient scatter lands in a
+// shared-memory window around the tile (margin REACH + 2, which holds every
+// tap of a warp up to REACH px) and reaches global memory once per window
+// element; taps outside the window (larger warps) go to global memory
+// directly.  Windows of neighbouring tiles overlap, so the final adds are
+// atomic too.
+constexpr int kSampTS = 32, kSampM = kBlockReach + 2, kSampWW = kSampTS + 2 * kSampM;
+
+struct ScatterWindow {
+    float (*win)[kSampWW + 1];
+    float *g;
+    int pitch, wx0, wy0;
+    __device__ __forceinline__ void operator()(int y, int x, float v) const
+    {
+        const int r = y - wy0, c = x - wx0;
+        if ((unsigned)r < (unsigned)kSampWW && (unsigned)c < (unsigned)kSampWW)
+            atomicAdd(&win[r][c], v);
+        else
+            atomicAdd(g + (int64_t)y * pitch + x, v);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bw_samples_tile(IterArgs a, Planes5 gprod, float2 *gV0, float *gP1,
+                                                         float *gP2, int gpitch)
+{
+    __shared__ float acc[2][kSampWW][kSampWW + 1];
+    const int tid = threadIdx.x;
+    const int tx0 = blockIdx.x * kSampTS, ty0 = blockIdx.y * kSampTS;
+    const int wx0 = tx0 - kSampM, wy0 = ty0 - kSampM;
+    float *flat = &acc[0][0][0];
+    for (int i = tid; i < 2 * kSampWW * (kSampWW + 1); i += 256) flat[i] = 0.f;
+    __syncthreads();
+    const ScatterWindow s1{acc[0], gP1, gpitch, wx0, wy0}, s2{acc[1], gP2, gpitch, wx0, wy0};
+    for (int i = tid; i < kSampTS * kSampTS; i += 256) {
+        const int y = ty0 + i / kSampTS, x = tx0 + i % kSampTS;
+        if (y < a.H && x < a.W) samples_adjoint_pixel<T>(a, gprod, gV0, x, y, s1, s2);
+    }
+    __syncthreads();
+    for (int i = tid; i < 2 * kSampWW * kSampWW; i += 256) {
+        const int f = i / (kSampWW * kSampWW), rem = i - f * kSampWW * kSampWW;
+        const int r = rem / kSampWW, c = rem - r * kSampWW;
+        const int y = wy0 + r, x = wx0 + c;
+        const float v = acc[f][r][c];
+        if (v != 0.f && y >= 0 && y < a.H && x >= 0 && x < a.W) atomicAdd((f ? gP2 : gP1) + (int64_t)y * gpitch + x, v);
+    }
 }
 
 // Transpose of the x2 up-sampling: scatter 2 * w * gV0(fine) to the coarse
@@ -324,10 +385,50 @@ cudaError_t bw_v0(const IterArgs &a, int mode, float2 *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
+namespace {
+cudaError_t box_tile(int kr, Planes5 in, Planes5 out, int H, int W, cudaStream_t s)
+{
+    switch (kr) {
+#define OFV_BOX_CASE(K) \
+    case K: return run_bw_box_tile<K>(in, out, H, W, s);
+    OFV_BOX_CASE(1) OFV_BOX_CASE(2) OFV_BOX_CASE(3) OFV_BOX_CASE(4) OFV_BOX_CASE(5)
+    OFV_BOX_CASE(6) OFV_BOX_CASE(7) OFV_BOX_CASE(8) OFV_BOX_CASE(9) OFV_BOX_CASE(10)
+#undef OFV_BOX_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+// One stage of the adjoint.  Window radii 1..10: the forward block kernel's
+// tile again with the solve adjoint as its epilogue (gS into B, direct part
+// of gV0), the box-sum adjoint tile by tile (gS -> gprod in A), the samples
+// adjoint with the scatter accumulated per tile in shared memory.  Larger
+// radii: one pixel per thread throughout.
 cudaError_t bw_stage(const IterArgs &a, int store, Planes5 A, Planes5 B, const float2 *gV, float2 *gV0, float *gP1,
                      float *gP2, int gpitch, cudaStream_t s)
 {
     const dim3 g = grid2(a.W, a.H), b(32, 8);
+    if (block_supports(a.kr)) {
+        BwStageParams q;
+        q.a = a;
+        q.epi.gV = gV;
+        q.epi.gV0 = gV0;
+        q.epi.gS = B;
+        q.epi.vpitch = a.vpitch;
+        cudaError_t e = store == ST_F16    ? launch_bw_stage_S_f16(q, s)
+                        : store == ST_BF16 ? launch_bw_stage_S_bf16(q, s)
+                                           : launch_bw_stage_S_f32(q, s);
+        if (e != cudaSuccess) return e;
+        e = box_tile(a.kr, B, A, a.H, a.W, s);
+        if (e != cudaSuccess) return e;
+        const dim3 gt((a.W + kSampTS - 1) / kSampTS, (a.H + kSampTS - 1) / kSampTS);
+        switch (store) {
+        case ST_F16: k_bw_samples_tile<__half><<<gt, 256, 0, s>>>(a, A, gV0, gP1, gP2, gpitch); break;
+        case ST_BF16: k_bw_samples_tile<__nv_bfloat16><<<gt, 256, 0, s>>>(a, A, gV0, gP1, gP2, gpitch); break;
+        default: k_bw_samples_tile<float><<<gt, 256, 0, s>>>(a, A, gV0, gP1, gP2, gpitch); break;
+        }
+        return cudaGetLastError();
+    }
     switch (store) {
     case ST_F16: k_bw_products<__half><<<g, b, 0, s>>>(a, A); break;
     case ST_BF16: k_bw_products<__nv_bfloat16><<<g, b, 0, s>>>(a, A); break;

@@ -414,10 +414,36 @@ __device__ __forceinline__ void window_sums_inplace(float *line, int stride)
     for (; b < NB; ++b) window_step<KR, TS, true>(line, stride, b * WIN, cur);
 }
 
-template <typename T, int KR, bool COH>
+// Phase 4 of the forward iteration: the guarded 2x2 solve of pixel (gx, gy)
+// from its window sums S = (Sxx, Sxy, Syy, Sxr, Syr) and the store of V.
+struct SolveStore {
+    template <bool COH>
+    __device__ __forceinline__ void apply(const IterArgs &a, int mode, int gx, int gy, const float (&S)[5]) const
+    {
+        const float sxx = S[0], sxy = S[1], syy = S[2], sxr = S[3], syr = S[4];
+        const float tr = sxx + syy;
+        const float det = sxx * syy - sxy * sxy;
+        float2 V;
+        if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr) {
+            V = fetch_v0_rt<COH>(a, mode, gx, gy);
+        } else {
+            const float inv = __frcp_rn(det);  // one correctly rounded reciprocal, two products
+            V = make_float2((syy * sxr - sxy * syr) * inv, (sxx * syr - sxy * sxr) * inv);
+        }
+        if (a.u_out) {
+            a.u_out[(int64_t)gy * a.W + gx] = V.x;
+            a.v_out[(int64_t)gy * a.W + gx] = V.y;
+        } else {
+            a.Vout[(int64_t)gy * a.vpitch + gx] = V;
+        }
+    }
+};
+
+// Phases 0-3 of one tile, then epi.apply() per output pixel (phase 4).
+template <typename T, int KR, bool COH, typename Epi = SolveStore>
 __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4,
                                            const CUtensorMap *tm1 = nullptr, const CUtensorMap *tm2 = nullptr,
-                                           int *err = nullptr)
+                                           int *err = nullptr, const Epi &epi = Epi())
 {
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
@@ -552,28 +578,14 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
     }
     __syncthreads();
 
-    // phase 4: guarded solve and store
+    // phase 4: per output pixel, the epilogue (guarded solve and store)
     for (int idx = tid; idx < TS * TS; idx += NT) {
         const int oy = idx / TS, ox = idx - oy * TS;
         const int gy = ty0 + oy, gx = tx0 + ox;
         if (gy >= H || gx >= W) continue;
         const float *q = prod + oy * RWP + ox;
-        const float sxx = q[0], sxy = q[PLANE], syy = q[2 * PLANE], sxr = q[3 * PLANE], syr = q[4 * PLANE];
-        const float tr = sxx + syy;
-        const float det = sxx * syy - sxy * sxy;
-        float2 V;
-        if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr) {
-            V = fetch_v0_rt<COH>(a, mode, gx, gy);
-        } else {
-            const float inv = __frcp_rn(det);  // one correctly rounded reciprocal, two products
-            V = make_float2((syy * sxr - sxy * syr) * inv, (sxx * syr - sxy * sxr) * inv);
-        }
-        if (a.u_out) {
-            a.u_out[(int64_t)gy * W + gx] = V.x;
-            a.v_out[(int64_t)gy * W + gx] = V.y;
-        } else {
-            a.Vout[(int64_t)gy * a.vpitch + gx] = V;
-        }
+        const float S[5] = {q[0], q[PLANE], q[2 * PLANE], q[3 * PLANE], q[4 * PLANE]};
+        epi.template apply<COH>(a, mode, gx, gy, S);
     }
 }
 

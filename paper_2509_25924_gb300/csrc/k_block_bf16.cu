@@ -1,6 +1,7 @@
 // Block-tiled iteration kernel instantiated for __nv_bfloat16 level storage, window
 // radii 1..10.
 #include "k_block.cuh"
+#include "k_bw_block.cuh"
 
 namespace ofv {
 
@@ -103,5 +104,22 @@ int queue_occupancy_bf16(int kr)
     }
 }
 
+
+}  // namespace ofv
+
+namespace ofv {
+
+// Reverse-mode stage kernel (window sums again, solve adjoint) for this storage.
+cudaError_t launch_bw_stage_S_bf16(const BwStageParams &q, cudaStream_t s)
+{
+    switch (q.a.kr) {
+#define OFV_BW_CASE(K) \
+    case K: return run_bw_stage_S<__nv_bfloat16, K>(q, s);
+    OFV_BW_CASE(1) OFV_BW_CASE(2) OFV_BW_CASE(3) OFV_BW_CASE(4) OFV_BW_CASE(5)
+    OFV_BW_CASE(6) OFV_BW_CASE(7) OFV_BW_CASE(8) OFV_BW_CASE(9) OFV_BW_CASE(10)
+#undef OFV_BW_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 }  // namespace ofv
