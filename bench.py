@@ -300,6 +300,8 @@ def run_ours(args, ws, rank, local):
     if not args.no_e2e:
         line["e2e"] = e2e(args, ofv, torch, h, frames_h, dev, stream, barrier, max_over_ranks, ws)
 
+    line["derived_1Mp"] = derived_rates(ofv, torch, u, v, H1, W1, npairs, stream)
+
     if not args.no_sizes:
         line["sizes"] = sizes(ofv, torch, synth, dev, stream, frames, u, v)
         line["live_21Mp"] = live_loop(ofv, torch, synth, dev, stream)
@@ -425,6 +427,34 @@ def sizes(ofv, torch, synth, dev, stream, frames1, u1, v1):
         if kind is not None:
             del frames, u, v
             torch.cuda.empty_cache()
+    return out
+
+
+def derived_rates(ofv, torch, u, v, H, W, n, stream, reps=5):
+    """Vorticity and recirculation-area count (Sec. 7, Eq. 6) over the n
+    fields of the stream, resident in HBM: fields/s and the fraction of the
+    measured copy bandwidth (algorithmic bytes: u, v read and omega written,
+    12 B/px; u read, 4 B/px)."""
+    N = H * W
+    omega = torch.empty_like(u)
+    counts = torch.empty(n, dtype=torch.int64, device=u.device)
+    peak, _ = peaks()
+    out = {}
+    for name, fn, bpp in (("vorticity", lambda: ofv.ofv_vorticity(H, W, n, u, v, N, omega, stream), 12.0),
+                          ("recirculation_area", lambda: ofv.ofv_recirculation_area(H, W, n, u, N, None, counts,
+                                                                                   stream), 4.0)):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"fields_per_s": n / sec, "gbs": n * N * bpp / sec / 1e9, "frac_of_hbm": n * N * bpp / sec / 1e9 / peak}
+    del omega, counts
     return out
 
 

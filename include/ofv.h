@@ -150,6 +150,28 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
                                      size_t frame_stride_bytes, float *u, float *v,
                                      size_t field_stride, ofv_stream_t s);
 
+/* ---- derived quantities (Sec. 7) ------------------------------------------
+ * Computed from the fields in real time, like the vorticity maps and the
+ * recirculation-area time series of the paper's cylinder-wake experiment.
+ * Both take n fields of a sequence at u + k * field_stride (and v + k *
+ * field_stride), H x W dense each, device pointers, 1 <= n <= 65535.
+ *
+ * ofv_vorticity writes omega = dv/dx - du/dy per field (u along columns x,
+ * v along rows y; omega + k * field_stride), with second-order central
+ * differences inside and first-order one-sided differences on the first and
+ * last column / row; for px/frame fields the unit is 1/frame (divide by the
+ * frame interval for 1/s).
+ *
+ * ofv_recirculation_area writes counts[k] (device, unsigned 64-bit) = the
+ * number of pixels of field k where u < 0 (H(-u) = 1 in Eq. 6), inside the
+ * region mask (H x W bytes, nonzero = inside; NULL = every pixel).  RA(t) is
+ * counts[k] times the pixel area dx dz.  counts is cleared on stream s
+ * first. */
+ofv_status ofv_vorticity(int H, int W, int n, const float *u, const float *v, size_t field_stride,
+                         float *omega, ofv_stream_t s);
+ofv_status ofv_recirculation_area(int H, int W, int n, const float *u, size_t field_stride,
+                                  const uint8_t *mask, unsigned long long *counts, ofv_stream_t s);
+
 /* ---- reverse mode -------------------------------------------------------
  * The paper defines no derivative; this is the chain rule through the steps
  * of Sec. 2 (Eq. 2 and its Gauss-Newton linearisation, the pyramid, the

@@ -80,6 +80,9 @@ def _load():
             lib.orc_flow.restype = I
             lib.orc_flow_grad.argtypes = [I, I, P, P, ctypes.POINTER(_Params), P, P, P, P, P, P, P]
             lib.orc_flow_grad.restype = I
+            lib.orc_vorticity.argtypes = [I, I, P, P, P]
+            lib.orc_recirculation_count.argtypes = [I, I, P, P]
+            lib.orc_recirculation_count.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -264,3 +267,18 @@ def flow_grad(I1, I2, params: Params, gu, gv):
     if rc:
         raise RuntimeError(f"orc_flow_grad failed ({rc})")
     return g1, g2, (gw.reshape(5, 5) if params.prefilter is not None else None), u, v
+
+
+def vorticity(u, v):
+    """omega = dv/dx - du/dy of a field (u along columns, v along rows)."""
+    u, v = _f64(u), _f64(v)
+    out = np.empty_like(u)
+    _load().orc_vorticity(u.shape[0], u.shape[1], _p(u), _p(v), _p(out))
+    return out
+
+
+def recirculation_count(u, mask=None):
+    """Pixels of the region (mask != 0, or all) where u < 0 (Eq. 6 in pixels)."""
+    u = _f64(u)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    return int(_load().orc_recirculation_count(u.shape[0], u.shape[1], _p(u), None if m is None else _p(m)))

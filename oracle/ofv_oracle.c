@@ -412,3 +412,38 @@ int orc_pyramid(int H, int W, const double *raw, const orc_params *p, double *ou
     }
     return 0;
 }
+
+/* ---- quantities derived from a field (Sec. 7) --------------------------- */
+
+/* d f / d x along a row of n samples at unit spacing: central differences
+   inside, one-sided differences at the two ends (0 for n = 1). */
+static double row_derivative(const double *f, int n, int j, int step)
+{
+    if (n < 2) return 0.0;
+    if (j == 0) return f[step] - f[0];
+    if (j == n - 1) return f[(int64_t)(n - 1) * step] - f[(int64_t)(n - 2) * step];
+    return 0.5 * (f[(int64_t)(j + 1) * step] - f[(int64_t)(j - 1) * step]);
+}
+
+/* Out-of-plane vorticity of the field (u along columns x, v along rows y):
+   omega = dv/dx - du/dy (Sec. 7: computed from the instantaneous 2D field). */
+void orc_vorticity(int H, int W, const double *u, const double *v, double *omega)
+{
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            const double dvdx = row_derivative(v + (int64_t)i * W, W, j, 1);
+            const double dudy = row_derivative(u + j, H, i, W);
+            omega[(int64_t)i * W + j] = dvdx - dudy;
+        }
+}
+
+/* Recirculation area of Eq. 6 in pixels: the number of pixels of the region
+   (mask[k] != 0, or every pixel when mask is NULL) where u < 0, i.e. where
+   the Heaviside function H(-u) is 1. */
+int64_t orc_recirculation_count(int H, int W, const double *u, const unsigned char *mask)
+{
+    int64_t c = 0;
+    for (int64_t k = 0; k < (int64_t)H * W; ++k)
+        if ((mask == NULL || mask[k] != 0) && u[k] < 0.0) ++c;
+    return c;
+}

@@ -19,7 +19,7 @@ from . import build as _build
 __all__ = [
     "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter",
     "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host",
-    "ofv_compute_noalloc", "ofv_backward", "ofv_level_shape",
+    "ofv_compute_noalloc", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
     "Flow", "lib_path", "EXPORTED_SYMBOLS",
@@ -37,6 +37,7 @@ EXPORTED_SYMBOLS = [
     "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host", "ofv_compute_noalloc",
     "ofv_graph_create", "ofv_graph_launch",
     "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
+    "ofv_vorticity", "ofv_recirculation_area",
     "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
@@ -82,6 +83,8 @@ def _load_library():
                               ctypes.POINTER(I)], I),
         "ofv_queue_selftest": ([I, ctypes.POINTER(I)], I),
         "ofv_backward": ([P, P, P, P, P, P, P, P, P], I),
+        "ofv_vorticity": ([I, I, I, P, P, Z, P, P], I),
+        "ofv_recirculation_area": ([I, I, I, P, Z, P, P, P], I),
         "ofv_level_shape": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "ofv_read_level": ([P, I, I, P, P], I),
         "ofv_profile_enable": ([P, I], I),
@@ -192,6 +195,18 @@ def ofv_backward(h: int, I1, I2, gu, gv, gI1, gI2, gw25=None, stream=None):
     receive dL/dI1, dL/dI2, dL/dw for dL/du = gu, dL/dv = gv."""
     _check(_lib.ofv_backward(h, _addr(I1), _addr(I2), _addr(gu), _addr(gv), _addr(gI1), _addr(gI2), _addr(gw25),
                              _stream(stream)), "ofv_backward")
+
+
+def ofv_vorticity(H: int, W: int, n: int, u, v, field_stride: int, omega, stream=None):
+    """omega = dv/dx - du/dy of n fields (device)."""
+    _check(_lib.ofv_vorticity(H, W, n, _addr(u), _addr(v), field_stride, _addr(omega), _stream(stream)),
+           "ofv_vorticity")
+
+
+def ofv_recirculation_area(H: int, W: int, n: int, u, field_stride: int, mask, counts, stream=None):
+    """counts[k] (device uint64 / int64) = pixels of field k in the mask where u < 0."""
+    _check(_lib.ofv_recirculation_area(H, W, n, _addr(u), field_stride, _addr(mask), _addr(counts),
+                                       _stream(stream)), "ofv_recirculation_area")
 
 
 class Pair(ctypes.Structure):
