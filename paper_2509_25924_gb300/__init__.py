@@ -322,6 +322,13 @@ class Flow:
         ofv_compute(self.h, I1, I2, u, v, stream)
         return u, v
 
+    @staticmethod
+    def apply(I1, I2, prefilter_w=None, params=None):
+        """torch.autograd entry: differentiable (u, v) of (I1, I2); see
+        ``autograd.apply``."""
+        from .autograd import apply as _apply
+        return _apply(I1, I2, prefilter_w, params)
+
     def close(self):
         if getattr(self, "h", None):
             ofv_destroy(self.h)

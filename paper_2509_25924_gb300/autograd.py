@@ -50,3 +50,29 @@ class FlowFunction(torch.autograd.Function):
 def flow_fn(flow: Flow, I1, I2, w25=None):
     """Differentiable (u, v) of the pair (I1, I2) on the handle ``flow``."""
     return FlowFunction.apply(I1, I2, w25, flow)
+
+
+_handles: dict = {}
+
+
+def apply(I1, I2, prefilter_w=None, params=None):
+    """Differentiable (u, v) of (I1, I2) for estimator parameters ``params``
+    (an ofv_params structure, a dict of its fields, or None for the
+    defaults; input type and pre-filter follow the arguments).  Handles are
+    created on first use per (device, shape, parameters) and kept."""
+    from . import ofv_default_params, Params, OFV_IN_F32, OFV_IN_U16, OFV_IN_U8
+    kw = {}
+    if isinstance(params, Params):
+        kw = {name: getattr(params, name) for name, _ in Params._fields_}
+    elif params:
+        kw = dict(params)
+    kw["input"] = {torch.float32: OFV_IN_F32, torch.uint8: OFV_IN_U8}.get(I1.dtype, OFV_IN_U16)
+    kw["prefilter"] = 0 if prefilter_w is None else 1
+    H, W = I1.shape[-2], I1.shape[-1]
+    key = (I1.device.index, H, W, tuple(sorted(kw.items())))
+    flow = _handles.get(key)
+    if flow is None:
+        with torch.cuda.device(I1.device):
+            flow = Flow(H, W, ofv_default_params(**kw))
+        _handles[key] = flow
+    return FlowFunction.apply(I1, I2, prefilter_w, flow)

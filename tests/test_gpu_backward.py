@@ -192,3 +192,30 @@ def test_prefilter_training_step_lowers_the_loss():
         assert losses[-1] < 0.97 * losses[0], losses
     finally:
         flow.close()
+
+
+def test_flow_apply_entry_matches_flow_fn():
+    H, W = 64, 72
+    I1, I2, gu, gv = _smooth(H, W, seed=21)
+    w = np.zeros((5, 5), np.float32)
+    w[2, 2] = 0.8
+    w[2, 1] = w[2, 3] = 0.1
+    params = dict(levels_psl=1, kernel_radius=3, iterations=2)
+    tgu = torch.from_numpy(gu.astype(np.float32)).to(DEV)
+    tgv = torch.from_numpy(gv.astype(np.float32)).to(DEV)
+    grads = []
+    for use_apply in (True, False):
+        t1 = torch.from_numpy(I1).to(DEV).requires_grad_(True)
+        t2 = torch.from_numpy(I2).to(DEV).requires_grad_(True)
+        tw = torch.from_numpy(w).to(DEV).requires_grad_(True)
+        if use_apply:
+            u, v = ofv.Flow.apply(t1, t2, tw, params)
+        else:
+            flow = ofv.Flow(H, W, input=ofv.OFV_IN_F32, prefilter=1, **params)
+            u, v = flow_fn(flow, t1, t2, tw)
+        ((u * tgu).sum() + (v * tgv).sum()).backward()
+        grads.append((u.detach().cpu().numpy(), t1.grad.cpu().numpy(), tw.grad.cpu().numpy()))
+        if not use_apply:
+            flow.close()
+    assert np.array_equal(grads[0][0], grads[1][0])
+    assert _rel(grads[0][1], grads[1][1]) <= 1e-5 and _rel(grads[0][2], grads[1][2]) <= 1e-5
