@@ -324,7 +324,7 @@ __host__ __device__ constexpr int first_iter_of_band(int b)
 template <typename T, int KR, bool COH, int MODE, int SP>
 __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const T *__restrict__ st1,
                                                        const T *__restrict__ st2, int sx0, int sy0, int px0, int py0,
-                                                       float *prod, uint64_t *bars, int *err)
+                                                       float *prod, uint64_t *bars, unsigned parity, int *err)
 {
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
@@ -337,10 +337,10 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
     float2 V0n = make_float2(0.f, 0.f);
     if (ry < RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
     auto wait_band = [&](int b) {
-        if (bars && !mbar_wait_bounded(bars + b, 0, 2000000000LL)) {
+        if (bars && !mbar_wait_bounded(bars + b, parity, 2000000000LL)) {
             // report; the tile's results are then undefined
             if (err) atomicExch(err, 1);
-            mbar_wait_bounded(bars + b, 0, 1000000000LL);
+            mbar_wait_bounded(bars + b, parity, 1000000000LL);
         }
     };
     auto pixel = [&](int idx) {
@@ -440,10 +440,17 @@ struct SolveStore {
 };
 
 // Phases 0-3 of one tile, then epi.apply() per output pixel (phase 4).
+// TMA staging needs tensor maps tm1, tm2 of the two level images and NBAND
+// mbarriers tma_bars (shared memory): with init_bars the tile initialises
+// them (one tile per CTA), else the caller did and made them visible to the
+// CTA; parity is the phase this tile's copies complete (the number of
+// earlier TMA tiles of the CTA, mod 2).  Returns true when the tile was
+// staged by TMA.
 template <typename T, int KR, bool COH, typename Epi = SolveStore>
-__device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4,
+__device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4,
                                            const CUtensorMap *tm1 = nullptr, const CUtensorMap *tm2 = nullptr,
-                                           int *err = nullptr, const Epi &epi = Epi())
+                                           int *err = nullptr, const Epi &epi = Epi(), uint64_t *tma_bars = nullptr,
+                                           unsigned parity = 0, bool init_bars = false)
 {
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
@@ -454,7 +461,6 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
 
     float *prod = reinterpret_cast<float *>(smem_f4);                // [5][RW][RWP]
     T *stage = reinterpret_cast<T *>(prod + ProdFloats<KR>::v);     // [2][STG]: SH rows of SP
-    __shared__ __align__(8) uint64_t s_bar[NBAND];
     uint64_t *bars = nullptr;                                      // set when staged by TMA
 
     const int tid = threadIdx.x;
@@ -474,18 +480,22 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
     // columns.  Rows are clamped as a whole.
     const bool vec_ok = sx0 >= 0 && sx0 + SP <= W;
     const bool interior = vec_ok && sy0 >= 0 && sy0 + SH <= H;
-    if (tm1 != nullptr && interior && (smem_u32(stage) & 127u) == 0) {
+    if (tm1 != nullptr && tma_bars != nullptr && interior && (smem_u32(stage) & 127u) == 0) {
         // NBAND bands of SHB rows per frame, band b of both frames on barrier b
         if (tid == 0) {
-            for (int b = 0; b < NBAND; ++b) mbar_init(&s_bar[b], 1);
+            if (init_bars)
+                for (int b = 0; b < NBAND; ++b) mbar_init(&tma_bars[b], 1);
+            // order earlier generic-proxy accesses of the buffer (a previous
+            // tile of this CTA) before the copies
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             for (int b = 0; b < NBAND; ++b) {
-                mbar_expect_tx(&s_bar[b], (unsigned)(2 * SHB * SP * sizeof(T)));
-                tma_load_2d(stage + b * SHB * SP, tm1, sx0, sy0 + b * SHB, &s_bar[b]);
-                tma_load_2d(stage + STG + b * SHB * SP, tm2, sx0, sy0 + b * SHB, &s_bar[b]);
+                mbar_expect_tx(&tma_bars[b], (unsigned)(2 * SHB * SP * sizeof(T)));
+                tma_load_2d(stage + b * SHB * SP, tm1, sx0, sy0 + b * SHB, &tma_bars[b]);
+                tma_load_2d(stage + STG + b * SHB * SP, tm2, sx0, sy0 + b * SHB, &tma_bars[b]);
             }
         }
-        __syncthreads();  // barriers initialised before anyone waits on them
-        bars = s_bar;
+        if (init_bars) __syncthreads();  // barriers initialised before anyone waits on them
+        bars = tma_bars;
     } else {
         for (int t = tid; t < 2 * SH * NV; t += NT) {
             const int f = t >= SH * NV ? 1 : 0;
@@ -513,14 +523,16 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
     if (interior) {
         const T *st2 = stage + STG;
         if (mode == V0_SAME)
-            products_tile_interior<T, KR, COH, V0_SAME, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, err);
+            products_tile_interior<T, KR, COH, V0_SAME, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity,
+                                                           err);
         else if (mode == V0_UP)
-            products_tile_interior<T, KR, COH, V0_UP, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, err);
+            products_tile_interior<T, KR, COH, V0_UP, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity, err);
         else
-            products_tile_interior<T, KR, COH, V0_ZERO, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, err);
+            products_tile_interior<T, KR, COH, V0_ZERO, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity,
+                                                           err);
         // every band has landed before the CTA can finish (no copy in flight at exit)
         if (bars && tid == 0)
-            for (int b = 0; b < NBAND; ++b) mbar_wait_bounded(&s_bar[b], 0, 1000000000LL);
+            for (int b = 0; b < NBAND; ++b) mbar_wait_bounded(&bars[b], parity, 1000000000LL);
     } else {
         constexpr int DY = NT / RW, DX = NT % RW;  // index step in rows and columns
         int ry = tid / RW, rx = tid - (tid / RW) * RW;
@@ -587,6 +599,7 @@ __device__ __forceinline__ void block_tile(const IterArgs &a, int mode, int bx, 
         const float S[5] = {q[0], q[PLANE], q[2 * PLANE], q[3 * PLANE], q[4 * PLANE]};
         epi.template apply<COH>(a, mode, gx, gy, S);
     }
+    return bars != nullptr;
 }
 
 // One tile per CTA; blockIdx.z selects the pair.
@@ -594,12 +607,14 @@ template <typename T, int KR>
 __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __grid_constant__ BlockParams prm)
 {
     extern __shared__ __align__(128) float4 smem_f4[];
+    __shared__ __align__(8) uint64_t s_bar[StageShape<T, KR>::NBAND];
     const int z = blockIdx.z;
-    if (prm.use_tma)
+    if (prm.use_tma) {
         block_tile<T, KR, false>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4, &prm.tm[z][0], &prm.tm[z][1],
-                                 prm.err);
-    else
+                                 prm.err, SolveStore(), s_bar, 0u, true);
+    } else {
         block_tile<T, KR, false>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -632,6 +647,8 @@ struct QueueParams {
     int *error;              // 0, or 1 + the unit whose wait expired
     long long timeout_ns;
     int spin_limit;
+    const CUtensorMap *tmaps;  // [pair][16 levels][2 frames] for TMA staging, or null
+    int *tma_err;              // set to 1 when a TMA wait expires, or null
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -650,7 +667,11 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __gr
     constexpr int TS = BlockShape<KR>::TS;
     extern __shared__ __align__(128) float4 smem_f4[];
     __shared__ int s_unit, s_fail;
+    __shared__ __align__(8) uint64_t s_bar[StageShape<T, KR>::NBAND];
     const int S = q.L * q.IT;
+    unsigned tma_uses = 0;  // TMA-staged tiles of this CTA so far
+    if (q.tmaps && threadIdx.x == 0)
+        for (int b = 0; b < StageShape<T, KR>::NBAND; ++b) mbar_init(&s_bar[b], 1);  // visible after the loop's first barrier
     for (;;) {
         if (threadIdx.x == 0) {
             s_unit = atomicAdd(q.head, 1);
@@ -715,7 +736,10 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __gr
             a.Vout = bp.vb[s & 1];
         }
         const int ntx = (a.W + TS - 1) / TS;
-        block_tile<T, KR, true>(a, mode, tile % ntx, tile / ntx, smem_f4);
+        const CUtensorMap *tm = q.tmaps ? q.tmaps + ((size_t)p * 16 + l) * 2 : nullptr;
+        if (block_tile<T, KR, true>(a, mode, tile % ntx, tile / ntx, smem_f4, tm, tm ? tm + 1 : nullptr, q.tma_err,
+                                    SolveStore(), q.tmaps ? s_bar : nullptr, tma_uses & 1u))
+            ++tma_uses;
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(q.done + s * q.npairs + p, 1);

@@ -146,6 +146,8 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     }
     const size_t pairs_off = off;
     off = align_up(off + sizeof(BatchPair) * n, 256);
+    const size_t tmaps_off = off;  // [pair][16 levels][2 frames] tensor maps
+    off = align_up(off + sizeof(CUtensorMap) * 32 * (size_t)n, 256);
     const size_t maxgroups = (size_t)S * n;
     const size_t goff_off = off;
     off = align_up(off + sizeof(int) * (maxgroups + 1), 256);
@@ -249,6 +251,35 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     e = cudaMemcpyAsync(base + pairs_off, bp.data(), sizeof(BatchPair) * n, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading pair descriptors");
 
+    // TMA tensor maps of every pair's level images (encoded once per layout:
+    // the arena, the pair sizes in order and the parameters fix the
+    // addresses); levels smaller than the staged box never use theirs
+    bool use_tma = h->tma_err_d != nullptr;
+    if (use_tma) {
+        std::string mkey = std::to_string(reinterpret_cast<uintptr_t>(base)) + "/" + std::to_string(p.storage) + "/" +
+                           std::to_string(KR) + "/" + std::to_string(L);
+        for (int i = 0; i < n; ++i) mkey += "/" + std::to_string(Hs[i][0]) + "x" + std::to_string(Ws[i][0]);
+        auto mit = h->batch_maps.find(mkey);
+        if (mit == h->batch_maps.end()) {
+            std::vector<CUtensorMap> maps(32 * (size_t)n);
+            memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+            for (int i = 0; i < n && use_tma; ++i)
+                for (int l = 0; l < L && use_tma; ++l)
+                    for (int f = 0; f < 2 && use_tma; ++f)
+                        use_tma = encode_block_map(&maps[((size_t)i * 16 + l) * 2 + f], lvl(i, f, l), Ws[i][l], Hs[i][l],
+                                                   pitch_for(Ws[i][l]), p.storage, KR);
+            if (use_tma) {
+                if (h->batch_maps.size() > 64) h->batch_maps.clear();
+                mit = h->batch_maps.emplace(mkey, std::move(maps)).first;
+            }
+        }
+        if (use_tma) {
+            e = cudaMemcpyAsync(base + tmaps_off, mit->second.data(), sizeof(CUtensorMap) * mit->second.size(),
+                                cudaMemcpyHostToDevice, cs);
+            if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading tensor maps");
+        }
+    }
+
     int dev = h->device, sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int occ = std::max(1, queue_occupancy(p.storage, KR));
@@ -288,6 +319,8 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     q.error = q.head + 1;
     q.timeout_ns = kWaitTimeoutNs;
     q.spin_limit = kWaitSpinLimit;
+    q.tmaps = use_tma ? reinterpret_cast<const CUtensorMap *>(base + tmaps_off) : nullptr;
+    q.tma_err = h->tma_err_d;
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tuning) {

@@ -135,7 +135,7 @@ struct ProfScope {
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (no link to
 // the driver library).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder_impl()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static bool tried = false;
@@ -153,31 +153,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Tensor maps of the level images for the block kernel's staged box: 2-D,
-// W x H elements, row stride pitch * element bytes, no swizzle.  Levels
-// smaller than the box never have an interior tile and keep cp.async.
+// Tensor maps of the level images for the block kernel's staged box (see
+// encode_block_map).  Levels smaller than the box never have an interior
+// tile and keep cp.async.
 void encode_tensor_maps(ofv_handle *h)
 {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     int cols = 0, rows = 0;
     block_stage_box(h->p.storage, h->p.kernel_radius, &cols, &rows);
-    const CUtensorMapDataType dt = h->p.storage == OFV_STORE_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                   : h->p.storage == OFV_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const int sb = store_bytes(h->p.storage);
     for (int l = 0; l < h->L; ++l) {
         h->tma_ok[l] = 0;
-        if (!enc || cols < 1 || h->Ws[l] < cols || h->Hs[l] < rows) continue;
+        if (cols < 1 || h->Ws[l] < cols || h->Hs[l] < rows) continue;
         bool ok = true;
-        for (int f = 0; f < h->nslots && ok; ++f) {
-            const cuuint64_t dim[2] = {(cuuint64_t)h->Ws[l], (cuuint64_t)h->Hs[l]};
-            const cuuint64_t stride[1] = {(cuuint64_t)h->pitch[l] * sb};
-            const cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)rows};
-            const cuuint32_t estr[2] = {1, 1};
-            ok = enc(&h->tmap[f][l], dt, 2, h->lvl[f][l], dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-        }
+        for (int f = 0; f < h->nslots && ok; ++f)
+            ok = encode_block_map(&h->tmap[f][l], h->lvl[f][l], h->Ws[l], h->Hs[l], h->pitch[l], h->p.storage,
+                                  h->p.kernel_radius);
         h->tma_ok[l] = ok ? 1 : 0;
     }
 }
@@ -423,6 +412,28 @@ ofv_status cuda_fail_msg(cudaError_t e, const char *where) { return cuda_fail(e,
 ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s)
 {
     return build_pyramids(h, frames, slots, nf, s);
+}
+
+// 2-D tensor map of a level image (W x H elements of the storage type, row
+// stride pitch elements) with the block kernel's TMA box for radius kr; no
+// swizzle, out-of-bounds fill unused (only boxes inside the image are
+// copied).  False when the encoder is unavailable or refuses.
+bool encode_block_map(CUtensorMap *m, const void *base, int W, int H, int pitch, int store, int kr)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder_impl();
+    int cols = 0, rows = 0;
+    block_stage_box(store, kr, &cols, &rows);
+    if (!enc || cols < 1) return false;
+    const CUtensorMapDataType dt = store == OFV_STORE_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : store == OFV_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dim[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t stride[1] = {(cuuint64_t)pitch * store_bytes(store)};
+    const cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, dt, 2, const_cast<void *>(base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 }  // namespace ofv
 

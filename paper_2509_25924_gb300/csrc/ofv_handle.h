@@ -80,6 +80,7 @@ struct ofv_handle {
     std::map<std::string, ofv::BatchTune> tune;
     ofv::BatchTune last_tune;
     int last_tuned;  // 1 if the last batched call ran the autotuner
+    std::map<std::string, std::vector<CUtensorMap>> batch_maps;  // tensor maps per batch layout
     // reverse mode: grow-only workspace (stage fields, sums, gradients)
     void *bw_arena;
     size_t bw_bytes;
@@ -100,4 +101,6 @@ struct ofv_handle {
 namespace ofv {
 // Steps 1-2 into the handle's pyramid slots (defined with the C ABI).
 ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s);
+// Tensor map of a level image with the block kernel's TMA box.
+bool encode_block_map(CUtensorMap *m, const void *base, int W, int H, int pitch, int store, int kr);
 }  // namespace ofv
