@@ -52,7 +52,7 @@ def test_frame_gradients_match_finite_differences(psl, kr, it):
         else:
             fd = _fd_dir(lambda X: _loss(I1, X, p, gu, gv), I2, d, 1e-6)
             an = float(np.sum(g2 * d))
-        assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (frame, fd, an)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (frame, fd, an)
 
 
 def test_single_pixel_perturbations_match_finite_differences():
@@ -66,8 +66,8 @@ def test_single_pixel_perturbations_match_finite_differences():
         d[i, j] = 1.0
         fd1 = _fd_dir(lambda X: _loss(X, I2, p, gu, gv), I1, d, 1e-6)
         fd2 = _fd_dir(lambda X: _loss(I1, X, p, gu, gv), I2, d, 1e-6)
-        assert abs(fd1 - g1[i, j]) <= 1e-5 * max(1.0, abs(g1[i, j])), (i, j, fd1, g1[i, j])
-        assert abs(fd2 - g2[i, j]) <= 1e-5 * max(1.0, abs(g2[i, j])), (i, j, fd2, g2[i, j])
+        assert abs(fd1 - g1[i, j]) <= 1e-6 * max(1.0, abs(g1[i, j])), (i, j, fd1, g1[i, j])
+        assert abs(fd2 - g2[i, j]) <= 1e-6 * max(1.0, abs(g2[i, j])), (i, j, fd2, g2[i, j])
 
 
 def test_prefilter_weight_gradient_matches_finite_differences():
@@ -88,11 +88,11 @@ def test_prefilter_weight_gradient_matches_finite_differences():
         d = rng.standard_normal((5, 5))
         fd = _fd_dir(lw, w, d, 1e-6)
         an = float(np.sum(gw * d))
-        assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (fd, an)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
     # frames through the pre-filter
     d = rng.standard_normal((H, W))
     fd = _fd_dir(lambda X: _loss(X, I2, p, gu, gv), I1, d, 1e-6)
-    assert abs(fd - float(np.sum(g1 * d))) <= 1e-5 * max(1.0, abs(fd))
+    assert abs(fd - float(np.sum(g1 * d))) <= 1e-6 * max(1.0, abs(fd))
 
 
 def test_gradient_is_linear_in_the_output_gradient():
