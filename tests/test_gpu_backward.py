@@ -3,12 +3,15 @@ torch.autograd wrapper, vs the FP64 oracle's reverse mode on the same seeded
 inputs.
 
 Tolerance (written here): relative L2 error of each gradient
-||g_gpu - g_oracle|| / ||g_oracle|| <= 2e-3 for FP32 storage on smooth
-textured pairs, 3e-2 on particle images and 5e-2 for FP16 level storage.
-The gradient multiplies FP32 round-off by the condition number of each 2x2
-system and by the slopes of the bilinear cells, so it is compared in the
-aggregate rather than element by element; float atomics make the last bits
-vary between runs.
+||g_gpu - g_oracle|| / ||g_oracle|| <= 1e-4 for FP32 storage (measured 2e-7
+to 2e-6 on smooth pairs and particle images, 8e-6 for the pre-filter
+weights) and 5e-3 for FP16 level storage (measured 6e-4).  The gradient
+multiplies FP32 round-off by the condition number of each 2x2 system and by
+the slopes of the bilinear cells, so it is compared in the aggregate rather
+than element by element; float atomics make the last bits vary between
+runs.  A finite difference of the GPU forward pass along random pre-filter
+directions checks the GPU gradient without the oracle (h = 3e-3, measured
+1.6e-4 relative, bound 2e-3).
 """
 import numpy as np
 import pytest
@@ -77,8 +80,8 @@ def test_frame_gradients_match_oracle(H, W, psl, kr, it):
     I1, I2, gu, gv = _smooth(H, W, seed=H + W)
     g1, g2, _ = gpu_grad(I1, I2, gu, gv, levels_psl=psl, kernel_radius=kr, iterations=it)
     o1, o2, _ = oracle_grad(I1, I2, gu, gv, psl=psl, kr=kr, it=it)
-    assert _rel(g1, o1) <= 2e-3, _rel(g1, o1)
-    assert _rel(g2, o2) <= 2e-3, _rel(g2, o2)
+    assert _rel(g1, o1) <= 1e-4, _rel(g1, o1)
+    assert _rel(g2, o2) <= 1e-4, _rel(g2, o2)
 
 
 def test_prefilter_weight_gradient_matches_oracle():
@@ -91,8 +94,42 @@ def test_prefilter_weight_gradient_matches_oracle():
     w = (w + 0.01 * rng.standard_normal((5, 5))).astype(np.float32)
     g1, g2, gw = gpu_grad(I1, I2, gu, gv, w25=w, levels_psl=1, kernel_radius=3, iterations=2)
     o1, o2, ow = oracle_grad(I1, I2, gu, gv, w25=w.astype(np.float64), psl=1, kr=3, it=2)
-    assert _rel(gw, ow) <= 2e-3, _rel(gw, ow)
-    assert _rel(g1, o1) <= 2e-3 and _rel(g2, o2) <= 2e-3
+    assert _rel(gw, ow) <= 1e-4, _rel(gw, ow)
+    assert _rel(g1, o1) <= 1e-4 and _rel(g2, o2) <= 1e-4
+
+
+def test_prefilter_gradient_matches_gpu_finite_differences():
+    # central differences of the GPU forward pass (FP32) along random
+    # directions of the 25 weights, against ofv_backward
+    H, W = 70, 66
+    I1, I2, gu, gv = _smooth(H, W, seed=4)
+    rng = np.random.default_rng(4)
+    w = np.zeros((5, 5))
+    w[2, 2] = 0.6
+    w[1:4, 1:4] += 0.05
+    w = (w + 0.01 * rng.standard_normal((5, 5))).astype(np.float32)
+    _, _, gw = gpu_grad(I1, I2, gu, gv, w25=w, levels_psl=1, kernel_radius=3, iterations=2)
+    p = ofv.ofv_default_params(input=ofv.OFV_IN_F32, prefilter=1, levels_psl=1, kernel_radius=3, iterations=2)
+    h = ofv.ofv_create(H, W, p)
+    try:
+        t1 = torch.from_numpy(I1).to(DEV)
+        t2 = torch.from_numpy(I2).to(DEV)
+        u = torch.empty((H, W), device=DEV)
+        v = torch.empty_like(u)
+
+        def loss(wx):
+            ofv.ofv_set_prefilter(h, torch.tensor(wx.reshape(25), dtype=torch.float32, device=DEV))
+            ofv.ofv_compute(h, t1, t2, u, v)
+            torch.cuda.synchronize()
+            return float((u.double().cpu().numpy() * gu).sum() + (v.double().cpu().numpy() * gv).sum())
+
+        for trial in range(2):
+            d = np.random.default_rng(100 + trial).standard_normal((5, 5))
+            fd = (loss(w + 3e-3 * d) - loss(w - 3e-3 * d)) / 6e-3
+            an = float((gw * d).sum())
+            assert abs(fd - an) <= 2e-3 * abs(an), (fd, an)
+    finally:
+        ofv.ofv_destroy(h)
 
 
 @pytest.mark.parametrize("dtype,bits", [(np.uint16, 12), (np.uint8, 8)])
@@ -105,15 +142,15 @@ def test_particle_images_counts_input(dtype, bits):
     gu, gv = rng.standard_normal(I1.shape), rng.standard_normal(I1.shape)
     g1, g2, _ = gpu_grad(I1, I2, gu, gv, bits=bits)
     o1, o2, _ = oracle_grad(I1, I2, gu, gv, bits=bits)
-    assert _rel(g1, o1) <= 3e-2, _rel(g1, o1)
-    assert _rel(g2, o2) <= 3e-2, _rel(g2, o2)
+    assert _rel(g1, o1) <= 1e-4, _rel(g1, o1)
+    assert _rel(g2, o2) <= 1e-4, _rel(g2, o2)
 
 
 def test_fp16_storage_gradient():
     I1, I2, gu, gv = _smooth(64, 80, seed=9)
     g1, g2, _ = gpu_grad(I1, I2, gu, gv, storage=ofv.OFV_STORE_F16, levels_psl=1, kernel_radius=3, iterations=2)
     o1, o2, _ = oracle_grad(I1, I2, gu, gv, psl=1, kr=3, it=2)
-    assert _rel(g1, o1) <= 5e-2 and _rel(g2, o2) <= 5e-2
+    assert _rel(g1, o1) <= 5e-3 and _rel(g2, o2) <= 5e-3
 
 
 def test_zero_output_gradient_gives_zero():
@@ -154,9 +191,9 @@ def test_autograd_function_matches_c_abi_and_oracle():
                (v * torch.from_numpy(gv.astype(np.float32)).to(DEV)).sum()
         loss.backward()
         o1, o2, ow = oracle_grad(I1, I2, gu, gv, w25=w.astype(np.float64), psl=1, kr=3, it=2)
-        assert _rel(t1.grad.cpu().numpy(), o1) <= 2e-3
-        assert _rel(t2.grad.cpu().numpy(), o2) <= 2e-3
-        assert _rel(tw.grad.cpu().numpy(), ow) <= 2e-3
+        assert _rel(t1.grad.cpu().numpy(), o1) <= 1e-4
+        assert _rel(t2.grad.cpu().numpy(), o2) <= 1e-4
+        assert _rel(tw.grad.cpu().numpy(), ow) <= 1e-4
         # forward of the autograd node is the plain estimator
         ou, ov = oracle.flow(I1.astype(np.float64), I2.astype(np.float64),
                              oracle.Params(psl=1, kr=3, it=2, prefilter=w.astype(np.float64)))
