@@ -98,6 +98,28 @@ def test_null_arguments_are_rejected():
     assert lib.ofv_destroy(None) == ofv.OFV_OK
 
 
+def test_null_arguments_of_the_later_entry_points_are_rejected():
+    lib = ctypes.CDLL(ofv.lib_path)
+    P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    lib.ofv_compute_sequence_host.argtypes = [P, I, P, Z, P, P, Z, P]
+    lib.ofv_compute_sequence_host.restype = I
+    assert lib.ofv_compute_sequence_host(None, 3, None, 0, None, None, 0, None) == ofv.OFV_ERR_INVALID_ARG
+    lib.ofv_backward.argtypes = [P] * 9
+    lib.ofv_backward.restype = I
+    assert lib.ofv_backward(None, None, None, None, None, None, None, None, None) == ofv.OFV_ERR_INVALID_ARG
+    lib.ofv_vorticity.argtypes = [I, I, I, P, P, Z, P, P]
+    lib.ofv_vorticity.restype = I
+    assert lib.ofv_vorticity(8, 8, 1, None, None, 64, None, None) == ofv.OFV_ERR_INVALID_ARG
+    lib.ofv_recirculation_area.argtypes = [I, I, I, P, Z, P, P, P]
+    lib.ofv_recirculation_area.restype = I
+    assert lib.ofv_recirculation_area(8, 8, 1, None, 64, None, None, None) == ofv.OFV_ERR_INVALID_ARG
+    # shape and stride checks come before any device work
+    dummy = ctypes.c_void_p(16)
+    assert lib.ofv_vorticity(0, 8, 1, dummy, dummy, 64, dummy, None) == ofv.OFV_ERR_SHAPE
+    assert lib.ofv_vorticity(8, 8, 1, dummy, dummy, 63, dummy, None) == ofv.OFV_ERR_INVALID_ARG
+    assert lib.ofv_recirculation_area(8, 8, 0, dummy, 64, None, dummy, None) == ofv.OFV_ERR_SHAPE
+
+
 def test_status_strings():
     assert ofv.ofv_status_string(ofv.OFV_ERR_SHAPE) == "OFV_ERR_SHAPE"
     assert ofv.ofv_status_string(99) == "OFV_ERR_UNKNOWN"
