@@ -395,6 +395,35 @@ def test_profile_counts_launches_and_bytes():
         ofv.ofv_destroy(h)
 
 
+def test_sequence_on_group_streams_equals_single_stream_order():
+    """With kernel timing on, a sequence runs in order on the caller's
+    stream; off, consecutive groups run on the library's group streams.
+    Both give the same fields bitwise, and the caller's stream orders the
+    work before and after the call."""
+    n, H, W = 29, 128, 160
+    F = synth.stream_frames(H, W, n, seed=8)
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(max_batch=2, **PARAMS))
+    try:
+        fr = torch.from_numpy(F).to(DEV)
+        s = torch.cuda.Stream()
+        out = []
+        for prof in (True, False):
+            ofv.ofv_profile_enable(h, prof)
+            u = torch.full((n - 1, H, W), float("nan"), device=DEV)
+            v = torch.full_like(u, float("nan"))
+            torch.cuda.synchronize()
+            with torch.cuda.stream(s):
+                ofv.ofv_compute_sequence(h, n, fr, H * W * 2, u, v, H * W, s)
+                us, vs = u.clone(), v.clone()  # queued on s: must see the finished fields
+            torch.cuda.synchronize()
+            out.append((us.cpu(), vs.cpu()))
+        ofv.ofv_profile_enable(h, False)
+        assert not torch.isnan(out[1][0]).any()
+        assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    finally:
+        ofv.ofv_destroy(h)
+
+
 # --------------------------------------------------------------------------
 # full-size workloads (the configurations the benchmark times)
 # --------------------------------------------------------------------------
