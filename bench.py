@@ -528,6 +528,13 @@ def live_loop(ofv, torch, synth, dev, stream, n_pairs=2000, ring=8, lanes=1):
         torch.cuda.synchronize()
         per = np.array([e0[i].elapsed_time(e1[i]) for i in range(n_pairs)])
         total = start.elapsed_time(end)
+        # algorithmic bytes of one field (kernel timing pass of the same pipeline)
+        ofv.ofv_profile_enable(hs[0], True)
+        ofv.ofv_compute(hs[0], frames[0], frames[1], u[0], v[0], stream)
+        field_bytes = sum(ofv.ofv_profile_read(hs[0], k)[2]
+                          for k in (ofv.OFV_K_INGEST, ofv.OFV_K_REDUCE, ofv.OFV_K_ITERATE))
+        ofv.ofv_profile_enable(hs[0], False)
+        torch.cuda.synchronize()
     finally:
         for g in graphs:
             ofv.ofv_graph_destroy(g)
@@ -538,7 +545,8 @@ def live_loop(ofv, torch, synth, dev, stream, n_pairs=2000, ring=8, lanes=1):
     return {"workload": f"5120x4096 u16 cylinder-wake stream, ring of {ring} pairs, one CUDA graph per pair, "
                         f"{lanes} handle/stream lane(s)",
             "pairs": n_pairs, "hz": n_pairs / (total / 1e3), "p50_ms": float(np.percentile(per, 50)),
-            "p99_ms": float(np.percentile(per, 99)), "max_ms": float(per.max())}
+            "p99_ms": float(np.percentile(per, 99)), "max_ms": float(per.max()),
+            "frac_of_hbm": field_bytes * n_pairs / (total / 1e3) / 1e9 / peaks()[0]}
 
 
 def batched_uneven(ofv, torch, synth, dev, stream, n_pairs=64, reps=5):
