@@ -31,6 +31,10 @@
  *     failure in the calling thread.
  *   - A handle is not thread-safe.  Distinct handles on distinct streams are
  *     independent.
+ *   - The fused kernels stage image tiles with TMA copies and wait for them
+ *     with a bound (2 s).  If a wait ever expires the kernel records it in a
+ *     handle-owned word of page-locked host memory, and every later compute
+ *     call on that handle returns OFV_ERR_TIMEOUT without enqueuing work.
  */
 #ifndef OFV_H
 #define OFV_H
