@@ -33,8 +33,9 @@
  *     independent.
  *   - The fused kernels stage image tiles with TMA copies and wait for them
  *     with a bound (2 s).  If a wait ever expires the kernel records it in a
- *     handle-owned word of page-locked host memory, and every later compute
- *     call on that handle returns OFV_ERR_TIMEOUT without enqueuing work.
+ *     handle-owned word of page-locked host memory, and every later compute,
+ *     graph-launch and backward call on that handle returns OFV_ERR_TIMEOUT
+ *     without enqueuing work.
  */
 #ifndef OFV_H
 #define OFV_H

@@ -567,6 +567,7 @@ extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2
             return cuda_fail_msg(e, "error pending before ofv_backward");
         }
     }
+    if (tma_expired(h)) return fail_msg(OFV_ERR_TIMEOUT, "ofv_backward: a TMA copy of an earlier launch did not complete");
     cudaStream_t s = (cudaStream_t)stream;
     BwLayout w;
     const size_t need = bw_layout(h, nullptr, &w);

@@ -122,6 +122,8 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
         cudaGetLastError();
         return cuda_fail_msg(e, "error pending before ofv_compute_batched");
     }
+    if (tma_expired(h))
+        return fail_msg(OFV_ERR_TIMEOUT, "ofv_compute_batched: a TMA copy of an earlier launch did not complete");
 
     // workspace: per pair two pyramids and two fields, then the queue data
     std::vector<size_t> lvl_off(2 * (size_t)n * L), vb_off(2 * (size_t)n), tmp_off(2 * (size_t)n, 0);

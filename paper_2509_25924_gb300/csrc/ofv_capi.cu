@@ -382,8 +382,7 @@ struct GroupRunner {
 
 ofv_status pending_error(const ofv_handle *h, const char *where)
 {
-    if (h->tma_err_h && *static_cast<volatile int *>(h->tma_err_h))
-        return fail(OFV_ERR_TIMEOUT, "%s: a TMA copy of an earlier launch did not complete", where);
+    if (tma_expired(h)) return fail(OFV_ERR_TIMEOUT, "%s: a TMA copy of an earlier launch did not complete", where);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -914,6 +913,7 @@ ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float
 ofv_status ofv_graph_launch(ofv_graph *g, ofv_stream_t s)
 {
     if (!g) return fail(OFV_ERR_INVALID_ARG, "graph is NULL");
+    if (tma_expired(g->h)) return fail(OFV_ERR_TIMEOUT, "ofv_graph_launch: a TMA copy of an earlier launch did not complete");
     DeviceGuard dg(g->h->device);
     cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the graph");

@@ -103,4 +103,9 @@ namespace ofv {
 ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s);
 // Tensor map of a level image with the block kernel's TMA box.
 bool encode_block_map(CUtensorMap *m, const void *base, int W, int H, int pitch, int store, int kr);
+// True once a kernel of this handle recorded an expired TMA wait.
+inline bool tma_expired(const ofv_handle *h)
+{
+    return h->tma_err_h && *static_cast<volatile int *>(h->tma_err_h) != 0;
+}
 }  // namespace ofv
