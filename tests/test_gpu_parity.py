@@ -225,6 +225,36 @@ def test_ragged_shapes_and_minimum_levels(H, W, psl, kr, it):
     compare(u, v, ou, ov, nd, label=f"{H}x{W} psl={psl} kr={kr} it={it}", max_masked=0.05, sens=sens)
 
 
+def _random_configs(n=12, seed=20250930):
+    r = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        psl, kr, it = int(r.integers(0, 4)), int(r.integers(1, 11)), int(r.integers(1, 4))
+        minsz = max(8, 2 * kr + 1) * (1 << psl)
+        H, W = int(r.integers(minsz, minsz + 150)), int(r.integers(minsz, minsz + 150))
+        dm = 0.9 if psl == 0 else 2.5  # PSL 0 (no pyramid) resolves displacements of about 1 px (Sec. 6)
+        d = (float(r.uniform(-dm, dm)), float(r.uniform(-dm, dm)))
+        store = int(r.integers(0, 3))
+        out.append((H, W, psl, kr, it, d, store, int(r.integers(0, 2**31))))
+    return out
+
+
+@pytest.mark.parametrize("H,W,psl,kr,it,d,store,seed", _random_configs())
+def test_random_configurations_match_oracle(H, W, psl, kr, it, d, store, seed):
+    """Seeded random shapes, pyramid depths, window radii, iteration counts,
+    displacements and storage types: FP32 by the max rule, FP16 / BF16 by
+    the RMS rule."""
+    I1, I2 = synth.translation_pair(H, W, d, seed=seed % 100000, kind=synth.OUT_F32)
+    u, v = gpu_flow(I1, I2, levels_psl=psl, kernel_radius=kr, iterations=it, storage=store)
+    ou, ov, nd, _ = oracle_flow(I1, I2, psl=psl, kr=kr, it=it)
+    label = f"{H}x{W} psl={psl} kr={kr} it={it} d={d[0]:.2f},{d[1]:.2f} store={store}"
+    if store == ofv.OFV_STORE_F32:
+        sens = fp32_sensitivity(I1, I2, psl=psl, kr=kr, it=it)
+        compare(u, v, ou, ov, nd, label=label, max_masked=0.05, sens=sens)
+    else:
+        compare(u, v, ou, ov, nd, rms_tol=REDUCED_RMS_TOL, label=label, max_masked=0.05)
+
+
 @pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_TILE])
 def test_large_displacement_uses_global_taps(path):
     """A (9.3, -8.7) px shift with PSL 3: at level 0 the warp offsets exceed
