@@ -185,28 +185,61 @@ cudaError_t launch_ingest_frames(const IngestArgs *f, int nframes, int store, cu
 // ---------------------------------------------------------------------------
 struct ReducePair { ReduceArgs f[kMaxFramesPerLaunch]; };
 
+// Two horizontally adjacent outputs j = 2t, 2t+1 per thread: they share
+// input columns 4t-2 .. 4t+4 (7 loads per row instead of 10), loaded as
+// 8-byte pairs for FP32 storage away from the left and right borders.  Each
+// output is accumulated in the same order as the one-output form.
+template <typename TS>
+__device__ __forceinline__ void load7(const TS *row, int c0, int Ws, bool inside, float v[7])
+{
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] = ld_store(row + (inside ? c0 + k : clampi(c0 + k, 0, Ws - 1)));
+}
+template <>
+__device__ __forceinline__ void load7<float>(const float *row, int c0, int Ws, bool inside, float v[7])
+{
+    if (inside) {  // c0 even, row 8-byte aligned
+        const float2 a = __ldg(reinterpret_cast<const float2 *>(row + c0));
+        const float2 b = __ldg(reinterpret_cast<const float2 *>(row + c0 + 2));
+        const float2 c = __ldg(reinterpret_cast<const float2 *>(row + c0 + 4));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+        v[6] = __ldg(row + c0 + 6);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] = __ldg(row + clampi(c0 + k, 0, Ws - 1));
+}
+
 template <typename TS>
 __global__ void __launch_bounds__(256) k_reduce(ReducePair p)
 {
     const ReduceArgs &a = p.f[blockIdx.z];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= a.Hd || j >= a.Wd) return;
+    const int j0 = 2 * t;
+    if (i >= a.Hd || j0 >= a.Wd) return;
     const TS *src = static_cast<const TS *>(a.src);
     const float c[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
-    int cols[5];
-#pragma unroll
-    for (int b = 0; b < 5; ++b) cols[b] = clampi(2 * j + b - 2, 0, a.Ws - 1);
-    float acc = 0.f;
+    const int c0 = 2 * j0 - 2;  // first input column of output j0
+    const bool inside = c0 >= 0 && c0 + 6 <= a.Ws - 1;
+    float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
         const TS *row = src + (int64_t)clampi(2 * i + r - 2, 0, a.Hs - 1) * a.spitch;
-        float h = 0.f;
+        float v[7];
+        load7<TS>(row, c0, a.Ws, inside, v);
+        float h0 = 0.f, h1 = 0.f;
 #pragma unroll
-        for (int b = 0; b < 5; ++b) h = fmaf(c[b], ld_store(row + cols[b]), h);
-        acc = fmaf(c[r], h, acc);
+        for (int b = 0; b < 5; ++b) {
+            h0 = fmaf(c[b], v[b], h0);
+            h1 = fmaf(c[b], v[b + 2], h1);
+        }
+        acc0 = fmaf(c[r], h0, acc0);
+        acc1 = fmaf(c[r], h1, acc1);
     }
-    st_store(static_cast<TS *>(a.dst) + (int64_t)i * a.dpitch + j, acc);
+    TS *dst = static_cast<TS *>(a.dst) + (int64_t)i * a.dpitch;
+    st_store(dst + j0, acc0);
+    if (j0 + 1 < a.Wd) st_store(dst + j0 + 1, acc1);
 }
 
 // Reduce one level of nframes (1 .. kMaxFramesPerLaunch) frames in one launch.
@@ -216,7 +249,7 @@ cudaError_t launch_reduce_frames(const ReduceArgs *f, int nframes, int store, cu
     ReducePair p;
     for (int k = 0; k < nframes; ++k) p.f[k] = f[k];
     dim3 blk(32, 8);
-    dim3 grd((f[0].Wd + 31) / 32, (f[0].Hd + 7) / 8, nframes);
+    dim3 grd(((f[0].Wd + 1) / 2 + 31) / 32, (f[0].Hd + 7) / 8, nframes);
     switch (store) {
     case ST_F16: k_reduce<__half><<<grd, blk, 0, s>>>(p); break;
     case ST_BF16: k_reduce<__nv_bfloat16><<<grd, blk, 0, s>>>(p); break;
