@@ -49,7 +49,8 @@ class _Params(ctypes.Structure):
         ("psl", ctypes.c_int), ("kr", ctypes.c_int), ("it", ctypes.c_int), ("nr", ctypes.c_int),
         ("bits", ctypes.c_int), ("prefilter", ctypes.c_int), ("w25", ctypes.c_void_p),
         ("eps_rel", ctypes.c_double), ("eps_abs", ctypes.c_double), ("eps_n", ctypes.c_double),
-        ("increment_form", ctypes.c_int),
+        ("increment_form", ctypes.c_int), ("win_sigma", ctypes.c_double),
+        ("u_init", ctypes.c_void_p), ("v_init", ctypes.c_void_p),
     ]
 
 
@@ -69,8 +70,10 @@ def _load():
             lib.orc_bilinear.restype = D
             lib.orc_central_diff.argtypes = [I, I, P, P, P]
             lib.orc_box_sum.argtypes = [I, I, P, I, P]
+            lib.orc_window_sum.argtypes = [I, I, P, I, D, P]
+            lib.orc_decimate_field.argtypes = [I, I, P, P, I, P, P]
             lib.orc_upsample.argtypes = [I, I, P, P, I, I, P, P]
-            lib.orc_iterate.argtypes = [I, I, P, P, P, P, I, D, D, I, P, P, P, P]
+            lib.orc_iterate.argtypes = [I, I, P, P, P, P, I, D, D, D, I, P, P, P, P]
             lib.orc_iterate.restype = I
             lib.orc_ingest.argtypes = [I, I, P, ctypes.POINTER(_Params), P]
             lib.orc_ingest.restype = I
@@ -99,7 +102,8 @@ def _p(a: np.ndarray):
 class Params:
     """Estimator parameters (Sec. 2, Table 2): PSL pyramid sub-levels, KR
     kernel radius, IT Gauss-Newton iterations per level, NR normalization
-    radius (0 = off)."""
+    radius (0 = off).  Variants: increment_form, win_sigma > 0 (Gaussian
+    window weights), init = (u0, v0) level-0 initial field (warm start)."""
     psl: int = 2
     kr: int = 4
     it: int = 3
@@ -110,17 +114,27 @@ class Params:
     eps_abs: float = EPS_ABS
     eps_n: float = EPS_N
     increment_form: bool = False
+    win_sigma: float = 0.0
+    init: tuple | None = None
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Params:
         s = _Params()
         s.psl, s.kr, s.it, s.nr, s.bits = self.psl, self.kr, self.it, self.nr, self.bits
+        self._keep = []
         if self.prefilter is not None:
             w = _f64(self.prefilter).reshape(25)
-            self._keep = [w]
+            self._keep.append(w)
             s.prefilter, s.w25 = 1, w.ctypes.data
         else:
             s.prefilter, s.w25 = 0, None
+        s.win_sigma = float(self.win_sigma)
+        if self.init is not None:
+            u0, v0 = _f64(self.init[0]), _f64(self.init[1])
+            self._keep += [u0, v0]
+            s.u_init, s.v_init = u0.ctypes.data, v0.ctypes.data
+        else:
+            s.u_init, s.v_init = None, None
         s.eps_rel, s.eps_abs, s.eps_n = self.eps_rel, self.eps_abs, self.eps_n
         s.increment_form = 1 if self.increment_form else 0
         return s
@@ -184,6 +198,24 @@ def box_sum(a, kr: int) -> np.ndarray:
     return out
 
 
+def window_sum(a, kr: int, sigma: float) -> np.ndarray:
+    """Window sums with Gaussian weights exp(-(a^2+b^2)/(2 sigma^2)) (box for sigma <= 0)."""
+    a = _f64(a)
+    out = np.empty_like(a)
+    _load().orc_window_sum(a.shape[0], a.shape[1], _p(a), kr, float(sigma), _p(out))
+    return out
+
+
+def decimate_field(u, v, level: int):
+    """The level-`level` warm-start field from a level-0 field: V(2^l i, 2^l j) / 2^l."""
+    u, v = _f64(u), _f64(v)
+    H, W = u.shape
+    h, w = level_sizes(H, W, level)[level]
+    uc = np.empty((h, w)); vc = np.empty((h, w))
+    _load().orc_decimate_field(H, W, _p(u), _p(v), level, _p(uc), _p(vc))
+    return uc, vc
+
+
 def upsample(uc, vc, H: int, W: int):
     uc, vc = _f64(uc), _f64(vc)
     u = np.empty((H, W))
@@ -193,13 +225,13 @@ def upsample(uc, vc, H: int, W: int):
 
 
 def iterate(P1, P2, u0, v0, kr: int, eps_rel: float = EPS_REL, eps_abs: float = EPS_ABS,
-            increment_form: bool = False):
+            increment_form: bool = False, win_sigma: float = 0.0):
     """One Gauss-Newton iteration at one level: returns (u, v, ndet, guarded)."""
     P1, P2, u0, v0 = _f64(P1), _f64(P2), _f64(u0), _f64(v0)
     H, W = P1.shape
     u = np.empty((H, W)); v = np.empty((H, W)); nd = np.empty((H, W))
     g = np.empty((H, W), dtype=np.uint8)
-    rc = _load().orc_iterate(H, W, _p(P1), _p(P2), _p(u0), _p(v0), kr, eps_rel, eps_abs,
+    rc = _load().orc_iterate(H, W, _p(P1), _p(P2), _p(u0), _p(v0), kr, float(win_sigma), eps_rel, eps_abs,
                              1 if increment_form else 0, _p(u), _p(v), _p(nd), _p(g))
     if rc:
         raise MemoryError("orc_iterate failed")

@@ -21,7 +21,9 @@
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - window N(m): square (2KR+1)^2 box of uniform weight, truncated at the
- *     image border (terms outside the image count zero);
+ *     image border (terms outside the image count zero); as a variant, the
+ *     same box with Gaussian weights exp(-(a^2 + b^2) / (2 sigma^2)) of the
+ *     offset (a, b) from the centre (orc_params.win_sigma > 0);
  *   - the warp of Eq. 2 is applied per pixel with the current field V0(k) and
  *     the 2x2 system is solved for V(m) directly:
  *       H V = sum_k G_k (G_k . V0(k) - It_k)
@@ -37,7 +39,10 @@
  *   - normalization: zero mean, unit deviation over the (2NR+1)^2 box,
  *     I~ = (I - mu) / sqrt(sigma^2 + eps_n^2), eps_n = 1e-2 (parity unpinned);
  *   - guard: if Sxx + Syy <= eps_abs or det <= eps_rel (Sxx + Syy)^2 the
- *     pixel keeps V0(m) (parity unpinned).
+ *     pixel keeps V0(m) (parity unpinned);
+ *   - warm start (a variant for time-resolved sequences): the coarsest level
+ *     starts from a given level-0 field sampled at the pixels that level
+ *     keeps, V_L(i, j) = V(2^L i, 2^L j) / 2^L, instead of from zero.
  *
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off ofv_oracle.c -lm
  */
@@ -185,6 +190,49 @@ void orc_box_sum(int H, int W, const double *in, int kr, double *out)
         }
 }
 
+/* Window sum with Gaussian weights: out(i,j) = sum over the in-image taps
+   (i+a, j+b), |a|, |b| <= KR, of exp(-(a^2 + b^2) / (2 sigma^2)) in(i+a, j+b).
+   sigma <= 0 gives the uniform box (orc_box_sum). */
+void orc_window_sum(int H, int W, const double *in, int kr, double sigma, double *out)
+{
+    if (!(sigma > 0.0)) {
+        orc_box_sum(H, W, in, kr, out);
+        return;
+    }
+    const double c = 1.0 / (2.0 * sigma * sigma);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double s = 0.0;
+            for (int a = -kr; a <= kr; ++a) {
+                int ii = i + a;
+                if (ii < 0 || ii >= H) continue;
+                for (int b = -kr; b <= kr; ++b) {
+                    int jj = j + b;
+                    if (jj < 0 || jj >= W) continue;
+                    s += exp(-(double)(a * a + b * b) * c) * in[(int64_t)ii * W + jj];
+                }
+            }
+            out[(int64_t)i * W + j] = s;
+        }
+}
+
+/* Warm start: the level-`level` field taken from a level-0 field (H x W) at
+   the pixels that level keeps (even-sample decimation `level` times puts
+   level pixel i at level-0 pixel 2^level i), in level units (/ 2^level). */
+void orc_decimate_field(int H, int W, const double *u, const double *v, int level, double *uc, double *vc)
+{
+    int Hs[16], Ws[16];
+    orc_level_sizes(H, W, level, Hs, Ws);
+    const int f = 1 << level;
+    for (int i = 0; i < Hs[level]; ++i)
+        for (int j = 0; j < Ws[level]; ++j) {
+            const int64_t src = (int64_t)(f * i) * W + (int64_t)f * j;
+            uc[(int64_t)i * Ws[level] + j] = u[src] / f;
+            vc[(int64_t)i * Ws[level] + j] = v[src] / f;
+        }
+}
+
 /* ------------------------------------------------------------------ */
 /* Step 4: carry the field of level l+1 (Hc x Wc) to level l (H x W):     */
 /* coarse pixel i sits at fine 2i, so V_l(x, y) = 2 V_{l+1}(x/2, y/2),    */
@@ -214,8 +262,8 @@ void orc_upsample(int Hc, int Wc, const double *uc, const double *vc, int H, int
 /* below eps_abs) and guarded = 1 where V0(m) was kept.                    */
 /* ------------------------------------------------------------------ */
 int orc_iterate(int H, int W, const double *P1, const double *P2, const double *u0,
-                const double *v0, int kr, double eps_rel, double eps_abs, int increment_form,
-                double *u, double *v, double *ndet, unsigned char *guarded)
+                const double *v0, int kr, double win_sigma, double eps_rel, double eps_abs,
+                int increment_form, double *u, double *v, double *ndet, unsigned char *guarded)
 {
     int64_t N = (int64_t)H * W;
     double *buf = (double *)malloc(sizeof(double) * (size_t)N * 14);
@@ -254,11 +302,11 @@ int orc_iterate(int H, int W, const double *P1, const double *P2, const double *
         }
 
     /* window sums over N(m) */
-    orc_box_sum(H, W, Gxx, kr, Sxx);
-    orc_box_sum(H, W, Gxy, kr, Sxy);
-    orc_box_sum(H, W, Gyy, kr, Syy);
-    orc_box_sum(H, W, Gxr, kr, Sxr);
-    orc_box_sum(H, W, Gyr, kr, Syr);
+    orc_window_sum(H, W, Gxx, kr, win_sigma, Sxx);
+    orc_window_sum(H, W, Gxy, kr, win_sigma, Sxy);
+    orc_window_sum(H, W, Gyy, kr, win_sigma, Syy);
+    orc_window_sum(H, W, Gxr, kr, win_sigma, Sxr);
+    orc_window_sum(H, W, Gyr, kr, win_sigma, Syr);
 
     /* guarded 2x2 solve per pixel */
 #pragma omp parallel for schedule(static)
@@ -360,11 +408,14 @@ int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_par
     }
     if (guard0) memset(guard0, 0, (size_t)N);
 
-    /* steps 3-5: coarse to fine; the coarsest level starts from V = 0 */
+    /* steps 3-5: coarse to fine; the coarsest level starts from V = 0, or
+       from the decimated initial field (warm start) */
     for (int l = L - 1; l >= 0; --l) {
         int h = Hs[l], w = Ws[l];
         int64_t n = (int64_t)h * w;
-        if (l == L - 1) {
+        if (l == L - 1 && p->u_init && p->v_init) {
+            orc_decimate_field(H, W, p->u_init, p->v_init, l, cu, cv);
+        } else if (l == L - 1) {
             memset(cu, 0, sizeof(double) * (size_t)n);
             memset(cv, 0, sizeof(double) * (size_t)n);
         } else {
@@ -375,7 +426,7 @@ int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_par
         }
         for (int t = 0; t < p->it; ++t) {
             int last = (l == 0 && t == p->it - 1);
-            if (orc_iterate(h, w, pyr1[l], pyr2[l], cu, cv, p->kr, p->eps_rel, p->eps_abs,
+            if (orc_iterate(h, w, pyr1[l], pyr2[l], cu, cv, p->kr, p->win_sigma, p->eps_rel, p->eps_abs,
                             p->increment_form, nu, nv, last ? ndet : NULL, g)) {
                 rc = 1;
                 goto done;

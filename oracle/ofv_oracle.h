@@ -23,6 +23,9 @@ typedef struct {
     double eps_abs;       /* absolute trace guard */
     double eps_n;         /* normalization floor */
     int increment_form;   /* 1: V = V0(m) + H^-1 sum G(-It) instead of the direct form */
+    double win_sigma;     /* > 0: Gaussian window weights exp(-(a^2+b^2)/(2 sigma^2)); 0: uniform box */
+    const double *u_init; /* initial level-0 field (warm start), or NULL for V = 0 at the coarsest level */
+    const double *v_init;
 } orc_params;
 
 void orc_scale(int64_t n, const double *raw, int bits, double *out);
@@ -32,11 +35,13 @@ void orc_reduce(int H, int W, const double *P, double *out);
 double orc_bilinear(const double *P, int H, int W, double px, double py);
 void orc_central_diff(int H, int W, const double *P, double *Dx, double *Dy);
 void orc_box_sum(int H, int W, const double *in, int kr, double *out);
+void orc_window_sum(int H, int W, const double *in, int kr, double sigma, double *out);
 void orc_upsample(int Hc, int Wc, const double *uc, const double *vc, int H, int W,
                   double *u, double *v);
 int orc_iterate(int H, int W, const double *P1, const double *P2, const double *u0,
-                const double *v0, int kr, double eps_rel, double eps_abs, int increment_form,
-                double *u, double *v, double *ndet, unsigned char *guarded);
+                const double *v0, int kr, double win_sigma, double eps_rel, double eps_abs,
+                int increment_form, double *u, double *v, double *ndet, unsigned char *guarded);
+void orc_decimate_field(int H, int W, const double *u, const double *v, int level, double *uc, double *vc);
 void orc_level_sizes(int H, int W, int psl, int *Hs, int *Ws);
 int orc_ingest(int H, int W, const double *raw, const orc_params *p, double *out);
 int orc_pyramid(int H, int W, const double *raw, const orc_params *p, double *out);
