@@ -166,7 +166,7 @@ def run_reference(args, ws, rank):
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_block.cuh", "iter_math.cuh", "ofv_common.cuh"):
+    for f in ("k_block.cuh", "k_block_inst.cuh", "iter_math.cuh", "ofv_common.cuh"):
         with open(os.path.join(ROOT, "paper_2509_25924_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -307,6 +307,7 @@ def run_ours(args, ws, rank, local):
         line["live_21Mp"] = live_loop(ofv, torch, synth, dev, stream)
         line["live_21Mp_3lanes"] = live_loop(ofv, torch, synth, dev, stream, ring=9, lanes=3)
         line["live_21Mp_paper_params"] = live_loop(ofv, torch, synth, dev, stream, n_pairs=500, paper_params=True)
+        line["variants_1Mp"] = variants(ofv, torch, synth, dev, stream, frames, u, v)
         line["paper_perf_set"] = paper_perf_set(ofv, torch, synth, dev, stream)
         line["batched_64_uneven"] = batched_uneven(ofv, torch, synth, dev, stream)
 
@@ -456,6 +457,44 @@ def derived_rates(ofv, torch, u, v, H, W, n, stream, reps=5):
         sec = e0.elapsed_time(e1) / 1e3 / reps
         out[name] = {"fields_per_s": n / sec, "gbs": n * N * bpp / sec / 1e9, "frac_of_hbm": n * N * bpp / sec / 1e9 / peak}
     del omega, counts
+    return out
+
+
+def variants(ofv, torch, synth, dev, stream, frames, u, v, n_frames=201, reps=5):
+    """The estimator variants on the first n_frames of the 1 Mp stream:
+    fields/s and the error against the analytic displacement of the stream
+    (Rankine vortex plus uniform shift), mean and 99th percentile of |V -
+    V_true| over pixels at least 16 px from the border, over the last 100
+    pairs.  Warm start d: pair k starts from pair k-d's field."""
+    H, W = H1, W1
+    tu, tv = synth.stream_field(H, W).grid(H, W)
+    tu = torch.from_numpy(tu.astype(np.float32)).to(dev)
+    tv = torch.from_numpy(tv.astype(np.float32)).to(dev)
+    cases = [
+        ("box_direct_psl2_it3", {}),
+        ("gauss_sigma2_psl2_it3", dict(window=ofv.OFV_WINDOW_GAUSS, window_sigma=2.0)),
+        ("increment_psl2_it3", dict(increment_form=1)),
+        ("warm_d8_psl2_it3", dict(warm_start=8)),
+        ("warm_d8_psl0_it2", dict(warm_start=8, levels_psl=0, iterations=2)),
+        ("warm_d8_psl0_it1", dict(warm_start=8, levels_psl=0, iterations=1)),
+        ("warm_d1_psl0_it2", dict(warm_start=1, levels_psl=0, iterations=2)),
+        ("cold_psl0_it2", dict(levels_psl=0, iterations=2)),
+    ]
+    out = {}
+    s = (slice(None), slice(16, H - 16), slice(16, W - 16))
+    for name, kw in cases:
+        h = ofv.ofv_create(H, W, ofv.ofv_default_params(**kw))
+        try:
+            rate = time_sequence(ofv, torch, h, frames, n_frames, H, W, u, v, stream, reps)
+            k0 = n_frames - 1 - 100
+            err = torch.hypot(u[k0:n_frames - 1][s] - tu[s[1:]], v[k0:n_frames - 1][s] - tv[s[1:]]).flatten()
+            smp = err[torch.randint(0, err.numel(), (1 << 22,), device=dev, generator=None)]
+            out[name] = {"fields_per_s": rate, "err_mean_px": float(err.mean()),
+                         "err_p99_px": float(torch.quantile(smp, 0.99))}
+        finally:
+            ofv.ofv_destroy(h)
+    out["stream"] = (f"first {n_frames} frames of the 1 Mp bench stream, KR 4, FP32 storage, fused path; "
+                     "defaults PSL 2 IT 3 unless named; error over the last 100 pairs")
     return out
 
 

@@ -76,6 +76,12 @@ typedef enum { OFV_STORE_F32 = 0, OFV_STORE_F16 = 1, OFV_STORE_BF16 = 2 } ofv_st
    five product planes through device memory (kept for comparison). */
 typedef enum { OFV_PATH_FUSED = 0, OFV_PATH_PLAIN = 1, OFV_PATH_TILE = 2 } ofv_path_t;
 
+/* Weights of the window N(m) of Eq. 2.  The paper names only its radius KR
+   (Sec. 2); the default is the uniform (2KR+1)^2 box.  OFV_WINDOW_GAUSS
+   weights tap (a, b) of the box by exp(-(a^2 + b^2) / (2 sigma^2)), sigma =
+   window_sigma (a variant; the box is still truncated at the image border). */
+typedef enum { OFV_WINDOW_BOX = 0, OFV_WINDOW_GAUSS = 1 } ofv_window_t;
+
 typedef struct {
     int levels_psl;     /* PSL >= 0 pyramid sub-levels; levels = PSL + 1 (Sec. 2; Table 2 uses 2..4) */
     int kernel_radius;  /* KR, 1..16: window (2KR+1)^2, uniform weights (Sec. 2; Table 2 uses 2..7) */
@@ -92,12 +98,22 @@ typedef struct {
     int max_batch;      /* pairs of a sequence per iteration launch, 0..8; 0 = auto (as many as keep
                            about 16 Mp per launch).  Each costs three more pyramids and six fields
                            of workspace (three groups of a sequence are in flight). */
+    /* Estimator variants (defaults: 0, i.e. the estimator as read from Sec. 2). */
+    int window;         /* ofv_window_t (every forward path; ofv_backward covers the box only) */
+    float window_sigma; /* OFV_WINDOW_GAUSS: sigma in px, finite and > 0 */
+    int increment_form; /* 1: each Gauss-Newton step solves for the increment,
+                           V(m) = V0(m) + H^-1 sum G (-It), instead of H V = sum G (G.V0 - It) */
+    int warm_start;     /* sequences only, 0..8: 0 = every pair starts from V = 0; d > 0 = pair k >= d
+                           starts its coarsest level from pair k-d's field sampled at that level's pixels,
+                           V_L(i, j) = V(2^L i, 2^L j) / 2^L (pairs k < d start from 0).  Pairs then run in
+                           groups of d per launch; d must not exceed the handle's pairs-per-launch. */
 } ofv_params;
 
 typedef struct ofv_handle ofv_handle;
 
 /* Fill *p with the defaults: PSL 2, KR 4, IT 3, NR 0, 12-bit uint16 input,
-   FP32 storage, fused path, no pre-filter, guards 1e-6 / 1e-20, floor 1e-2. */
+   FP32 storage, fused path, no pre-filter, guards 1e-6 / 1e-20, floor 1e-2,
+   box window, direct form, no warm start. */
 void ofv_default_params(ofv_params *p);
 
 /* Create a handle for H x W frames with parameters *p (copied).  Allocates
@@ -138,7 +154,9 @@ ofv_status ofv_compute_host(ofv_handle *h, const void *I1, const void *I2, float
    handle's pairs-per-launch; with the fused path consecutive groups run on
    library-owned streams so that one group's coarse levels overlap another's
    fine levels.  Work queued on s before the call runs first, and s reaches
-   the end of the call only when every field is written. */
+   the end of the call only when every field is written.  With
+   params.warm_start = d, pair k >= d starts from pair k-d's field (groups of
+   d pairs; OFV_ERR_INVALID_ARG if d exceeds the pairs-per-launch). */
 ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
                                 size_t frame_stride_bytes, float *u, float *v, size_t field_stride,
                                 ofv_stream_t s);
@@ -195,7 +213,9 @@ ofv_status ofv_recirculation_area(int H, int W, int n, const float *u, size_t fi
  * bilinear cell boundary the derivative is that of the cell floor() picks.
  * Float atomics scatter the gradients, so the last bits vary between runs.
  * The handle's pyramid slots are overwritten (as by ofv_compute).
- * OFV_ERR_UNSUPPORTED when local normalization is on (NR > 0). */
+ * OFV_ERR_UNSUPPORTED when local normalization is on (NR > 0), with the
+ * Gaussian window or with the increment form (the reverse mode covers the
+ * direct form with the uniform box). */
 ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2, const float *gu,
                         const float *gv, float *gI1, float *gI2, float *gw25, ofv_stream_t s);
 

@@ -29,6 +29,7 @@ OFV_OK, OFV_ERR_INVALID_ARG, OFV_ERR_SHAPE, OFV_ERR_ALLOC, OFV_ERR_CUDA, OFV_ERR
 OFV_IN_U8, OFV_IN_U16, OFV_IN_F32 = range(3)
 OFV_STORE_F32, OFV_STORE_F16, OFV_STORE_BF16 = range(3)
 OFV_PATH_FUSED, OFV_PATH_PLAIN, OFV_PATH_TILE = range(3)
+OFV_WINDOW_BOX, OFV_WINDOW_GAUSS = range(2)
 OFV_K_INGEST, OFV_K_REDUCE, OFV_K_ITERATE, OFV_K_COUNT = range(4)
 OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -58,6 +59,8 @@ class Params(ctypes.Structure):
         ("storage", ctypes.c_int), ("path", ctypes.c_int), ("prefilter", ctypes.c_int),
         ("det_rel_eps", ctypes.c_float), ("det_abs_eps", ctypes.c_float), ("norm_eps", ctypes.c_float),
         ("max_batch", ctypes.c_int),
+        ("window", ctypes.c_int), ("window_sigma", ctypes.c_float), ("increment_form", ctypes.c_int),
+        ("warm_start", ctypes.c_int),
     ]
 
 

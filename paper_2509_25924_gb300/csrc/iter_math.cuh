@@ -5,12 +5,15 @@
 //   p1 = k - V0/2, p2 = k + V0/2 (symmetric midpoint warp, Eq. 2)
 //   A = P1(p1), B = P2(p2)                 bilinear, clamp-to-edge
 //   g1 = (Dx P1, Dy P1)(p1), g2 likewise   central differences sampled bilinearly
-//   G = (g1 + g2) / 2, It = B - A, r = G . V0 - It
+//   G = (g1 + g2) / 2, It = B - A, r = G . V0 - It (r = -It in the
+//   increment form)
 //   products: Gx^2, Gx Gy, Gy^2, Gx r, Gy r
 // and for pixel m, with S the window sums of the products over N(m):
-//   H = [[Sxx, Sxy], [Sxy, Syy]], V(m) = H^-1 (Sxr, Syr) by Cramer's rule,
-//   unless Sxx + Syy <= eps_abs or det <= eps_rel (Sxx + Syy)^2, where V0(m)
-//   is kept.
+//   H = [[Sxx, Sxy], [Sxy, Syy]], V(m) = H^-1 (Sxr, Syr) by Cramer's rule
+//   (V0(m) + H^-1 (Sxr, Syr) in the increment form), unless
+//   Sxx + Syy <= eps_abs or det <= eps_rel (Sxx + Syy)^2, where V0(m) is
+//   kept.  The window sums weigh tap (a, b) by wg[|a|] wg[|b|] with the
+//   Gaussian window, by 1 with the box.
 #pragma once
 #include "ofv_common.cuh"
 
@@ -99,7 +102,7 @@ __device__ __forceinline__ void pixel_products(const IterArgs &a, int x, int y, 
     const Sample s2 = sample_level(P2, a.H, a.W, a.pitch, x, y, hx, hy);
     const float Gx = 0.5f * (s1.gx + s2.gx), Gy = 0.5f * (s1.gy + s2.gy);
     const float It = s2.val - s1.val;
-    const float r = Gx * V0.x + Gy * V0.y - It;
+    const float r = a.inc ? -It : Gx * V0.x + Gy * V0.y - It;
     p[0] = Gx * Gx;
     p[1] = Gx * Gy;
     p[2] = Gy * Gy;
@@ -107,14 +110,22 @@ __device__ __forceinline__ void pixel_products(const IterArgs &a, int x, int y, 
     p[4] = Gy * r;
 }
 
-// Guarded Cramer solve of [[Sxx, Sxy], [Sxy, Syy]] V = (Sxr, Syr).
-__device__ __forceinline__ float2 solve2(const float S[5], float2 V0, float eps_rel, float eps_abs)
+// Guarded Cramer solve of [[Sxx, Sxy], [Sxy, Syy]] X = (Sxr, Syr); V = X,
+// or V0 + X in the increment form.
+__device__ __forceinline__ float2 solve2(const float S[5], float2 V0, float eps_rel, float eps_abs, int inc)
 {
     const float a = S[0], b = S[1], c = S[2];
     const float tr = a + c;
     const float det = a * c - b * b;
     if (!(tr > eps_abs) || det <= eps_rel * tr * tr) return V0;
-    return make_float2((c * S[3] - b * S[4]) / det, (a * S[4] - b * S[3]) / det);
+    const float2 X = make_float2((c * S[3] - b * S[4]) / det, (a * S[4] - b * S[3]) / det);
+    return inc ? make_float2(V0.x + X.x, V0.y + X.y) : X;
+}
+
+// Window weight of tap offset t = 0 .. 2 kr along one axis.
+__device__ __forceinline__ float win_weight(const IterArgs &a, int t)
+{
+    return a.gauss ? a.wg[abs(t - a.kr)] : 1.f;
 }
 
 }  // namespace ofv

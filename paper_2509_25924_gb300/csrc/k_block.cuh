@@ -265,7 +265,7 @@ __device__ __forceinline__ Sample bilin_staged(const T *__restrict__ rm, float f
 // within REACH px.  The frame-1 offset -h and frame-2 offset +h share their
 // fractional part: floor(-h) = -floor(h) - 1 and frac(-h) = 1 - frac(h)
 // unless h is an integer.  Farther warps take the general sampler.
-template <typename T, int SP>
+template <typename T, int SP, bool VAR = false>
 __device__ __forceinline__ void products_interior(const T *__restrict__ st1, const T *__restrict__ st2, int sx0,
                                                   int sy0, const IterArgs &a, int x, int y, float2 V0, float p[5])
 {
@@ -293,7 +293,7 @@ __device__ __forceinline__ void products_interior(const T *__restrict__ st1, con
         Gy = 0.5f * (s1.gy + s2.gy);
     }
     const float It = s2.val - s1.val;
-    const float r = Gx * V0.x + Gy * V0.y - It;
+    const float r = (VAR && a.inc) ? -It : Gx * V0.x + Gy * V0.y - It;
     p[0] = Gx * Gx;
     p[1] = Gx * Gy;
     p[2] = Gy * Gy;
@@ -321,7 +321,7 @@ __host__ __device__ constexpr int first_iter_of_band(int b)
 // With bars (TMA staging in three bands), the loop waits for band b just
 // before the first iteration that can touch it, so the first rows of
 // products overlap the copies of the later bands.
-template <typename T, int KR, bool COH, int MODE, int SP>
+template <typename T, int KR, bool COH, int MODE, int SP, bool VAR>
 __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const T *__restrict__ st1,
                                                        const T *__restrict__ st2, int sx0, int sy0, int px0, int py0,
                                                        float *prod, uint64_t *bars, unsigned parity, int *err)
@@ -355,7 +355,7 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
         }
         if (idx + NT < RW * RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
         float p[5];
-        products_interior<T, SP>(st1, st2, sx0, sy0, a, gx, gy, V0c, p);
+        products_interior<T, SP, VAR>(st1, st2, sx0, sy0, a, gx, gy, V0c, p);
         q[0] = p[0];
         q[PLANE] = p[1];
         q[2 * PLANE] = p[2];
@@ -414,9 +414,37 @@ __device__ __forceinline__ void window_sums_inplace(float *line, int stride)
     for (; b < NB; ++b) window_step<KR, TS, true>(line, stride, b * WIN, cur);
 }
 
+// Weighted window sums of one line, in place (Gaussian window):
+// line[o*stride] <- sum_{j=0}^{2KR} w(j - KR) line[(o+j)*stride] for
+// o = 0 .. TS-1, with w(d) = wg[|d|].  The 2KR+1 values under the window sit
+// in a register ring (value n in slot n mod WIN); output o is written after
+// its own value was read and no later output needs it.
+template <int KR, int TS>
+__device__ __forceinline__ void window_wsums_inplace(float *line, int stride, const float *wg)
+{
+    constexpr int WIN = 2 * KR + 1;
+    float ring[WIN];
+#pragma unroll
+    for (int i = 0; i < WIN - 1; ++i) ring[i] = line[i * stride];
+#pragma unroll 1
+    for (int o0 = 0; o0 < TS; o0 += WIN) {
+#pragma unroll
+        for (int k = 0; k < WIN; ++k) {
+            if (o0 + k < TS) {
+                ring[(k + WIN - 1) % WIN] = line[(o0 + k + WIN - 1) * stride];
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < WIN; ++j) acc = fmaf(wg[j < KR ? KR - j : j - KR], ring[(k + j) % WIN], acc);
+                line[(o0 + k) * stride] = acc;
+            }
+        }
+    }
+}
+
 // Phase 4 of the forward iteration: the guarded 2x2 solve of pixel (gx, gy)
 // from its window sums S = (Sxx, Sxy, Syy, Sxr, Syr) and the store of V.
-struct SolveStore {
+template <bool VAR>
+struct SolveStoreT {
     template <bool COH>
     __device__ __forceinline__ void apply(const IterArgs &a, int mode, int gx, int gy, const float (&S)[5]) const
     {
@@ -429,6 +457,11 @@ struct SolveStore {
         } else {
             const float inv = __frcp_rn(det);  // one correctly rounded reciprocal, two products
             V = make_float2((syy * sxr - sxy * syr) * inv, (sxx * syr - sxy * sxr) * inv);
+            if (VAR && a.inc) {  // increment form: V = V0(m) + H^-1 (Sxr, Syr)
+                const float2 V0 = fetch_v0_rt<COH>(a, mode, gx, gy);
+                V.x += V0.x;
+                V.y += V0.y;
+            }
         }
         if (a.u_out) {
             a.u_out[(int64_t)gy * a.W + gx] = V.x;
@@ -439,14 +472,18 @@ struct SolveStore {
     }
 };
 
+using SolveStore = SolveStoreT<false>;
+
 // Phases 0-3 of one tile, then epi.apply() per output pixel (phase 4).
+// VAR: the tile honours the estimator variants of a (increment form,
+// Gaussian window); without it the kernel carries no code for them.
 // TMA staging needs tensor maps tm1, tm2 of the two level images and NBAND
 // mbarriers tma_bars (shared memory): with init_bars the tile initialises
 // them (one tile per CTA), else the caller did and made them visible to the
 // CTA; parity is the phase this tile's copies complete (the number of
 // earlier TMA tiles of the CTA, mod 2).  Returns true when the tile was
 // staged by TMA.
-template <typename T, int KR, bool COH, typename Epi = SolveStore>
+template <typename T, int KR, bool COH, typename Epi = SolveStore, bool VAR = false>
 __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4,
                                            const CUtensorMap *tm1 = nullptr, const CUtensorMap *tm2 = nullptr,
                                            int *err = nullptr, const Epi &epi = Epi(), uint64_t *tma_bars = nullptr,
@@ -523,12 +560,12 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
     if (interior) {
         const T *st2 = stage + STG;
         if (mode == V0_SAME)
-            products_tile_interior<T, KR, COH, V0_SAME, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity,
+            products_tile_interior<T, KR, COH, V0_SAME, SP, VAR>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity,
                                                            err);
         else if (mode == V0_UP)
-            products_tile_interior<T, KR, COH, V0_UP, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity, err);
+            products_tile_interior<T, KR, COH, V0_UP, SP, VAR>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity, err);
         else
-            products_tile_interior<T, KR, COH, V0_ZERO, SP>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity,
+            products_tile_interior<T, KR, COH, V0_ZERO, SP, VAR>(a, stage, st2, sx0, sy0, px0, py0, prod, bars, parity,
                                                            err);
         // every band has landed before the CTA can finish (no copy in flight at exit)
         if (bars && tid == 0)
@@ -549,7 +586,7 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
                 V0n = fetch_v0_rt<COH>(a, mode, px0 + nrx, py0 + nry);
             float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             if (gx > kBlockReach && gx < W - kBlockReach - 2 && gy > kBlockReach && gy < H - kBlockReach - 2) {
-                products_interior<T, SP>(stage, stage + STG, sx0, sy0, a, gx, gy, V0c, p);
+                products_interior<T, SP, VAR>(stage, stage + STG, sx0, sy0, a, gx, gy, V0c, p);
             } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
                 const float2 V0 = V0c;
                 const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
@@ -557,7 +594,7 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
                 const Sample s2 = sample_staged<T, SP>(stage + STG, sx0, sy0, P2, H, W, pitch, gx, gy, hx, hy);
                 const float Gx = 0.5f * (s1.gx + s2.gx), Gy = 0.5f * (s1.gy + s2.gy);
                 const float It = s2.val - s1.val;
-                const float r = Gx * V0.x + Gy * V0.y - It;
+                const float r = (VAR && a.inc) ? -It : Gx * V0.x + Gy * V0.y - It;
                 p[0] = Gx * Gx;
                 p[1] = Gx * Gy;
                 p[2] = Gy * Gy;
@@ -577,16 +614,31 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
     __syncthreads();
 
     // phase 2: horizontal window sums, one (row, channel) per thread
-    for (int t = tid; t < 5 * RW; t += NT) {
-        const int c = t / RW, row = t - c * RW;
-        window_sums_inplace<KR, TS>(prod + c * PLANE + row * RWP, 1);
+    // (weighted sums with the Gaussian window)
+    if (VAR && a.gauss) {
+        for (int t = tid; t < 5 * RW; t += NT) {
+            const int c = t / RW, row = t - c * RW;
+            window_wsums_inplace<KR, TS>(prod + c * PLANE + row * RWP, 1, a.wg);
+        }
+    } else {
+        for (int t = tid; t < 5 * RW; t += NT) {
+            const int c = t / RW, row = t - c * RW;
+            window_sums_inplace<KR, TS>(prod + c * PLANE + row * RWP, 1);
+        }
     }
     __syncthreads();
 
     // phase 3: vertical window sums, one (column, channel) per thread
-    for (int t = tid; t < 5 * TS; t += NT) {
-        const int c = t / TS, col = t - c * TS;
-        window_sums_inplace<KR, TS>(prod + c * PLANE + col, RWP);
+    if (VAR && a.gauss) {
+        for (int t = tid; t < 5 * TS; t += NT) {
+            const int c = t / TS, col = t - c * TS;
+            window_wsums_inplace<KR, TS>(prod + c * PLANE + col, RWP, a.wg);
+        }
+    } else {
+        for (int t = tid; t < 5 * TS; t += NT) {
+            const int c = t / TS, col = t - c * TS;
+            window_sums_inplace<KR, TS>(prod + c * PLANE + col, RWP);
+        }
     }
     __syncthreads();
 
@@ -602,18 +654,19 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
     return bars != nullptr;
 }
 
-// One tile per CTA; blockIdx.z selects the pair.
-template <typename T, int KR>
+// One tile per CTA; blockIdx.z selects the pair.  VAR: estimator variants.
+template <typename T, int KR, bool VAR>
 __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __grid_constant__ BlockParams prm)
 {
     extern __shared__ __align__(128) float4 smem_f4[];
     __shared__ __align__(8) uint64_t s_bar[StageShape<T, KR>::NBAND];
     const int z = blockIdx.z;
     if (prm.use_tma) {
-        block_tile<T, KR, false>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4, &prm.tm[z][0], &prm.tm[z][1],
-                                 prm.err, SolveStore(), s_bar, 0u, true);
+        block_tile<T, KR, false, SolveStoreT<VAR>, VAR>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4,
+                                                        &prm.tm[z][0], &prm.tm[z][1], prm.err, SolveStoreT<VAR>(),
+                                                        s_bar, 0u, true);
     } else {
-        block_tile<T, KR, false>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4);
+        block_tile<T, KR, false, SolveStoreT<VAR>, VAR>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4);
     }
 }
 
@@ -642,6 +695,8 @@ struct QueueParams {
     int ngroups, total_units, npairs;
     int L, IT, kr;
     float eps_rel, eps_abs;
+    int inc, gauss;          // estimator variants (as IterArgs)
+    float wg[kBlockMaxKR + 1];
     int *head;               // next unclaimed unit
     int *done;               // [stages * npairs] finished tiles
     int *error;              // 0, or 1 + the unit whose wait expired
@@ -661,7 +716,7 @@ __device__ __forceinline__ int ld_acquire(const int *p)
 template <int TS>
 __device__ __forceinline__ int tiles_of(int H, int W) { return ((W + TS - 1) / TS) * ((H + TS - 1) / TS); }
 
-template <typename T, int KR>
+template <typename T, int KR, bool VAR>
 __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __grid_constant__ QueueParams q)
 {
     constexpr int TS = BlockShape<KR>::TS;
@@ -719,6 +774,12 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __gr
         a.kr = q.kr;
         a.eps_rel = q.eps_rel;
         a.eps_abs = q.eps_abs;
+        if (VAR) {
+            a.inc = q.inc;
+            a.gauss = q.gauss;
+#pragma unroll
+            for (int d = 0; d <= kBlockMaxKR; ++d) a.wg[d] = q.wg[d];
+        }
         int mode = V0_ZERO;
         if (s > 0 && t == 0) {
             mode = V0_UP;
@@ -737,13 +798,27 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __gr
         }
         const int ntx = (a.W + TS - 1) / TS;
         const CUtensorMap *tm = q.tmaps ? q.tmaps + ((size_t)p * 16 + l) * 2 : nullptr;
-        if (block_tile<T, KR, true>(a, mode, tile % ntx, tile / ntx, smem_f4, tm, tm ? tm + 1 : nullptr, q.tma_err,
-                                    SolveStore(), q.tmaps ? s_bar : nullptr, tma_uses & 1u))
+        if (block_tile<T, KR, true, SolveStoreT<VAR>, VAR>(a, mode, tile % ntx, tile / ntx, smem_f4, tm,
+                                                           tm ? tm + 1 : nullptr, q.tma_err, SolveStoreT<VAR>(),
+                                                           q.tmaps ? s_bar : nullptr, tma_uses & 1u))
             ++tma_uses;
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(q.done + s * q.npairs + p, 1);
     }
 }
+
+// Host launchers, explicitly instantiated per level storage type T and
+// variant flag VAR in k_block_{f32,f16,bf16}.cu (VAR = false, plus the
+// reverse-mode stage kernel) and k_block_var_{f32,f16,bf16}.cu (VAR = true).
+template <typename T, bool VAR>
+cudaError_t launch_block_t(const BlockParams &p, int kr, int npairs, cudaStream_t s);
+template <typename T, bool VAR>
+cudaError_t launch_queue_t(const QueueParams &q, int kr, int ctas, cudaStream_t s);
+template <typename T, bool VAR>
+int queue_occupancy_t(int kr);
+
+// Output tile edge of the block kernel for radius kr.
+inline int block_tile_size(int kr) { return kr <= 5 ? BlockShape<5>::TS : BlockShape<10>::TS; }
 
 }  // namespace ofv

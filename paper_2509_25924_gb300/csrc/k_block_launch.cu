@@ -5,9 +5,12 @@
 
 namespace ofv {
 
-cudaError_t launch_block_f32(const BlockParams &p, int kr, int npairs, cudaStream_t s);
-cudaError_t launch_block_f16(const BlockParams &p, int kr, int npairs, cudaStream_t s);
-cudaError_t launch_block_bf16(const BlockParams &p, int kr, int npairs, cudaStream_t s);
+extern template cudaError_t launch_block_t<float, false>(const BlockParams &, int, int, cudaStream_t);
+extern template cudaError_t launch_block_t<float, true>(const BlockParams &, int, int, cudaStream_t);
+extern template cudaError_t launch_block_t<__half, false>(const BlockParams &, int, int, cudaStream_t);
+extern template cudaError_t launch_block_t<__half, true>(const BlockParams &, int, int, cudaStream_t);
+extern template cudaError_t launch_block_t<__nv_bfloat16, false>(const BlockParams &, int, int, cudaStream_t);
+extern template cudaError_t launch_block_t<__nv_bfloat16, true>(const BlockParams &, int, int, cudaStream_t);
 
 bool block_supports(int kr) { return kr >= 1 && kr <= kBlockMaxKR; }
 
@@ -32,10 +35,15 @@ cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode
             p.tm[k][1] = *tm[2 * k + 1];
         }
     }
+    // the kernels with variant code only when a variant is on (uniform per launch)
+    const bool var = a[0].inc || a[0].gauss;
     switch (store) {
-    case ST_F16: return launch_block_f16(p, a[0].kr, npairs, s);
-    case ST_BF16: return launch_block_bf16(p, a[0].kr, npairs, s);
-    default: return launch_block_f32(p, a[0].kr, npairs, s);
+    case ST_F16: return var ? launch_block_t<__half, true>(p, a[0].kr, npairs, s)
+                            : launch_block_t<__half, false>(p, a[0].kr, npairs, s);
+    case ST_BF16: return var ? launch_block_t<__nv_bfloat16, true>(p, a[0].kr, npairs, s)
+                             : launch_block_t<__nv_bfloat16, false>(p, a[0].kr, npairs, s);
+    default: return var ? launch_block_t<float, true>(p, a[0].kr, npairs, s)
+                        : launch_block_t<float, false>(p, a[0].kr, npairs, s);
     }
 }
 

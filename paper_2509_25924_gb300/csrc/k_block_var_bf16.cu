@@ -1,0 +1,9 @@
+// Block-tiled iteration kernels for __nv_bfloat16 level storage, window radii 1..10,
+// with the estimator variants (increment form, Gaussian window).
+#include "k_block_inst.cuh"
+
+namespace ofv {
+
+OFV_INSTANTIATE_BLOCK_LAUNCHERS(__nv_bfloat16, true)
+
+}  // namespace ofv

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_iter_fused(IterArgs a)
     }
     __syncthreads();
 
-    // phase 2: row sums of 2KR+1 taps
+    // phase 2: row sums of 2KR+1 taps (weighted with the Gaussian window)
     const int taps = 2 * kr + 1;
     for (int idx = threadIdx.x; idx < RH * kTX; idx += kThreads) {
         const int ry = idx / kTX, ox = idx - ry * kTX;
@@ -58,7 +58,10 @@ __global__ void __launch_bounds__(kThreads) k_iter_fused(IterArgs a)
         for (int c = 0; c < 5; ++c) {
             const float *row = prod + c * RN + ry * RW + ox;
             float s = 0.f;
-            for (int t = 0; t < taps; ++t) s += row[t];
+            if (a.gauss)
+                for (int t = 0; t < taps; ++t) s = fmaf(win_weight(a, t), row[t], s);
+            else
+                for (int t = 0; t < taps; ++t) s += row[t];
             hs[c * RH * kTX + idx] = s;
         }
     }
@@ -74,10 +77,13 @@ __global__ void __launch_bounds__(kThreads) k_iter_fused(IterArgs a)
         for (int c = 0; c < 5; ++c) {
             const float *col = hs + c * RH * kTX + oy * kTX + ox;
             float s = 0.f;
-            for (int t = 0; t < taps; ++t) s += col[t * kTX];
+            if (a.gauss)
+                for (int t = 0; t < taps; ++t) s = fmaf(win_weight(a, t), col[t * kTX], s);
+            else
+                for (int t = 0; t < taps; ++t) s += col[t * kTX];
             S[c] = s;
         }
-        const float2 V = solve2(S, v0c[idx], a.eps_rel, a.eps_abs);
+        const float2 V = solve2(S, v0c[idx], a.eps_rel, a.eps_abs, a.inc);
         if (PLANAR) {
             a.u_out[(int64_t)gy * a.W + gx] = V.x;
             a.v_out[(int64_t)gy * a.W + gx] = V.y;

@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(256) k_plain_products(IterArgs a, PlainBufs b)
     for (int c = 0; c < 5; ++c) b.prod[c * b.plane + o] = p[c];
 }
 
-// Row sums over columns x-KR .. x+KR that lie inside the image.
+// Row sums over columns x-KR .. x+KR that lie inside the image (weighted
+// with the Gaussian window).
 __global__ void __launch_bounds__(256) k_plain_rowsum(IterArgs a, PlainBufs b)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,7 +43,10 @@ __global__ void __launch_bounds__(256) k_plain_rowsum(IterArgs a, PlainBufs b)
     for (int c = 0; c < 5; ++c) {
         const float *row = b.prod + c * b.plane + o;
         float s = 0.f;
-        for (int j = j0; j <= j1; ++j) s += row[j];
+        if (a.gauss)
+            for (int j = j0; j <= j1; ++j) s = fmaf(win_weight(a, j - x + a.kr), row[j], s);
+        else
+            for (int j = j0; j <= j1; ++j) s += row[j];
         b.hsum[c * b.plane + o + x] = s;
     }
 }
@@ -60,13 +64,16 @@ __global__ void __launch_bounds__(256) k_plain_colsum_solve(IterArgs a, PlainBuf
     for (int c = 0; c < 5; ++c) {
         const float *col = b.hsum + c * b.plane + x;
         float s = 0.f;
-        for (int i = i0; i <= i1; ++i) s += col[(int64_t)i * a.pitch];
+        if (a.gauss)
+            for (int i = i0; i <= i1; ++i) s = fmaf(win_weight(a, i - y + a.kr), col[(int64_t)i * a.pitch], s);
+        else
+            for (int i = i0; i <= i1; ++i) s += col[(int64_t)i * a.pitch];
         S[c] = s;
     }
     float2 V0 = make_float2(0.f, 0.f);
     if (mode == V0_SAME) V0 = a.V0[(int64_t)y * a.vpitch + x];
     else if (mode == V0_UP) V0 = b.vtmp[(int64_t)y * a.vpitch + x];
-    const float2 V = solve2(S, V0, a.eps_rel, a.eps_abs);
+    const float2 V = solve2(S, V0, a.eps_rel, a.eps_abs, a.inc);
     if (PLANAR) {
         a.u_out[(int64_t)y * a.W + x] = V.x;
         a.v_out[(int64_t)y * a.W + x] = V.y;

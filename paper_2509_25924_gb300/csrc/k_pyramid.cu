@@ -281,4 +281,38 @@ cudaError_t launch_read_level(const void *src, int H, int W, int pitch, int stor
     return cudaGetLastError();
 }
 
+// Warm start (a variant for time-resolved sequences): the coarsest level's
+// starting field taken from an earlier level-0 field at the pixels that
+// level keeps, V_L(i, j) = V(2^L i, 2^L j) / 2^L.  Division by a power of two
+// is exact.  One launch for up to kMaxPairsPerLaunch fields (blockIdx.z).
+struct SeedPack {
+    SeedArgs a[kMaxPairsPerLaunch];
+};
+
+__global__ void __launch_bounds__(256) k_seed_field(const __grid_constant__ SeedPack p)
+{
+    const SeedArgs &a = p.a[blockIdx.z];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.W) return;
+    const float sc = 1.f / (float)(1 << a.level);
+    for (int i = blockIdx.y; i < a.H; i += gridDim.y) {
+        const int64_t src = ((int64_t)i * a.W0 << a.level) + ((int64_t)j << a.level);
+        a.out[(int64_t)i * a.vpitch + j] = make_float2(__ldg(a.u + src) * sc, __ldg(a.v + src) * sc);
+    }
+}
+
+cudaError_t launch_seed_fields(const SeedArgs *a, int n, cudaStream_t s)
+{
+    if (n < 1 || n > kMaxPairsPerLaunch) return cudaErrorInvalidValue;
+    SeedPack p;
+    int H = 0, W = 0;
+    for (int k = 0; k < n; ++k) {
+        p.a[k] = a[k];
+        H = a[k].H > H ? a[k].H : H;
+        W = a[k].W > W ? a[k].W : W;
+    }
+    k_seed_field<<<dim3((W + 255) / 256, H < 65535 ? H : 65535, n), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 }  // namespace ofv

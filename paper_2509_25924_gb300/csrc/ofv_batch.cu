@@ -15,13 +15,16 @@
 #include "ofv_handle.h"
 
 namespace ofv {
-cudaError_t launch_queue_f32(const QueueParams &q, int kr, int ctas, cudaStream_t s);
-cudaError_t launch_queue_f16(const QueueParams &q, int kr, int ctas, cudaStream_t s);
-cudaError_t launch_queue_bf16(const QueueParams &q, int kr, int ctas, cudaStream_t s);
-int queue_occupancy_f32(int kr);
-int queue_occupancy_f16(int kr);
-int queue_occupancy_bf16(int kr);
-int block_tile_size(int kr);
+#define OFV_EXTERN_QUEUE(T, VAR)                                                                   \
+    extern template cudaError_t launch_queue_t<T, VAR>(const QueueParams &, int, int, cudaStream_t); \
+    extern template int queue_occupancy_t<T, VAR>(int);
+OFV_EXTERN_QUEUE(float, false)
+OFV_EXTERN_QUEUE(float, true)
+OFV_EXTERN_QUEUE(__half, false)
+OFV_EXTERN_QUEUE(__half, true)
+OFV_EXTERN_QUEUE(__nv_bfloat16, false)
+OFV_EXTERN_QUEUE(__nv_bfloat16, true)
+#undef OFV_EXTERN_QUEUE
 }  // namespace ofv
 
 using namespace ofv;
@@ -31,21 +34,26 @@ namespace {
 constexpr long long kWaitTimeoutNs = 5000000000LL;  // 5 s
 constexpr int kWaitSpinLimit = 200000000;
 
+// The kernels with variant code run only when a variant is on.
 cudaError_t launch_queue(int store, const QueueParams &q, int kr, int ctas, cudaStream_t s)
 {
+    const bool var = q.inc || q.gauss;
     switch (store) {
-    case OFV_STORE_F16: return launch_queue_f16(q, kr, ctas, s);
-    case OFV_STORE_BF16: return launch_queue_bf16(q, kr, ctas, s);
-    default: return launch_queue_f32(q, kr, ctas, s);
+    case OFV_STORE_F16: return var ? launch_queue_t<__half, true>(q, kr, ctas, s)
+                                   : launch_queue_t<__half, false>(q, kr, ctas, s);
+    case OFV_STORE_BF16: return var ? launch_queue_t<__nv_bfloat16, true>(q, kr, ctas, s)
+                                    : launch_queue_t<__nv_bfloat16, false>(q, kr, ctas, s);
+    default: return var ? launch_queue_t<float, true>(q, kr, ctas, s) : launch_queue_t<float, false>(q, kr, ctas, s);
     }
 }
 
-int queue_occupancy(int store, int kr)
+int queue_occupancy(int store, int kr, bool var)
 {
     switch (store) {
-    case OFV_STORE_F16: return queue_occupancy_f16(kr);
-    case OFV_STORE_BF16: return queue_occupancy_bf16(kr);
-    default: return queue_occupancy_f32(kr);
+    case OFV_STORE_F16: return var ? queue_occupancy_t<__half, true>(kr) : queue_occupancy_t<__half, false>(kr);
+    case OFV_STORE_BF16:
+        return var ? queue_occupancy_t<__nv_bfloat16, true>(kr) : queue_occupancy_t<__nv_bfloat16, false>(kr);
+    default: return var ? queue_occupancy_t<float, true>(kr) : queue_occupancy_t<float, false>(kr);
     }
 }
 
@@ -284,14 +292,14 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
 
     int dev = h->device, sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int occ = std::max(1, queue_occupancy(p.storage, KR));
+    const int occ = std::max(1, queue_occupancy(p.storage, KR, p.window == OFV_WINDOW_GAUSS || p.increment_form));
 
     // batch signature for the autotuner
     std::vector<std::pair<int, int>> sizes;
     for (int i = 0; i < n; ++i) sizes.push_back({Hs[i][0], Ws[i][0]});
     std::sort(sizes.begin(), sizes.end());
     std::string key = "kr" + std::to_string(KR) + "l" + std::to_string(L) + "it" + std::to_string(IT) + "s" +
-                      std::to_string(p.storage);
+                      std::to_string(p.storage) + "v" + std::to_string(p.window) + std::to_string(p.increment_form);
     for (auto &sz : sizes) key += ":" + std::to_string(sz.first) + "x" + std::to_string(sz.second);
 
     std::vector<BatchTune> cands;
@@ -316,6 +324,13 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     q.kr = KR;
     q.eps_rel = p.det_rel_eps;
     q.eps_abs = p.det_abs_eps;
+    {
+        IterArgs v = {};
+        set_iter_variant(v, KR, p.window == OFV_WINDOW_GAUSS, p.window_sigma, p.increment_form);
+        q.inc = v.inc;
+        q.gauss = v.gauss;
+        for (int d = 0; d <= kBlockMaxKR; ++d) q.wg[d] = v.wg[d];
+    }
     q.done = reinterpret_cast<int *>(base + done_off);
     q.head = q.done + maxgroups;
     q.error = q.head + 1;

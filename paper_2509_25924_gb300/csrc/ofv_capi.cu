@@ -88,6 +88,15 @@ ofv_status check_params(const ofv_params *p)
         return fail(OFV_ERR_INVALID_ARG, "guard / normalization epsilons must be finite (norm_eps > 0)");
     if (p->max_batch < 0 || p->max_batch > kMaxBatch)
         return fail(OFV_ERR_INVALID_ARG, "max_batch=%d outside 0..%d", p->max_batch, kMaxBatch);
+    if (p->window != OFV_WINDOW_BOX && p->window != OFV_WINDOW_GAUSS)
+        return fail(OFV_ERR_INVALID_ARG, "window=%d is not an ofv_window_t", p->window);
+    if (p->window == OFV_WINDOW_GAUSS && (!(p->window_sigma > 0.f) || !std::isfinite(p->window_sigma)))
+        return fail(OFV_ERR_INVALID_ARG, "window_sigma=%g must be finite and > 0 for the Gaussian window",
+                    (double)p->window_sigma);
+    if (p->increment_form != 0 && p->increment_form != 1)
+        return fail(OFV_ERR_INVALID_ARG, "increment_form=%d is not 0 or 1", p->increment_form);
+    if (p->warm_start < 0 || p->warm_start > kMaxBatch)
+        return fail(OFV_ERR_INVALID_ARG, "warm_start=%d outside 0..%d", p->warm_start, kMaxBatch);
     return OFV_OK;
 }
 
@@ -222,19 +231,37 @@ ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *s
 }
 
 // Steps 3-6 for np pairs: pair k uses pyramid slots s1[k], s2[k], field
-// buffers vbuf[2k], vbuf[2k+1], and writes u[k], v[k].
+// buffers vbuf[2k], vbuf[2k+1], and writes u[k], v[k].  With iu, iv (warm
+// start) pair k starts its coarsest level from the level-0 field iu[k],
+// iv[k] (H x W dense) decimated to that level, else from zero.
 ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float *const *u, float *const *v,
-                      cudaStream_t s, int vset = 0)
+                      cudaStream_t s, int vset = 0, const float *const *iu = nullptr, const float *const *iv = nullptr)
 {
     const ofv_params &p = h->p;
     const int sb = store_bytes(p.storage);
     float2 *const *vbuf = h->vbuf + 2 * h->B * vset;
     int cur = 0;  // vbuf[2k + cur] holds the latest field of pair k
     bool have = false;
+    if (iu && iv) {
+        SeedArgs sa[kMaxBatch];
+        for (int k = 0; k < np; ++k) {
+            sa[k].u = iu[k];
+            sa[k].v = iv[k];
+            sa[k].W0 = h->W;
+            sa[k].level = h->L - 1;
+            sa[k].out = vbuf[2 * k];
+            sa[k].H = h->Hs[h->L - 1];
+            sa[k].W = h->Ws[h->L - 1];
+            sa[k].vpitch = h->vpitch;
+        }
+        ofv_status st = last_launch(launch_seed_fields(sa, np, s), "warm-start field launch");
+        if (st != OFV_OK) return st;
+        have = true;  // vbuf[2k + 0] holds the starting field
+    }
     for (int l = h->L - 1; l >= 0; --l) {
         for (int t = 0; t < p.iterations; ++t) {
             int mode;
-            if (t == 0 && l == h->L - 1) mode = V0_ZERO;
+            if (t == 0 && l == h->L - 1) mode = have ? V0_SAME : V0_ZERO;
             else if (t == 0) mode = V0_UP;
             else mode = V0_SAME;
             const bool last = (l == 0 && t == p.iterations - 1);
@@ -253,6 +280,7 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
                 x.kr = p.kernel_radius;
                 x.eps_rel = p.det_rel_eps;
                 x.eps_abs = p.det_abs_eps;
+                set_iter_variant(x, p.kernel_radius, p.window == OFV_WINDOW_GAUSS, p.window_sigma, p.increment_form);
                 if (mode == V0_UP) {
                     x.Vc = vbuf[2 * k + cur];
                     x.Hc = h->Hs[l + 1];
@@ -327,9 +355,12 @@ struct GroupRunner {
     }
 
     // fr[k] = frame f0 + k (k = 0 .. np), device pointers; before_ingest
-    // (optional) is an event the group's stream waits for first
+    // (optional) is an event the group's stream waits for first.  iu, iv
+    // (warm start): pair k starts from the level-0 field iu[k], iv[k], which
+    // group g-1 wrote; the iterations then wait for group g-1.
     ofv_status group(int g, int f0, int np, const void *const *fr, float *const *uu, float *const *vv,
-                     cudaEvent_t before_ingest = nullptr)
+                     cudaEvent_t before_ingest = nullptr, const float *const *iu = nullptr,
+                     const float *const *iv = nullptr)
     {
         const int NS = h->nslots;
         cudaStream_t cs = stream_of(g);
@@ -352,12 +383,16 @@ struct GroupRunner {
             if (e == cudaSuccess && g >= 1) e = cudaStreamWaitEvent(cs, h->gev[ev(g - 1)][0], 0);
             if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
         }
+        if (K > 1 && iu && g >= 1) {
+            e = cudaStreamWaitEvent(cs, h->gev[ev(g - 1)][1], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "ordering a warm-started group");
+        }
         int s1[kMaxBatch], s2[kMaxBatch];
         for (int k = 0; k < np; ++k) {
             s1[k] = (f0 + k) % NS;
             s2[k] = (f0 + k + 1) % NS;
         }
-        st = run_levels(h, np, s1, s2, uu, vv, cs, g % K);
+        st = run_levels(h, np, s1, s2, uu, vv, cs, g % K, iu, iv);
         if (st != OFV_OK) return st;
         if (K > 1) {
             e = cudaEventRecord(h->gev[ev(g)][1], cs);
@@ -379,6 +414,18 @@ struct GroupRunner {
         return e == cudaSuccess ? OFV_OK : cuda_fail(e, "joining the group streams");
     }
 };
+
+// Pairs per group of a sequence: the handle's pairs-per-launch, or d with
+// a warm start from the pair d steps back (which is then pair k of the
+// previous group).
+ofv_status group_size(const ofv_handle *h, int *gb)
+{
+    const int d = h->p.warm_start;
+    if (d > h->B)
+        return fail(OFV_ERR_INVALID_ARG, "warm_start=%d exceeds the handle's %d pairs per launch", d, h->B);
+    *gb = d > 0 ? d : h->B;
+    return OFV_OK;
+}
 
 ofv_status pending_error(const ofv_handle *h, const char *where)
 {
@@ -454,6 +501,10 @@ void ofv_default_params(ofv_params *p)
     p->det_abs_eps = 1e-20f;
     p->norm_eps = 1e-2f;
     p->max_batch = 0;
+    p->window = OFV_WINDOW_BOX;
+    p->window_sigma = 0.f;
+    p->increment_form = 0;
+    p->warm_start = 0;
 }
 
 ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
@@ -712,18 +763,28 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
     cudaStream_t cs = (cudaStream_t)s;
     const char *fb = static_cast<const char *>(frames);
     const int npairs = n_frames - 1;
+    int GB;  // pairs per group
+    if ((st = group_size(h, &GB)) != OFV_OK) return st;
+    const int d = h->p.warm_start;
     GroupRunner gr(h, cs);
     if ((st = gr.begin()) != OFV_OK) return st;
-    for (int f0 = 0, g = 0; f0 < npairs; f0 += h->B, ++g) {
-        const int np = npairs - f0 < h->B ? npairs - f0 : h->B;
+    for (int f0 = 0, g = 0; f0 < npairs; f0 += GB, ++g) {
+        const int np = npairs - f0 < GB ? npairs - f0 : GB;
         const void *fr[kMaxSlots];
         for (int f = f0; f <= f0 + np; ++f) fr[f - f0] = fb + (size_t)f * frame_stride_bytes;
         float *uu[kMaxBatch], *vv[kMaxBatch];
+        const float *iu[kMaxBatch], *iv[kMaxBatch];
         for (int k = 0; k < np; ++k) {
             uu[k] = u + (size_t)(f0 + k) * field_stride;
             vv[k] = v + (size_t)(f0 + k) * field_stride;
+            if (d > 0 && f0 >= d) {  // pair f0+k-d is pair k of group g-1
+                iu[k] = u + (size_t)(f0 + k - d) * field_stride;
+                iv[k] = v + (size_t)(f0 + k - d) * field_stride;
+            }
         }
-        if ((st = gr.group(g, f0, np, fr, uu, vv)) != OFV_OK) return st;
+        const bool warm = d > 0 && f0 >= d;
+        if ((st = gr.group(g, f0, np, fr, uu, vv, nullptr, warm ? iu : nullptr, warm ? iv : nullptr)) != OFV_OK)
+            return st;
     }
     return gr.end();
 }
@@ -745,7 +806,9 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
     ofv_status st = pending_error(h, "error pending before ofv_compute_sequence_host");
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
-    const int B = h->B;
+    int B;  // pairs per group
+    if ((st = group_size(h, &B)) != OFV_OK) return st;
+    const int d = h->p.warm_start;
     // device ring: per slot B+1 frames and B fields (u and v)
     const size_t in_b = align_up(fb * (size_t)(B + 1), 256);
     const size_t out_b = align_up(N * sizeof(float) * (size_t)B, 256);
@@ -817,11 +880,19 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
         fr[0] = nullptr;  // frame f0 > 0 is already in its pyramid slot
         for (int f = fa; f <= fz; ++f) fr[f - f0] = slot + (size_t)(f - fa) * fb;
         float *uu[kMaxBatch], *vv[kMaxBatch];
+        const float *iu[kMaxBatch], *iv[kMaxBatch];
+        const bool warm = d > 0 && f0 >= d;  // then groups hold d pairs: pair f0+k-d is pair k of group c-1
+        char *pslot = static_cast<char *>(h->hs_stage) + (size_t)((c + kHostRing - 1) % kHostRing) * slot_b;
         for (int k = 0; k < np; ++k) {
             uu[k] = du + (size_t)k * N;
             vv[k] = dv + (size_t)k * N;
+            if (warm) {
+                iu[k] = reinterpret_cast<const float *>(pslot + in_b) + (size_t)k * N;
+                iv[k] = reinterpret_cast<const float *>(pslot + in_b + out_b) + (size_t)k * N;
+            }
         }
-        if ((st = gr.group(c, f0, np, fr, uu, vv)) != OFV_OK) return st;
+        if ((st = gr.group(c, f0, np, fr, uu, vv, nullptr, warm ? iu : nullptr, warm ? iv : nullptr)) != OFV_OK)
+            return st;
         e = cudaEventRecord(h->hs_ev[r][1], gsc);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(down, h->hs_ev[r][1], 0);
         if (e == cudaSuccess) {

@@ -3,6 +3,7 @@
 
 #include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -22,6 +23,7 @@ enum V0Mode : int {
 // Pairs of one time-resolved sequence processed by one iteration launch, and
 // frames ingested or reduced by one launch.
 constexpr int kMaxPairsPerLaunch = 8;
+constexpr int kMaxWindowRadius = 16;  // largest KR
 constexpr int kMaxFramesPerLaunch = kMaxPairsPerLaunch + 1;
 
 // Level images are stored with a row pitch (elements) that is a multiple of
@@ -55,7 +57,20 @@ struct IterArgs {
     int vpitch;
     int kr;
     float eps_rel, eps_abs;
+    int inc;              // 1: increment form, r = -It and V = V0(m) + H^-1 (Sxr, Syr)
+    int gauss;            // 1: window tap (a, b) weighted wg[|a|] wg[|b|]; 0: uniform box
+    float wg[kMaxWindowRadius + 1];  // Gaussian window weights exp(-d^2 / (2 sigma^2)), d = 0..KR
 };
+
+// Estimator variants of an iteration (host side): the increment form and
+// the Gaussian window weights of radius kr and width sigma.
+inline void set_iter_variant(IterArgs &a, int kr, int window_gauss, float sigma, int increment_form)
+{
+    a.inc = increment_form ? 1 : 0;
+    a.gauss = window_gauss ? 1 : 0;
+    for (int d = 0; d <= kMaxWindowRadius; ++d)
+        a.wg[d] = (a.gauss && d <= kr) ? (float)std::exp(-(double)d * d / (2.0 * (double)sigma * sigma)) : 1.f;
+}
 
 // Host-side launchers (defined in the kernel translation units).
 // Tile kernel: one CTA per 32x32 output tile, products staged in shared memory.
@@ -101,6 +116,16 @@ struct ReduceArgs {
 };
 // Reduce one level of nframes (1 or 2) frames in one launch.
 cudaError_t launch_reduce_frames(const ReduceArgs *f, int nframes, int store, cudaStream_t s);
+
+// Warm start: the starting field of the coarsest level from a level-0
+// field, out(i, j) = (u, v)(2^level i, 2^level j) / 2^level (pitch vpitch).
+struct SeedArgs {
+    const float *u, *v;  // level-0 field, dense rows of W0
+    int W0, level;
+    float2 *out;
+    int H, W, vpitch;    // the level's size
+};
+cudaError_t launch_seed_fields(const SeedArgs *a, int n, cudaStream_t s);
 
 cudaError_t launch_read_level(const void *src, int H, int W, int pitch, int store, float *dst,
                               cudaStream_t s);

@@ -82,7 +82,9 @@ extern "C" ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *p, con
         (p->storage != OFV_STORE_F32 && p->storage != OFV_STORE_F16 && p->storage != OFV_STORE_BF16) ||
         (p->prefilter != 0 && p->prefilter != 1) || !(p->det_rel_eps >= 0.f) || !std::isfinite(p->det_rel_eps) ||
         !(p->det_abs_eps >= 0.f) || !std::isfinite(p->det_abs_eps) || !(p->norm_eps > 0.f) ||
-        !std::isfinite(p->norm_eps))
+        !std::isfinite(p->norm_eps) || (p->window != OFV_WINDOW_BOX && p->window != OFV_WINDOW_GAUSS) ||
+        (p->window == OFV_WINDOW_GAUSS && (!(p->window_sigma > 0.f) || !std::isfinite(p->window_sigma))) ||
+        (p->increment_form != 0 && p->increment_form != 1))
         return na_fail(OFV_ERR_INVALID_ARG, "ofv_compute_noalloc: parameter out of range (see ofv_params)");
     if (p->path != OFV_PATH_FUSED)
         return na_fail(OFV_ERR_UNSUPPORTED, "ofv_compute_noalloc: only the fused path is available without allocation");
@@ -191,6 +193,7 @@ extern "C" ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *p, con
             a.kr = p->kernel_radius;
             a.eps_rel = p->det_rel_eps;
             a.eps_abs = p->det_abs_eps;
+            set_iter_variant(a, p->kernel_radius, p->window == OFV_WINDOW_GAUSS, p->window_sigma, p->increment_form);
             int mode;
             if (t == 0 && l == L - 1) {
                 mode = V0_ZERO;

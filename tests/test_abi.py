@@ -50,18 +50,44 @@ def test_defaults_follow_the_documented_values():
     assert (p.input, p.bit_depth, p.storage, p.path, p.prefilter) == (ofv.OFV_IN_U16, 12, ofv.OFV_STORE_F32,
                                                                       ofv.OFV_PATH_FUSED, 0)
     assert abs(p.det_rel_eps - 1e-6) < 1e-12 and abs(p.norm_eps - 1e-2) < 1e-9
+    assert (p.window, p.window_sigma, p.increment_form, p.warm_start) == (ofv.OFV_WINDOW_BOX, 0.0, 0, 0)
+
+
+def test_params_struct_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of ofv_params has the C struct's size and field
+    offsets (compiled against include/ofv.h with the host compiler)."""
+    names = [f[0] for f in ofv.Params._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'    printf("%zu\\n", offsetof(ofv_params, {n}));\n' for n in names)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "ofv.h"\nint main(void) {\n'
+                   '    printf("%zu\\n", sizeof(ofv_params));\n' + body + '    return 0;\n}\n')
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
+    out = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert out[0] == ctypes.sizeof(ofv.Params)
+    assert out[1:] == [getattr(ofv.Params, n).offset for n in names]
 
 
 @pytest.mark.parametrize("field,value", [
     ("levels_psl", -1), ("levels_psl", 16), ("kernel_radius", 0), ("kernel_radius", 17),
     ("iterations", 0), ("iterations", 65), ("norm_radius", -1), ("input", 7), ("storage", 3),
     ("path", 3), ("prefilter", 2), ("bit_depth", 0), ("bit_depth", 17), ("det_rel_eps", float("nan")),
-    ("norm_eps", 0.0), ("max_batch", -1), ("max_batch", 9),
+    ("norm_eps", 0.0), ("max_batch", -1), ("max_batch", 9), ("window", 2), ("window", -1),
+    ("increment_form", 2), ("warm_start", -1), ("warm_start", 9),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(field, value):
     p = ofv.ofv_default_params(**{field: value})
     with pytest.raises(ofv.OfvError) as ei:
         ofv.ofv_create(1024, 1024, p)
+    assert ei.value.status == ofv.OFV_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("sigma", [0.0, -1.0, float("nan"), float("inf")])
+def test_gaussian_window_needs_a_finite_positive_sigma(sigma):
+    p = ofv.ofv_default_params(window=ofv.OFV_WINDOW_GAUSS, window_sigma=sigma)
+    with pytest.raises(ofv.OfvError) as ei:
+        ofv.ofv_create(256, 256, p)
     assert ei.value.status == ofv.OFV_ERR_INVALID_ARG
 
 

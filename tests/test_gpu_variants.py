@@ -1,0 +1,235 @@
+"""GPU parity of the estimator variants against the FP64 oracle, through the
+C ABI: the Gaussian-weighted window, the increment form of the Gauss-Newton
+step and the warm start of a time-resolved sequence from an earlier field.
+
+Tolerances as for the default estimator: FP32 max |dV| <= 1e-3 px over
+pixels whose oracle det/(Sxx+Syy)^2 >= 1e-3.  For a warm-started sequence
+the GPU chain starts from its own earlier fields and the oracle chain from
+its own, so the comparison also checks that the differences do not grow
+along the chain.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2509_25924_gb300 as ofv  # noqa: E402
+import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+FP32_TOL = 1e-3
+NDET_MIN = 1e-3
+PATHS = [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_PLAIN, ofv.OFV_PATH_TILE]
+
+
+def _variant_params(gauss_sigma=0.0, inc=False, **kw):
+    p = dict(kw)
+    if gauss_sigma > 0:
+        p.update(window=ofv.OFV_WINDOW_GAUSS, window_sigma=gauss_sigma)
+    if inc:
+        p["increment_form"] = 1
+    return p
+
+
+def _gpu(I1, I2, **kw):
+    H, W = I1.shape
+    kw.setdefault("input", ofv.OFV_IN_F32 if I1.dtype == np.float32 else ofv.OFV_IN_U16)
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(**kw))
+    try:
+        t1 = torch.from_numpy(np.ascontiguousarray(I1)).to(DEV)
+        t2 = torch.from_numpy(np.ascontiguousarray(I2)).to(DEV)
+        u = torch.empty((H, W), device=DEV); v = torch.empty_like(u)
+        ofv.ofv_compute(h, t1, t2, u, v)
+        torch.cuda.synchronize()
+        return u.cpu().numpy(), v.cpu().numpy()
+    finally:
+        ofv.ofv_destroy(h)
+
+
+def _oracle(I1, I2, psl, kr, it, sigma=0.0, inc=False, init=None):
+    bits = 0 if I1.dtype == np.float32 else 12
+    return oracle.flow(I1.astype(np.float64), I2.astype(np.float64),
+                       oracle.Params(psl=psl, kr=kr, it=it, bits=bits, win_sigma=sigma, increment_form=inc,
+                                     init=init), diagnostics=True)
+
+
+def _compare(u, v, ou, ov, nd, label, tol=FP32_TOL, max_masked=0.01):
+    m = nd >= NDET_MIN
+    masked = 1.0 - m.mean()
+    assert np.isfinite(u).all() and np.isfinite(v).all(), f"{label}: non-finite output"
+    assert masked <= max_masked, f"{label}: {masked:.3%} ill-conditioned pixels"
+    dmax = max(np.abs(u - ou)[m].max(), np.abs(v - ov)[m].max())
+    print(f"{label}: max|dV|={dmax:.3e} masked={masked:.4%}")
+    assert dmax <= tol, f"{label}: max |dV| {dmax:.3e} > {tol}"
+    return dmax
+
+
+@pytest.fixture(scope="module")
+def rankine():
+    I1, I2, _, _ = synth.rankine_pair()
+    return I1, I2
+
+
+VARIANTS = [
+    ("gauss_s1.5_kr4", dict(gauss_sigma=1.5), 4),
+    ("gauss_s3_kr7", dict(gauss_sigma=3.0), 7),
+    ("increment_kr4", dict(inc=True), 4),
+    ("gauss_increment_kr3", dict(gauss_sigma=2.0, inc=True), 3),
+]
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("name,var,kr", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_variant_matches_oracle(rankine, path, name, var, kr):
+    I1, I2 = rankine
+    u, v = _gpu(I1, I2, path=path, levels_psl=2, kernel_radius=kr, iterations=3, **_variant_params(**var))
+    ou, ov, nd, _ = _oracle(I1, I2, 2, kr, 3, var.get("gauss_sigma", 0.0), var.get("inc", False))
+    _compare(u, v, ou, ov, nd, f"{name} path {path}")
+
+
+def test_gaussian_window_beyond_the_block_kernel_radius(rankine):
+    """KR 12 runs the one-tile-per-CTA kernel on the fused path."""
+    I1, I2 = rankine
+    u, v = _gpu(I1, I2, levels_psl=1, kernel_radius=12, iterations=2, **_variant_params(gauss_sigma=5.0))
+    ou, ov, nd, _ = _oracle(I1, I2, 1, 12, 2, 5.0)
+    _compare(u, v, ou, ov, nd, "gauss kr12")
+
+
+@pytest.mark.parametrize("storage", [ofv.OFV_STORE_F16, ofv.OFV_STORE_BF16])
+def test_variants_with_reduced_storage(rankine, storage):
+    I1, I2 = rankine
+    var = _variant_params(gauss_sigma=2.0, inc=True)
+    u, v = _gpu(I1, I2, storage=storage, **var)
+    ou, ov, nd, _ = _oracle(I1, I2, 2, 4, 3, 2.0, True)
+    m = nd >= NDET_MIN
+    rms = float(np.sqrt(np.mean((np.hypot(u - ou, v - ov)[m]) ** 2)))
+    assert rms <= 1e-2, rms
+
+
+def test_gaussian_with_wide_sigma_approaches_the_box(rankine):
+    I1, I2 = rankine
+    ub, vb = _gpu(I1, I2)
+    uw, vw = _gpu(I1, I2, **_variant_params(gauss_sigma=1e4))
+    ou, ov, nd, _ = _oracle(I1, I2, 2, 4, 3)
+    m = nd >= NDET_MIN
+    assert max(np.abs(uw - ub)[m].max(), np.abs(vw - vb)[m].max()) < 2e-3
+
+
+def test_batched_and_noalloc_run_the_variants_bitwise_like_compute():
+    var = _variant_params(gauss_sigma=1.8, inc=True, levels_psl=1, kernel_radius=3, iterations=2,
+                          input=ofv.OFV_IN_F32)
+    shapes = [(96, 128), (80, 72), (128, 128)]
+    H, W = 128, 128
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(**var))
+    try:
+        pairs, ref = [], []
+        for k, (hh, ww) in enumerate(shapes):
+            I1, I2, _, _ = synth.rankine_pair(hh, ww, seed=30 + k, R=16.0, dmax=1.5)
+            t1 = torch.from_numpy(I1).to(DEV); t2 = torch.from_numpy(I2).to(DEV)
+            u = torch.empty((hh, ww), device=DEV); v = torch.empty_like(u)
+            pairs.append((t1, t2, u, v))
+            hk = ofv.ofv_create(hh, ww, ofv.ofv_default_params(**var))
+            try:
+                ru = torch.empty_like(u); rv = torch.empty_like(u)
+                ofv.ofv_compute(hk, t1, t2, ru, rv)
+                nu = torch.empty_like(u); nv = torch.empty_like(u)
+                ofv.ofv_compute_noalloc(hh, ww, ofv.ofv_default_params(**var), None, t1, t2, nu, nv)
+                torch.cuda.synchronize()
+                assert torch.equal(nu, ru) and torch.equal(nv, rv)
+                ref.append((ru, rv))
+            finally:
+                ofv.ofv_destroy(hk)
+        ofv.ofv_compute_batched(h, pairs)
+        torch.cuda.synchronize()
+        for (_, _, u, v), (ru, rv) in zip(pairs, ref):
+            assert torch.equal(u, ru) and torch.equal(v, rv)
+    finally:
+        ofv.ofv_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# warm start of a time-resolved sequence
+# --------------------------------------------------------------------------
+def _oracle_chain(F, d, psl, kr, it):
+    out = []
+    for k in range(F.shape[0] - 1):
+        init = (out[k - d][0], out[k - d][1]) if d > 0 and k >= d else None
+        out.append(_oracle(F[k], F[k + 1], psl, kr, it, init=init))
+    return out
+
+
+@pytest.mark.parametrize("d,batch,psl,it,path", [
+    (1, 8, 0, 2, ofv.OFV_PATH_FUSED), (2, 2, 2, 3, ofv.OFV_PATH_FUSED), (3, 4, 1, 2, ofv.OFV_PATH_FUSED),
+    (1, 1, 1, 2, ofv.OFV_PATH_PLAIN),
+])
+def test_warm_started_sequence_matches_the_oracle_chain(d, batch, psl, it, path):
+    n, H, W, kr = 8, 96, 128, 4
+    F = synth.stream_frames(H, W, n, seed=5)
+    p = ofv.ofv_default_params(levels_psl=psl, kernel_radius=kr, iterations=it, max_batch=batch, warm_start=d,
+                               path=path)
+    h = ofv.ofv_create(H, W, p)
+    try:
+        fr = torch.from_numpy(F).to(DEV)
+        us = torch.empty((n - 1, H, W), device=DEV); vs = torch.empty_like(us)
+        ofv.ofv_compute_sequence(h, n, fr, H * W * 2, us, vs, H * W)
+        torch.cuda.synchronize()
+        # the same sequence from host memory gives the same fields bitwise
+        hu = torch.empty((n - 1, H, W)).pin_memory(); hv = torch.empty_like(hu).pin_memory()
+        ofv.ofv_compute_sequence_host(h, n, torch.from_numpy(F).pin_memory(), H * W * 2, hu, hv, H * W)
+        torch.cuda.synchronize()
+        assert torch.equal(hu, us.cpu()) and torch.equal(hv, vs.cpu())
+        ref = _oracle_chain(F, d, psl, kr, it)
+        for k in range(n - 1):
+            ou, ov, nd, _ = ref[k]
+            _compare(us[k].cpu().numpy(), vs[k].cpu().numpy(), ou, ov, nd, f"warm d={d} pair {k}")
+    finally:
+        ofv.ofv_destroy(h)
+
+
+def test_warm_start_pairs_before_d_equal_the_cold_start():
+    n, H, W = 6, 96, 128
+    F = synth.stream_frames(H, W, n, seed=6)
+    fr = torch.from_numpy(F).to(DEV)
+    res = []
+    for d in (0, 3):
+        h = ofv.ofv_create(H, W, ofv.ofv_default_params(max_batch=4, warm_start=d))
+        try:
+            us = torch.empty((n - 1, H, W), device=DEV); vs = torch.empty_like(us)
+            ofv.ofv_compute_sequence(h, n, fr, H * W * 2, us, vs, H * W)
+            torch.cuda.synchronize()
+            res.append((us.clone(), vs.clone()))
+        finally:
+            ofv.ofv_destroy(h)
+    assert torch.equal(res[0][0][:3], res[1][0][:3]) and torch.equal(res[0][1][:3], res[1][1][:3])
+    assert not torch.equal(res[0][0][3:], res[1][0][3:])
+
+
+def test_warm_start_beyond_the_batch_is_rejected():
+    H, W = 96, 128
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(max_batch=2, warm_start=3))
+    try:
+        F = torch.zeros((4, H, W), dtype=torch.uint16, device=DEV)
+        u = torch.empty((3, H, W), device=DEV)
+        with pytest.raises(ofv.OfvError) as ei:
+            ofv.ofv_compute_sequence(h, 4, F, H * W * 2, u, torch.empty_like(u), H * W)
+        assert ei.value.status == ofv.OFV_ERR_INVALID_ARG
+    finally:
+        ofv.ofv_destroy(h)
+
+
+@pytest.mark.parametrize("var", [dict(gauss_sigma=2.0), dict(inc=True)])
+def test_reverse_mode_rejects_the_variants(var):
+    H, W = 64, 64
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(input=ofv.OFV_IN_F32, levels_psl=1, **_variant_params(**var)))
+    try:
+        z = torch.zeros((H, W), device=DEV)
+        with pytest.raises(ofv.OfvError) as ei:
+            ofv.ofv_backward(h, z, z, z, z, torch.empty_like(z), torch.empty_like(z))
+        assert ei.value.status == ofv.OFV_ERR_UNSUPPORTED
+    finally:
+        ofv.ofv_destroy(h)
