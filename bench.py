@@ -369,6 +369,21 @@ def e2e(args, ofv, torch, h, frames_h, dev, stream, barrier, max_over_ranks, ws)
     pairwise()
     torch.cuda.synchronize()
     out["pairwise_ofv_compute_host_fields_per_s"] = hp / (time.perf_counter() - t0)
+    # context: the host link itself (pinned copies of the fields buffer,
+    # one direction at a time); the e2e rate follows it from box to box
+    dbuf = torch.empty(hu.numel() // 4, dtype=torch.float32, device=dev)
+    hbuf = hu.view(-1)[:dbuf.numel()]
+    for name, fn in (("pinned_h2d_gbs", lambda: dbuf.copy_(hbuf, non_blocking=True)),
+                     ("pinned_d2h_gbs", lambda: hbuf.copy_(dbuf, non_blocking=True))):
+        with torch.cuda.stream(stream):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+        out[name] = 3 * dbuf.numel() * 4 / (time.perf_counter() - t0) / 1e9
+    del dbuf
     return out
 
 
