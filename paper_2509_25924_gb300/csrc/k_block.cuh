@@ -260,6 +260,41 @@ __device__ __forceinline__ Sample bilin_staged(const T *__restrict__ rm, float f
     return s;
 }
 
+// Packed FP32 (two lanes per instruction, each lane rounded as the scalar
+// operation): lane x carries frame 1, lane y frame 2.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // b * -1 is exact: one rounding, as a - b
+}
+
+struct Sample2 { float2 val, gx, gy; };
+
+// bilin_staged for the two frames at once, with the same operations in the
+// same order per lane (so each lane equals bilin_staged bitwise): rm1, rm2
+// point at the tap left of column x0 in row y0-1 of each frame's staged
+// neighbourhood; f_x, f_y hold each frame's fractions.
+template <typename T, int SP>
+__device__ __forceinline__ Sample2 bilin_staged2(const T *__restrict__ rm1, const T *__restrict__ rm2, float2 f_x,
+                                                 float2 f_y)
+{
+    auto ld2 = [&](int off) { return make_float2(to_f(rm1[off]), to_f(rm2[off])); };
+    const float2 e0 = ld2(1), e1 = ld2(2);
+    const float2 q00 = ld2(SP), q01 = ld2(SP + 1), q02 = ld2(SP + 2), q03 = ld2(SP + 3);
+    const float2 q10 = ld2(2 * SP), q11 = ld2(2 * SP + 1), q12 = ld2(2 * SP + 2), q13 = ld2(2 * SP + 3);
+    const float2 e2 = ld2(3 * SP + 1), e3 = ld2(3 * SP + 2);
+    Sample2 s;
+    const float2 v0 = fma2(f_x, sub2(q02, q01), q01), v1 = fma2(f_x, sub2(q12, q11), q11);
+    s.val = fma2(f_y, sub2(v1, v0), v0);
+    const float2 da0 = sub2(q02, q00), db0 = sub2(q03, q01), da1 = sub2(q12, q10), db1 = sub2(q13, q11);
+    const float2 gx0 = fma2(f_x, sub2(db0, da0), da0), gx1 = fma2(f_x, sub2(db1, da1), da1);
+    s.gx = fma2(f_y, sub2(gx1, gx0), gx0);
+    const float2 vm = fma2(f_x, sub2(e1, e0), e0), vp = fma2(f_x, sub2(e3, e2), e2);
+    const float2 gy0 = sub2(v1, vm), gy1 = sub2(vp, v0);
+    s.gy = fma2(f_y, sub2(gy1, gy0), gy0);
+    return s;
+}
+
 // Products of one pixel (x, y) of a tile whose staged region lies inside
 // the image: no clamping or border remap is needed while the warp stays
 // within REACH px.  The frame-1 offset -h and frame-2 offset +h share their
@@ -280,8 +315,10 @@ __device__ __forceinline__ void products_interior(const T *__restrict__ st1, con
         const int ix1 = zx ? -ix : -ix - 1, iy1 = zy ? -iy : -iy - 1;
         const float fx1 = zx ? 0.f : 1.f - fx2, fy1 = zy ? 0.f : 1.f - fy2;
         const int base = (y - 1 - sy0) * SP + (x - 1 - sx0);
-        s2 = bilin_staged<T, SP>(st2 + base + iy * SP + ix, fx2, fy2);
-        s1 = bilin_staged<T, SP>(st1 + base + iy1 * SP + ix1, fx1, fy1);
+        const Sample2 s12 = bilin_staged2<T, SP>(st1 + base + iy1 * SP + ix1, st2 + base + iy * SP + ix,
+                                                 make_float2(fx1, fx2), make_float2(fy1, fy2));
+        s1 = Sample{s12.val.x, s12.gx.x, s12.gy.x};
+        s2 = Sample{s12.val.y, s12.gx.y, s12.gy.y};
         // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4
         Gx = 0.25f * (s1.gx + s2.gx);
         Gy = 0.25f * (s1.gy + s2.gy);
