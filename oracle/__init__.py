@@ -50,7 +50,7 @@ class _Params(ctypes.Structure):
         ("bits", ctypes.c_int), ("prefilter", ctypes.c_int), ("w25", ctypes.c_void_p),
         ("eps_rel", ctypes.c_double), ("eps_abs", ctypes.c_double), ("eps_n", ctypes.c_double),
         ("increment_form", ctypes.c_int), ("win_sigma", ctypes.c_double),
-        ("u_init", ctypes.c_void_p), ("v_init", ctypes.c_void_p),
+        ("u_init", ctypes.c_void_p), ("v_init", ctypes.c_void_p), ("mask", ctypes.c_void_p),
     ]
 
 
@@ -73,7 +73,8 @@ def _load():
             lib.orc_window_sum.argtypes = [I, I, P, I, D, P]
             lib.orc_decimate_field.argtypes = [I, I, P, P, I, P, P]
             lib.orc_upsample.argtypes = [I, I, P, P, I, I, P, P]
-            lib.orc_iterate.argtypes = [I, I, P, P, P, P, I, D, D, D, I, P, P, P, P]
+            lib.orc_iterate.argtypes = [I, I, P, P, P, P, I, D, D, D, I, P, P, P, P, P]
+            lib.orc_decimate_mask.argtypes = [I, I, P, I, P]
             lib.orc_iterate.restype = I
             lib.orc_ingest.argtypes = [I, I, P, ctypes.POINTER(_Params), P]
             lib.orc_ingest.restype = I
@@ -103,7 +104,8 @@ class Params:
     """Estimator parameters (Sec. 2, Table 2): PSL pyramid sub-levels, KR
     kernel radius, IT Gauss-Newton iterations per level, NR normalization
     radius (0 = off).  Variants: increment_form, win_sigma > 0 (Gaussian
-    window weights), init = (u0, v0) level-0 initial field (warm start)."""
+    window weights), init = (u0, v0) level-0 initial field (warm start),
+    mask = level-0 region mask (nonzero = valid; masked output is NaN)."""
     psl: int = 2
     kr: int = 4
     it: int = 3
@@ -116,6 +118,7 @@ class Params:
     increment_form: bool = False
     win_sigma: float = 0.0
     init: tuple | None = None
+    mask: np.ndarray | None = None
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Params:
@@ -135,6 +138,12 @@ class Params:
             s.u_init, s.v_init = u0.ctypes.data, v0.ctypes.data
         else:
             s.u_init, s.v_init = None, None
+        if self.mask is not None:
+            m = np.ascontiguousarray(self.mask != 0, dtype=np.uint8)
+            self._keep.append(m)
+            s.mask = m.ctypes.data
+        else:
+            s.mask = None
         s.eps_rel, s.eps_abs, s.eps_n = self.eps_rel, self.eps_abs, self.eps_n
         s.increment_form = 1 if self.increment_form else 0
         return s
@@ -216,6 +225,16 @@ def decimate_field(u, v, level: int):
     return uc, vc
 
 
+def decimate_mask(mask, level: int):
+    """The level-`level` region mask: mask(2^l i, 2^l j) != 0 as 0 / 1."""
+    m = np.ascontiguousarray(mask != 0, dtype=np.uint8)
+    H, W = m.shape
+    h, w = level_sizes(H, W, level)[level]
+    out = np.empty((h, w), dtype=np.uint8)
+    _load().orc_decimate_mask(H, W, _p(m), level, _p(out))
+    return out
+
+
 def upsample(uc, vc, H: int, W: int):
     uc, vc = _f64(uc), _f64(vc)
     u = np.empty((H, W))
@@ -225,14 +244,15 @@ def upsample(uc, vc, H: int, W: int):
 
 
 def iterate(P1, P2, u0, v0, kr: int, eps_rel: float = EPS_REL, eps_abs: float = EPS_ABS,
-            increment_form: bool = False, win_sigma: float = 0.0):
+            increment_form: bool = False, win_sigma: float = 0.0, mask=None):
     """One Gauss-Newton iteration at one level: returns (u, v, ndet, guarded)."""
     P1, P2, u0, v0 = _f64(P1), _f64(P2), _f64(u0), _f64(v0)
     H, W = P1.shape
     u = np.empty((H, W)); v = np.empty((H, W)); nd = np.empty((H, W))
     g = np.empty((H, W), dtype=np.uint8)
+    m = None if mask is None else np.ascontiguousarray(mask != 0, dtype=np.uint8)
     rc = _load().orc_iterate(H, W, _p(P1), _p(P2), _p(u0), _p(v0), kr, float(win_sigma), eps_rel, eps_abs,
-                             1 if increment_form else 0, _p(u), _p(v), _p(nd), _p(g))
+                             1 if increment_form else 0, None if m is None else _p(m), _p(u), _p(v), _p(nd), _p(g))
     if rc:
         raise MemoryError("orc_iterate failed")
     return u, v, nd, g

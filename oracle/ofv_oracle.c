@@ -42,7 +42,11 @@
  *     pixel keeps V0(m) (parity unpinned);
  *   - warm start (a variant for time-resolved sequences): the coarsest level
  *     starts from a given level-0 field sampled at the pixels that level
- *     keeps, V_L(i, j) = V(2^L i, 2^L j) / 2^L, instead of from zero.
+ *     keeps, V_L(i, j) = V(2^L i, 2^L j) / 2^L, instead of from zero;
+ *   - region mask (a variant; masked regions such as a model and its shadow,
+ *     Sec. 7): the products of a masked pixel are left out of every window
+ *     sum (weight 0) at every level, the level-l mask being the level-0 mask
+ *     at (2^l i, 2^l j); the output of a masked pixel is NaN (no vector).
  *
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off ofv_oracle.c -lm
  */
@@ -217,6 +221,18 @@ void orc_window_sum(int H, int W, const double *in, int kr, double sigma, double
         }
 }
 
+/* Region mask at level `level`: the level-0 mask (H x W) at the pixels that
+   level keeps, (2^level i, 2^level j), as 0 / 1. */
+void orc_decimate_mask(int H, int W, const unsigned char *mask, int level, unsigned char *out)
+{
+    int Hs[16], Ws[16];
+    orc_level_sizes(H, W, level, Hs, Ws);
+    const int f = 1 << level;
+    for (int i = 0; i < Hs[level]; ++i)
+        for (int j = 0; j < Ws[level]; ++j)
+            out[(int64_t)i * Ws[level] + j] = mask[(int64_t)(f * i) * W + (int64_t)f * j] ? 1 : 0;
+}
+
 /* Warm start: the level-`level` field taken from a level-0 field (H x W) at
    the pixels that level keeps (even-sample decimation `level` times puts
    level pixel i at level-0 pixel 2^level i), in level units (/ 2^level). */
@@ -263,7 +279,8 @@ void orc_upsample(int Hc, int Wc, const double *uc, const double *vc, int H, int
 /* ------------------------------------------------------------------ */
 int orc_iterate(int H, int W, const double *P1, const double *P2, const double *u0,
                 const double *v0, int kr, double win_sigma, double eps_rel, double eps_abs,
-                int increment_form, double *u, double *v, double *ndet, unsigned char *guarded)
+                int increment_form, const unsigned char *mask, double *u, double *v, double *ndet,
+                unsigned char *guarded)
 {
     int64_t N = (int64_t)H * W;
     double *buf = (double *)malloc(sizeof(double) * (size_t)N * 14);
@@ -294,11 +311,12 @@ int orc_iterate(int H, int W, const double *P1, const double *P2, const double *
             double Gx = 0.5 * (g1x + g2x), Gy = 0.5 * (g1y + g2y);
             double It = B - A;
             double r = increment_form ? -It : (Gx * uk + Gy * vk - It);
-            Gxx[k] = Gx * Gx;
-            Gxy[k] = Gx * Gy;
-            Gyy[k] = Gy * Gy;
-            Gxr[k] = Gx * r;
-            Gyr[k] = Gy * r;
+            double w = (mask && !mask[k]) ? 0.0 : 1.0;  /* masked pixels leave the window sums */
+            Gxx[k] = w * Gx * Gx;
+            Gxy[k] = w * Gx * Gy;
+            Gyy[k] = w * Gy * Gy;
+            Gxr[k] = w * Gx * r;
+            Gyr[k] = w * Gy * r;
         }
 
     /* window sums over N(m) */
@@ -396,7 +414,8 @@ int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_par
     double *nu = (double *)malloc(sizeof(double) * (size_t)N);
     double *nv = (double *)malloc(sizeof(double) * (size_t)N);
     unsigned char *g = (unsigned char *)malloc((size_t)N);
-    if (!cu || !cv || !nu || !nv || !g) { rc = 1; goto done; }
+    unsigned char *lm = p->mask ? (unsigned char *)malloc((size_t)N) : NULL;
+    if (!cu || !cv || !nu || !nv || !g || (p->mask && !lm)) { rc = 1; goto done; }
     for (int l = 0; l < L; ++l)
         if (!pyr1[l] || !pyr2[l]) { rc = 1; goto done; }
 
@@ -424,10 +443,11 @@ int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_par
             memcpy(cu, nu, sizeof(double) * (size_t)n);
             memcpy(cv, nv, sizeof(double) * (size_t)n);
         }
+        if (lm) orc_decimate_mask(H, W, p->mask, l, lm);
         for (int t = 0; t < p->it; ++t) {
             int last = (l == 0 && t == p->it - 1);
             if (orc_iterate(h, w, pyr1[l], pyr2[l], cu, cv, p->kr, p->win_sigma, p->eps_rel, p->eps_abs,
-                            p->increment_form, nu, nv, last ? ndet : NULL, g)) {
+                            p->increment_form, lm, nu, nv, last ? ndet : NULL, g)) {
                 rc = 1;
                 goto done;
             }
@@ -437,13 +457,16 @@ int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_par
             memcpy(cv, nv, sizeof(double) * (size_t)n);
         }
     }
-    /* step 6: the level-0 field */
+    /* step 6: the level-0 field; no vector at masked pixels */
     memcpy(u, cu, sizeof(double) * (size_t)N);
     memcpy(v, cv, sizeof(double) * (size_t)N);
+    if (p->mask)
+        for (int64_t m = 0; m < N; ++m)
+            if (!p->mask[m]) u[m] = v[m] = NAN;
 
 done:
     for (int l = 0; l < L; ++l) { free(pyr1[l]); free(pyr2[l]); }
-    free(cu); free(cv); free(nu); free(nv); free(g);
+    free(cu); free(cv); free(nu); free(nv); free(g); free(lm);
     return rc;
 }
 

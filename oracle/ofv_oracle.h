@@ -26,6 +26,8 @@ typedef struct {
     double win_sigma;     /* > 0: Gaussian window weights exp(-(a^2+b^2)/(2 sigma^2)); 0: uniform box */
     const double *u_init; /* initial level-0 field (warm start), or NULL for V = 0 at the coarsest level */
     const double *v_init;
+    const unsigned char *mask; /* level-0 region mask (nonzero = valid), or NULL: masked pixels' products are
+                                  left out of every window sum and their output is NaN */
 } orc_params;
 
 void orc_scale(int64_t n, const double *raw, int bits, double *out);
@@ -40,7 +42,9 @@ void orc_upsample(int Hc, int Wc, const double *uc, const double *vc, int H, int
                   double *u, double *v);
 int orc_iterate(int H, int W, const double *P1, const double *P2, const double *u0,
                 const double *v0, int kr, double win_sigma, double eps_rel, double eps_abs,
-                int increment_form, double *u, double *v, double *ndet, unsigned char *guarded);
+                int increment_form, const unsigned char *mask, double *u, double *v, double *ndet,
+                unsigned char *guarded);
+void orc_decimate_mask(int H, int W, const unsigned char *mask, int level, unsigned char *out);
 void orc_decimate_field(int H, int W, const double *u, const double *v, int level, double *uc, double *vc);
 void orc_level_sizes(int H, int W, int psl, int *Hs, int *Ws);
 int orc_ingest(int H, int W, const double *raw, const orc_params *p, double *out);

@@ -231,7 +231,7 @@ int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const or
     if (H < 1 || W < 1 || p->psl < 0 || p->psl > 15 || p->kr < 0 || p->it < 1) return 2;
     if (p->nr > 0) return 3;
     /* the reverse mode covers the direct form with the uniform box, from V = 0 */
-    if (p->increment_form || p->win_sigma > 0.0 || p->u_init || p->v_init) return 3;
+    if (p->increment_form || p->win_sigma > 0.0 || p->u_init || p->v_init || p->mask) return 3;
     const int L = p->psl + 1, S = L * p->it;
     int Hs[16], Ws[16];
     orc_level_sizes(H, W, p->psl, Hs, Ws);
@@ -286,7 +286,7 @@ int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const or
             memcpy(V0[2 * s], V[2 * (s - 1)], sizeof(double) * (size_t)Hs[l] * Ws[l]);
             memcpy(V0[2 * s + 1], V[2 * (s - 1) + 1], sizeof(double) * (size_t)Hs[l] * Ws[l]);
         }
-        if (orc_iterate(Hs[l], Ws[l], pyr1[l], pyr2[l], V0[2 * s], V0[2 * s + 1], p->kr, 0.0, p->eps_rel, p->eps_abs, 0,
+        if (orc_iterate(Hs[l], Ws[l], pyr1[l], pyr2[l], V0[2 * s], V0[2 * s + 1], p->kr, 0.0, p->eps_rel, p->eps_abs, 0, NULL,
                         V[2 * s], V[2 * s + 1], NULL, NULL)) { rc = 1; goto done; }
     }
     if (u) memcpy(u, V[2 * (S - 1)], sizeof(double) * N);

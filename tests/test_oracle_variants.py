@@ -205,3 +205,91 @@ def test_reverse_mode_rejects_the_variants():
     for kw in (dict(increment_form=True), dict(win_sigma=1.5), dict(init=(g, g))):
         with pytest.raises(RuntimeError):
             oracle.flow_grad(I1, I2, oracle.Params(psl=0, kr=2, it=1, **kw), g, g)
+
+
+# ---------------------------------------------------------------------------
+# Region mask
+# ---------------------------------------------------------------------------
+def test_decimated_mask_is_every_2l_th_sample():
+    m = (RNG.random((37, 50)) > 0.3).astype(np.uint8) * 7
+    for level in (0, 1, 2, 3):
+        f = 2 ** level
+        assert np.array_equal(oracle.decimate_mask(m, level), (m[::f, ::f] != 0).astype(np.uint8))
+
+
+@pytest.mark.parametrize("psl", [0, 2])
+def test_all_valid_mask_is_no_mask_bitwise(psl):
+    I1, I2, _, _ = synth.rankine_pair(48, 40, seed=8, R=10.0, dmax=1.2)
+    a = oracle.flow(I1, I2, oracle.Params(psl=psl, kr=3, it=2))
+    b = oracle.flow(I1, I2, oracle.Params(psl=psl, kr=3, it=2, mask=np.ones((48, 40), np.uint8)))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_masked_one_step_is_lucas_kanade_over_the_valid_taps():
+    """PSL 0, IT 1 from V = 0 with a mask: per window, least squares of
+    G.V = -It over the valid taps only; masked pixels give no vector."""
+    kr = 2
+    I1 = _particles(14, 14, seed=51, ppp=0.15)
+    I2 = _particles(14, 14, seed=52, ppp=0.15) * 0.2 + I1 * 0.8
+    m = np.ones((14, 14), np.uint8)
+    m[3:6, 4:9] = 0
+    m[10:, 11:] = 0
+    u, v = oracle.flow(I1, I2, oracle.Params(psl=0, kr=kr, it=1, mask=m))
+    p1 = np.pad(I1, 1, mode="edge"); p2 = np.pad(I2, 1, mode="edge")
+    gx = 0.25 * ((p1[1:-1, 2:] - p1[1:-1, :-2]) + (p2[1:-1, 2:] - p2[1:-1, :-2]))
+    gy = 0.25 * ((p1[2:, 1:-1] - p1[:-2, 1:-1]) + (p2[2:, 1:-1] - p2[:-2, 1:-1]))
+    it = I2 - I1
+    for i in range(14):
+        for j in range(14):
+            if not m[i, j]:
+                assert np.isnan(u[i, j]) and np.isnan(v[i, j])
+                continue
+            rows, rhs = [], []
+            for a in range(-kr, kr + 1):
+                for b in range(-kr, kr + 1):
+                    ii, jj = i + a, j + b
+                    if 0 <= ii < 14 and 0 <= jj < 14 and m[ii, jj]:
+                        rows.append([gx[ii, jj], gy[ii, jj]])
+                        rhs.append(-it[ii, jj])
+            sol = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0]
+            assert abs(sol[0] - u[i, j]) < 1e-9 * max(1.0, abs(sol[0]))
+            assert abs(sol[1] - v[i, j]) < 1e-9 * max(1.0, abs(sol[1]))
+
+
+def test_masked_pixels_have_no_vector_and_a_full_mask_gives_none():
+    I1, I2, _, _ = synth.rankine_pair(40, 48, seed=5, R=10.0, dmax=1.0)
+    m = np.ones((40, 48), np.uint8)
+    m[10:20, 5:30] = 0
+    u, v = oracle.flow(I1, I2, oracle.Params(psl=2, kr=3, it=2, mask=m))
+    assert np.isnan(u[m == 0]).all() and np.isnan(v[m == 0]).all()
+    assert np.isfinite(u[m != 0]).all() and np.isfinite(v[m != 0]).all()
+    u, v = oracle.flow(I1, I2, oracle.Params(psl=1, kr=3, it=2, mask=np.zeros((40, 48), np.uint8)))
+    assert np.isnan(u).all() and np.isnan(v).all()
+
+
+def test_a_masked_pixel_weighs_nothing_at_every_level():
+    """Masking a pixel equals giving its products weight 0: with the whole
+    level masked except a window, the solve uses that window's taps only,
+    so the field inside a valid block is that of the block cut out with the
+    truncated window (PSL 0, IT 1, V = 0; borders of the cut-out block act
+    like image borders)."""
+    I1 = _particles(32, 32, seed=61, ppp=0.12)
+    I2 = _particles(32, 32, seed=62, ppp=0.12) * 0.25 + I1 * 0.75
+    m = np.zeros((32, 32), np.uint8)
+    m[8:24, 6:26] = 1
+    u, v = oracle.flow(I1, I2, oracle.Params(psl=0, kr=2, it=1, mask=m))
+    # the cut-out block sees its own image samples, but its central
+    # differences at the block edge read pixels outside it: rebuild the
+    # products on the full image and sum over valid taps only
+    p1 = np.pad(I1, 1, mode="edge"); p2 = np.pad(I2, 1, mode="edge")
+    gx = 0.25 * ((p1[1:-1, 2:] - p1[1:-1, :-2]) + (p2[1:-1, 2:] - p2[1:-1, :-2]))
+    gy = 0.25 * ((p1[2:, 1:-1] - p1[:-2, 1:-1]) + (p2[2:, 1:-1] - p2[:-2, 1:-1]))
+    r = -(I2 - I1)
+    w = m.astype(np.float64)
+    k = np.ones((5, 5))
+    S = [ndimage.correlate(w * a, k, mode="constant") for a in (gx * gx, gx * gy, gy * gy, gx * r, gy * r)]
+    sel = m != 0
+    det = np.where(sel, S[0] * S[2] - S[1] ** 2, 1.0)
+    eu = (S[2] * S[3] - S[1] * S[4]) / det
+    ev = (S[0] * S[4] - S[1] * S[3]) / det
+    assert np.allclose(u[sel], eu[sel], rtol=1e-9, atol=1e-12) and np.allclose(v[sel], ev[sel], rtol=1e-9, atol=1e-12)
