@@ -132,6 +132,16 @@ ofv_status ofv_destroy(ofv_handle *h);
    start as the identity (1 at the centre). */
 ofv_status ofv_set_prefilter(ofv_handle *h, const float *w25, ofv_stream_t s);
 
+/* Region mask (a variant; the masked regions of Sec. 7, such as a model and
+   its shadow): mask is H x W bytes (device), nonzero = valid.  Level l uses
+   the mask at (2^l i, 2^l j).  A masked pixel's products are left out of
+   every window sum at every level, and its output is NaN (no vector).  The
+   mask is copied into handle-owned level masks on stream s and applies to
+   every later compute, sequence and graph-creation call of the handle; NULL
+   clears it.  While a mask is set, ofv_compute_batched and ofv_backward
+   return OFV_ERR_UNSUPPORTED. */
+ofv_status ofv_set_mask(ofv_handle *h, const uint8_t *mask, ofv_stream_t s);
+
 /* Estimate the displacement field between frames I1 (time t) and I2 (time
    t + dt), both H x W of the handle's input type.  Writes u and v (H x W
    float each).  I1, I2, u and v are device pointers; u and v must not alias

@@ -17,7 +17,7 @@ import os
 from . import build as _build
 
 __all__ = [
-    "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter",
+    "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_set_mask",
     "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host",
     "ofv_compute_noalloc", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_level_shape",
     "ofv_read_level",
@@ -34,7 +34,7 @@ OFV_K_INGEST, OFV_K_REDUCE, OFV_K_ITERATE, OFV_K_COUNT = range(4)
 OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED_SYMBOLS = [
-    "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_compute",
+    "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_set_mask", "ofv_compute",
     "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host", "ofv_compute_noalloc",
     "ofv_graph_create", "ofv_graph_launch",
     "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
@@ -73,6 +73,7 @@ def _load_library():
         "ofv_create": ([I, I, ctypes.POINTER(Params), ctypes.POINTER(P)], I),
         "ofv_destroy": ([P], I),
         "ofv_set_prefilter": ([P, P, P], I),
+        "ofv_set_mask": ([P, P, P], I),
         "ofv_compute": ([P, P, P, P, P, P], I),
         "ofv_compute_host": ([P, P, P, P, P, P], I),
         "ofv_compute_sequence": ([P, I, P, Z, P, P, Z, P], I),
@@ -161,6 +162,11 @@ def ofv_destroy(h: int):
 
 def ofv_set_prefilter(h: int, w25, stream=None):
     _check(_lib.ofv_set_prefilter(h, _addr(w25), _stream(stream)), "ofv_set_prefilter")
+
+
+def ofv_set_mask(h: int, mask, stream=None):
+    """Region mask (H x W uint8 device tensor, nonzero = valid), or None to clear."""
+    _check(_lib.ofv_set_mask(h, _addr(mask), _stream(stream)), "ofv_set_mask")
 
 
 def ofv_compute(h: int, I1, I2, u, v, stream=None):

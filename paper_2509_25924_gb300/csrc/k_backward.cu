@@ -556,8 +556,9 @@ extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2
     const ofv_params &p = h->p;
     if (p.norm_radius > 0)
         return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_backward: local normalization (NR=%d) has no adjoint", p.norm_radius);
-    if (p.window != OFV_WINDOW_BOX || p.increment_form)
-        return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_backward: covers the direct form with the uniform box window only");
+    if (p.window != OFV_WINDOW_BOX || p.increment_form || h->mask_on)
+        return fail_msg(OFV_ERR_UNSUPPORTED,
+                        "ofv_backward: covers the direct form with the uniform box window and no region mask only");
     if (p.iterations * h->L > kMaxLevels * 64)
         return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_backward: too many stages");
     BwDevGuard g(h->device);

@@ -393,6 +393,7 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
         if (idx + NT < RW * RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
         float p[5];
         products_interior<T, SP, VAR>(st1, st2, sx0, sy0, a, gx, gy, V0c, p);
+        if (VAR && a.mask && !__ldg(a.mask + (int64_t)gy * a.W + gx)) p[0] = p[1] = p[2] = p[3] = p[4] = 0.f;
         q[0] = p[0];
         q[PLANE] = p[1];
         q[2 * PLANE] = p[2];
@@ -501,6 +502,7 @@ struct SolveStoreT {
             }
         }
         if (a.u_out) {
+            if (VAR && a.mask && !__ldg(a.mask + (int64_t)gy * a.W + gx)) V = make_float2(no_vector(), no_vector());
             a.u_out[(int64_t)gy * a.W + gx] = V.x;
             a.v_out[(int64_t)gy * a.W + gx] = V.y;
         } else {
@@ -638,6 +640,9 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
                 p[3] = Gx * r;
                 p[4] = Gy * r;
             }
+            // a masked pixel leaves the window sums
+            if (VAR && a.mask && gy >= 0 && gy < H && gx >= 0 && gx < W && !__ldg(a.mask + (int64_t)gy * W + gx))
+                p[0] = p[1] = p[2] = p[3] = p[4] = 0.f;
             float *q = prod + ry * RWP + rx;
             q[0] = p[0];
             q[PLANE] = p[1];

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_iter_fused(IterArgs a)
         if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
             const float2 V0 = fetch_v0<MODE>(a, gx, gy);
             pixel_products<T>(a, gx, gy, V0, p);
+            if (a.mask && !a.mask[(int64_t)gy * a.W + gx]) p[0] = p[1] = p[2] = p[3] = p[4] = 0.f;
             const int cy = ry - kr, cx = rx - kr;
             if (cy >= 0 && cy < kTY && cx >= 0 && cx < kTX) v0c[cy * kTX + cx] = V0;
         }
@@ -83,7 +84,8 @@ __global__ void __launch_bounds__(kThreads) k_iter_fused(IterArgs a)
                 for (int t = 0; t < taps; ++t) s += col[t * kTX];
             S[c] = s;
         }
-        const float2 V = solve2(S, v0c[idx], a.eps_rel, a.eps_abs, a.inc);
+        float2 V = solve2(S, v0c[idx], a.eps_rel, a.eps_abs, a.inc);
+        if (PLANAR && a.mask && !a.mask[(int64_t)gy * a.W + gx]) V = make_float2(no_vector(), no_vector());
         if (PLANAR) {
             a.u_out[(int64_t)gy * a.W + gx] = V.x;
             a.v_out[(int64_t)gy * a.W + gx] = V.y;

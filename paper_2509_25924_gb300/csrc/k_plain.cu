@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(256) k_plain_products(IterArgs a, PlainBufs b)
     const float2 V0 = fetch_v0<MODE>(a, x, y);
     float p[5];
     pixel_products<T>(a, x, y, V0, p);
+    if (a.mask && !a.mask[(int64_t)y * a.W + x]) p[0] = p[1] = p[2] = p[3] = p[4] = 0.f;
     const int64_t o = (int64_t)y * a.pitch + x;
 #pragma unroll
     for (int c = 0; c < 5; ++c) b.prod[c * b.plane + o] = p[c];
@@ -73,7 +74,8 @@ __global__ void __launch_bounds__(256) k_plain_colsum_solve(IterArgs a, PlainBuf
     float2 V0 = make_float2(0.f, 0.f);
     if (mode == V0_SAME) V0 = a.V0[(int64_t)y * a.vpitch + x];
     else if (mode == V0_UP) V0 = b.vtmp[(int64_t)y * a.vpitch + x];
-    const float2 V = solve2(S, V0, a.eps_rel, a.eps_abs, a.inc);
+    float2 V = solve2(S, V0, a.eps_rel, a.eps_abs, a.inc);
+    if (PLANAR && a.mask && !a.mask[(int64_t)y * a.W + x]) V = make_float2(no_vector(), no_vector());
     if (PLANAR) {
         a.u_out[(int64_t)y * a.W + x] = V.x;
         a.v_out[(int64_t)y * a.W + x] = V.y;

@@ -301,6 +301,29 @@ __global__ void __launch_bounds__(256) k_seed_field(const __grid_constant__ Seed
     }
 }
 
+// Region mask (a variant; masked regions of Sec. 7 such as a model and its
+// shadow): level l keeps the level-0 mask at (2^l i, 2^l j), as 0 / 1.
+__global__ void __launch_bounds__(256) k_mask_level(const uint8_t *__restrict__ mask, int W0, int level,
+                                                    uint8_t *__restrict__ out, int H, int W)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= W) return;
+    for (int i = blockIdx.y; i < H; i += gridDim.y)
+        out[(int64_t)i * W + j] = __ldg(mask + ((int64_t)i * W0 << level) + ((int64_t)j << level)) != 0 ? 1 : 0;
+}
+
+cudaError_t launch_mask_levels(const uint8_t *mask, int W, uint8_t *const *out, const int *Hs, const int *Ws, int L,
+                               cudaStream_t s)
+{
+    for (int l = 0; l < L; ++l) {
+        k_mask_level<<<dim3((Ws[l] + 255) / 256, Hs[l] < 65535 ? Hs[l] : 65535), 256, 0, s>>>(mask, W, l, out[l], Hs[l],
+                                                                                             Ws[l]);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_seed_fields(const SeedArgs *a, int n, cudaStream_t s)
 {
     if (n < 1 || n > kMaxPairsPerLaunch) return cudaErrorInvalidValue;

@@ -98,6 +98,8 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     const ofv_params &p = h->p;
     if (p.path != OFV_PATH_FUSED || p.kernel_radius > 10)
         return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_compute_batched: needs the fused path with KR <= 10");
+    if (h->mask_on)
+        return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_compute_batched: a region mask is set (it has the handle's size)");
     const int L = h->L, IT = p.iterations, S = L * IT, KR = p.kernel_radius;
     const int minsz = 2 * KR + 1 > 8 ? 2 * KR + 1 : 8;
     const int TS = block_tile_size(KR);

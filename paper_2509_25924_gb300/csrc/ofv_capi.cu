@@ -281,6 +281,7 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
                 x.eps_rel = p.det_rel_eps;
                 x.eps_abs = p.det_abs_eps;
                 set_iter_variant(x, p.kernel_radius, p.window == OFV_WINDOW_GAUSS, p.window_sigma, p.increment_form);
+                x.mask = h->mask_on ? h->mask_lvl[l] : nullptr;
                 if (mode == V0_UP) {
                     x.Vc = vbuf[2 * k + cur];
                     x.Hc = h->Hs[l + 1];
@@ -676,9 +677,38 @@ ofv_status ofv_destroy(ofv_handle *h)
         cudaStreamDestroy(h->hs_stream[0]);
         cudaStreamDestroy(h->hs_stream[1]);
     }
+    if (h->mask_arena) cudaFree(h->mask_arena);
     if (h->arena) cudaFree(h->arena);
     delete h;
     return st;
+}
+
+ofv_status ofv_set_mask(ofv_handle *h, const uint8_t *mask, ofv_stream_t s)
+{
+    if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    if (!mask) {
+        h->mask_on = 0;
+        return OFV_OK;
+    }
+    if (!h->mask_arena) {
+        size_t off[kMaxLevels], total = 0;
+        for (int l = 0; l < h->L; ++l) {
+            off[l] = total;
+            total += align_up((size_t)h->Hs[l] * h->Ws[l], 256);
+        }
+        if (cudaMalloc(&h->mask_arena, total) != cudaSuccess) {
+            cudaGetLastError();
+            h->mask_arena = nullptr;
+            return fail(OFV_ERR_ALLOC, "cudaMalloc of %zu mask bytes failed", total);
+        }
+        for (int l = 0; l < h->L; ++l) h->mask_lvl[l] = static_cast<uint8_t *>(h->mask_arena) + off[l];
+    }
+    cudaError_t e = launch_mask_levels(mask, h->W, h->mask_lvl, h->Hs, h->Ws, h->L, (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e, "mask level launch");
+    h->mask_on = 1;
+    return OFV_OK;
 }
 
 ofv_status ofv_set_prefilter(ofv_handle *h, const float *w25, ofv_stream_t s)

@@ -57,6 +57,7 @@ struct IterArgs {
     int vpitch;
     int kr;
     float eps_rel, eps_abs;
+    const uint8_t *mask;  // region mask of the level (dense rows of W, 0 = masked), or null
     int inc;              // 1: increment form, r = -It and V = V0(m) + H^-1 (Sxr, Syr)
     int gauss;            // 1: window tap (a, b) weighted wg[|a|] wg[|b|]; 0: uniform box
     float wg[kMaxWindowRadius + 1];  // Gaussian window weights exp(-d^2 / (2 sigma^2)), d = 0..KR
@@ -126,6 +127,14 @@ struct SeedArgs {
     int H, W, vpitch;    // the level's size
 };
 cudaError_t launch_seed_fields(const SeedArgs *a, int n, cudaStream_t s);
+
+// Region mask of every level from the level-0 mask (H x W bytes, nonzero =
+// valid): out[l](i, j) = mask(2^l i, 2^l j) != 0, dense rows of Ws[l].
+cudaError_t launch_mask_levels(const uint8_t *mask, int W, uint8_t *const *out, const int *Hs, const int *Ws, int L,
+                               cudaStream_t s);
+
+// The output of a masked pixel (no vector).
+__device__ __forceinline__ float no_vector() { return __int_as_float(0x7fc00000); }
 
 cudaError_t launch_read_level(const void *src, int H, int W, int pitch, int store, float *dst,
                               cudaStream_t s);

@@ -96,6 +96,11 @@ struct ofv_handle {
     int hs_ready;
     void *hs_stage;
     size_t hs_bytes;
+    // region mask per level (dense rows of Ws[l] bytes, 0 / 1), allocated on
+    // first use; applied while mask_on
+    uint8_t *mask_lvl[ofv::kMaxLevels];
+    void *mask_arena;
+    int mask_on;
 };
 
 namespace ofv {

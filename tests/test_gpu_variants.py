@@ -233,3 +233,78 @@ def test_reverse_mode_rejects_the_variants(var):
         assert ei.value.status == ofv.OFV_ERR_UNSUPPORTED
     finally:
         ofv.ofv_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# region mask
+# --------------------------------------------------------------------------
+def _disk_and_band_mask(H, W):
+    yy, xx = np.mgrid[0:H, 0:W]
+    m = np.ones((H, W), np.uint8)
+    m[(xx - 0.6 * W) ** 2 + (yy - 0.4 * H) ** 2 < (0.08 * W) ** 2] = 0
+    m[int(0.75 * H):int(0.75 * H) + 7, :int(0.5 * W)] = 0
+    return m
+
+
+def _gpu_masked(I1, I2, m, **kw):
+    H, W = I1.shape
+    kw.setdefault("input", ofv.OFV_IN_F32 if I1.dtype == np.float32 else ofv.OFV_IN_U16)
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(**kw))
+    try:
+        ofv.ofv_set_mask(h, torch.from_numpy(m).to(DEV))
+        t1 = torch.from_numpy(np.ascontiguousarray(I1)).to(DEV)
+        t2 = torch.from_numpy(np.ascontiguousarray(I2)).to(DEV)
+        u = torch.empty((H, W), device=DEV); v = torch.empty_like(u)
+        ofv.ofv_compute(h, t1, t2, u, v)
+        torch.cuda.synchronize()
+        return u.cpu().numpy(), v.cpu().numpy()
+    finally:
+        ofv.ofv_destroy(h)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("kr,psl", [(4, 2), (2, 1), (12, 1)])
+def test_masked_field_matches_oracle(rankine, path, kr, psl):
+    I1, I2 = rankine
+    m = _disk_and_band_mask(*I1.shape)
+    u, v = _gpu_masked(I1, I2, m, path=path, levels_psl=psl, kernel_radius=kr, iterations=2)
+    ou, ov, nd, _ = oracle.flow(I1.astype(np.float64), I2.astype(np.float64),
+                                oracle.Params(psl=psl, kr=kr, it=2, mask=m), diagnostics=True)
+    assert np.array_equal(np.isnan(u), m == 0) and np.array_equal(np.isnan(v), m == 0)
+    sel = m != 0
+    _compare(u[sel], v[sel], ou[sel], ov[sel], nd[sel], f"mask kr{kr} psl{psl} path {path}")
+
+
+def test_masked_sequence_and_clearing_the_mask():
+    n, H, W = 6, 96, 128
+    F = synth.stream_frames(H, W, n, seed=9)
+    m = _disk_and_band_mask(H, W)
+    fr = torch.from_numpy(F).to(DEV)
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params(max_batch=2))
+    try:
+        u0 = torch.empty((H, W), device=DEV); v0 = torch.empty_like(u0)
+        ofv.ofv_compute(h, fr[1], fr[2], u0, v0)
+        ofv.ofv_set_mask(h, torch.from_numpy(m).to(DEV))
+        us = torch.empty((n - 1, H, W), device=DEV); vs = torch.empty_like(us)
+        ofv.ofv_compute_sequence(h, n, fr, H * W * 2, us, vs, H * W)
+        u1 = torch.empty_like(u0); v1 = torch.empty_like(u0)
+        ofv.ofv_compute(h, fr[1], fr[2], u1, v1)
+        torch.cuda.synchronize()
+        assert torch.equal(u1.isnan(), torch.from_numpy(m == 0).to(DEV))
+        assert torch.equal(us[1].nan_to_num(7.0), u1.nan_to_num(7.0)) and torch.equal(vs[1].nan_to_num(7.0),
+                                                                                      v1.nan_to_num(7.0))
+        ou, ov, nd, _ = oracle.flow(F[1].astype(np.float64), F[2].astype(np.float64),
+                                    oracle.Params(bits=12, mask=m), diagnostics=True)
+        sel = m != 0
+        _compare(u1.cpu().numpy()[sel], v1.cpu().numpy()[sel], ou[sel], ov[sel], nd[sel], "masked u16 pair")
+        for fn in (lambda: ofv.ofv_compute_batched(h, [(fr[0], fr[1], u1, v1)]),
+                   lambda: ofv.ofv_backward(h, fr[0], fr[1], u1, v1, torch.empty_like(u1), torch.empty_like(u1))):
+            with pytest.raises(ofv.OfvError) as ei:
+                fn()
+            assert ei.value.status == ofv.OFV_ERR_UNSUPPORTED
+        ofv.ofv_set_mask(h, None)
+        ofv.ofv_compute(h, fr[1], fr[2], u1, v1)
+        torch.cuda.synchronize()
+        assert torch.equal(u1, u0) and torch.equal(v1, v0)
+    finally:
+        ofv.ofv_destroy(h)
