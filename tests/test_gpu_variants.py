@@ -1,6 +1,8 @@
 """GPU parity of the estimator variants against the FP64 oracle, through the
 C ABI: the Gaussian-weighted window, the increment form of the Gauss-Newton
-step and the warm start of a time-resolved sequence from an earlier field.
+step, the warm start of a time-resolved sequence from an earlier field and
+the region mask (no vector, NaN, at masked pixels, exactly where the oracle
+has none).
 
 Tolerances as for the default estimator: FP32 max |dV| <= 1e-3 px over
 pixels whose oracle det/(Sxx+Syy)^2 >= 1e-3.  For a warm-started sequence
