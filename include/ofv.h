@@ -205,6 +205,16 @@ ofv_status ofv_vorticity(int H, int W, int n, const float *u, const float *v, si
 ofv_status ofv_recirculation_area(int H, int W, int n, const float *u, size_t field_stride,
                                   const uint8_t *mask, unsigned long long *counts, ofv_stream_t s);
 
+/* Point probes: the time series of the field at npts points, as a probe
+ * of the live measurement would record it.  xy (device, npts x 2 floats,
+ * 8-byte aligned) holds the points (x along columns, y along rows) in pixel
+ * coordinates; out (device, n x npts x 2 floats, 8-byte aligned) receives
+ * (u, v) of field k at point p at out[2 (k npts + p)].  The field is sampled
+ * bilinearly with clamp-to-edge taps, the interpolation of the estimator; a
+ * tap on a pixel without a vector (region mask) gives NaN.  1 <= n <= 65535. */
+ofv_status ofv_probe(int H, int W, int n, const float *u, const float *v, size_t field_stride, int npts,
+                     const float *xy, float *out, ofv_stream_t s);
+
 /* ---- reverse mode -------------------------------------------------------
  * The paper defines no derivative; this is the chain rule through the steps
  * of Sec. 2 (Eq. 2 and its Gauss-Newton linearisation, the pyramid, the

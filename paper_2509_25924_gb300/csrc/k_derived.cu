@@ -1,5 +1,6 @@
 // Quantities derived from the displacement fields in real time (Sec. 7):
-// the out-of-plane vorticity and the recirculation area of Eq. 6.
+// the out-of-plane vorticity, the recirculation area of Eq. 6 and point
+// probes (time series of the field at chosen points).
 //
 //   omega = dv/dx - du/dy, the derivatives by second-order central
 //   differences inside the field and first-order one-sided differences on
@@ -97,6 +98,30 @@ __global__ void __launch_bounds__(256) k_recirc_count(int64_t N, const float *u,
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(counts + blockIdx.y, c);
 }
 
+// Point probes: the field of every one of n fields at npts points (x, y) in
+// pixel coordinates, bilinear with clamp-to-edge taps (the interpolation of
+// the estimator).  One thread per (point, field).
+__global__ void __launch_bounds__(256) k_probe(int H, int W, const float *u, const float *v, size_t stride, int npts,
+                                               const float2 *xy, float2 *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npts) return;
+    const size_t f = (size_t)blockIdx.y * stride;
+    const float2 p = __ldg(xy + k);
+    const float flx = floorf(p.x), fly = floorf(p.y);
+    const float fx = p.x - flx, fy = p.y - fly;
+    const int x0 = (int)fminf(fmaxf(flx, -1.f), (float)W), y0 = (int)fminf(fmaxf(fly, -1.f), (float)H);
+    const int xa = min(max(x0, 0), W - 1), xb = min(max(x0 + 1, 0), W - 1);
+    const int ya = min(max(y0, 0), H - 1), yb = min(max(y0 + 1, 0), H - 1);
+    const float *uf = u + f, *vf = v + f;
+    auto bil = [&](const float *g) {
+        const float a = __ldg(g + (size_t)ya * W + xa), b = __ldg(g + (size_t)ya * W + xb);
+        const float c = __ldg(g + (size_t)yb * W + xa), d = __ldg(g + (size_t)yb * W + xb);
+        return (1.f - fy) * ((1.f - fx) * a + fx * b) + fy * ((1.f - fx) * c + fx * d);
+    };
+    out[(size_t)blockIdx.y * npts + k] = make_float2(bil(uf), bil(vf));
+}
+
 }  // namespace ofv
 
 using namespace ofv;
@@ -140,6 +165,23 @@ ofv_status ofv_recirculation_area(int H, int W, int n, const float *u, size_t fi
     k_recirc_count<<<dim3(blocks, n), 256, 0, cs>>>(N, u, field_stride, mask, counts, vec);
     e = cudaGetLastError();
     return e == cudaSuccess ? OFV_OK : cuda_fail_msg(e, "ofv_recirculation_area launch");
+}
+
+ofv_status ofv_probe(int H, int W, int n, const float *u, const float *v, size_t field_stride, int npts,
+                     const float *xy, float *out, ofv_stream_t s)
+{
+    if (!u || !v || !xy || !out) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_probe: u, v, xy and out must be non-NULL");
+    if (H < 1 || W < 1 || n < 1 || n > 65535 || npts < 1)
+        return fail_msg(OFV_ERR_SHAPE, "ofv_probe: H=%d W=%d n=%d npts=%d (n at most 65535)", H, W, n, npts);
+    if (field_stride < (size_t)H * W)
+        return fail_msg(OFV_ERR_INVALID_ARG, "ofv_probe: field_stride=%zu is smaller than one field", field_stride);
+    if ((reinterpret_cast<uintptr_t>(xy) | reinterpret_cast<uintptr_t>(out)) & 7u)
+        return fail_msg(OFV_ERR_INVALID_ARG, "ofv_probe: xy and out must be 8-byte aligned");
+    k_probe<<<dim3((npts + 255) / 256, n), 256, 0, (cudaStream_t)s>>>(H, W, u, v, field_stride, npts,
+                                                                     reinterpret_cast<const float2 *>(xy),
+                                                                     reinterpret_cast<float2 *>(out));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OFV_OK : cuda_fail_msg(e, "ofv_probe launch");
 }
 
 }  // extern "C"

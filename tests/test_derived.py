@@ -1,5 +1,5 @@
-"""Quantities derived from the fields (Sec. 7): vorticity and the
-recirculation area of Eq. 6.
+"""Quantities derived from the fields (Sec. 7): vorticity, the
+recirculation area of Eq. 6 and point probes.
 
 CPU pins of the oracle: numpy.gradient (an independent finite-difference
 gradient with the same interior/border scheme), exactness on linear fields
@@ -116,3 +116,39 @@ def test_gpu_recirculation_count_is_exact(masked, H, W):
     got = counts.cpu().numpy()
     for k in range(n):
         assert got[k] == oracle.recirculation_count(u[k].astype(np.float64), mask)
+
+
+def test_probe_oracle_is_scipy_bilinear():
+    """A probe is the estimator's bilinear interpolation (clamp-to-edge):
+    scipy's map_coordinates(order=1, mode='nearest') at the same points."""
+    from scipy import ndimage
+    f = RNG.standard_normal((23, 31))
+    pts = np.concatenate([RNG.uniform(-3, 34, (40, 2)), [[0, 0], [30, 22], [12.5, 7.25], [-0.5, 22.7]]])
+    got = np.array([oracle.bilinear(f, x, y) for x, y in pts])
+    ref = ndimage.map_coordinates(f, [pts[:, 1], pts[:, 0]], order=1, mode="nearest")
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.gpu
+def test_gpu_probes_match_the_oracle_bilinear():
+    torch = pytest.importorskip("torch")
+    import paper_2509_25924_gb300 as ofv
+    n, H, W, npts = 4, 77, 131, 300
+    u, v = _fields(n, H, W, seed=11)
+    u[2, 10, 20] = np.nan  # a pixel without a vector
+    pts = np.concatenate([RNG.uniform(-4, W + 4, (npts - 4, 1)), RNG.uniform(-4, H + 4, (npts - 4, 1))], axis=1)
+    pts = np.concatenate([pts, [[20.0, 10.0], [20.5, 10.5], [0.0, 0.0], [W - 1.0, H - 1.0]]]).astype(np.float32)
+    dev = torch.device("cuda:0")
+    tu = torch.from_numpy(u).to(dev); tv = torch.from_numpy(v).to(dev)
+    out = torch.full((n, npts, 2), 7.0, device=dev)
+    ofv.ofv_probe(H, W, n, tu, tv, H * W, npts, torch.from_numpy(pts).to(dev), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for k in range(n):
+        for p, (x, y) in enumerate(pts.astype(np.float64)):
+            ru = oracle.bilinear(u[k].astype(np.float64), x, y)
+            rv = oracle.bilinear(v[k].astype(np.float64), x, y)
+            if np.isnan(ru):
+                assert np.isnan(got[k, p, 0])
+                continue
+            assert abs(got[k, p, 0] - ru) <= 2e-6 * max(1.0, abs(ru)) and abs(got[k, p, 1] - rv) <= 2e-6 * max(1.0, abs(rv))
