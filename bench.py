@@ -172,19 +172,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str):
-    """DRAM bytes per launch of the fused iteration kernel from a committed
-    ncu summary, if it was taken on the current kernel source."""
+def ncu_record(workload: str) -> dict:
+    """The committed ncu figures of the fused iteration kernel (DRAM bytes
+    per launch, issue-active fraction), if they were taken on the current
+    kernel source, else {}."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d.get(workload)
         if e and e.get("kernel_hash") == kernel_source_hash():
-            return e.get("dram_bytes_per_launch_scaled")
+            return e
     except Exception:
         pass
-    return None
+    return {}
 
 
 def reduce_max(x: float, dist=None, device="cpu") -> float:
@@ -273,13 +274,18 @@ def run_ours(args, ws, rank, local):
     # the fused path launches one kernel per timed record (ingest, reduce, iteration)
     launches_per_step = sum(p[1] for p in prof.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(workload),
+                "frac": achieved / peak, "traffic": ncu_record(workload).get("dram_bytes_per_launch_scaled"),
                 "kernel": "k_iter_block (one Gauss-Newton iteration of one level, all pairs of a group)",
                 "alg_bytes_per_launch": b_k / n_k, "launch_ms": ms_k / n_k, "launches_per_step": n_k,
                 "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
                 "share_of_step": ms_k / sum(p[0] for p in prof.values()),
                 "step_alg_bytes_per_field": alg_bytes_field,
                 "step_frac": alg_bytes_field * (value / ws) / 1e9 / peak}
+    issue = ncu_record(workload).get("issue_active_pct")
+    if issue is not None:
+        # what bounds the kernel in fact: the schedulers issue on this share
+        # of cycles (ncu smsp__issue_active, level-0 launch)
+        roofline["issue_active_frac"] = issue / 100.0
 
     line = {
         "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": ws, "steps": args.steps,
