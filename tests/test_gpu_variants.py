@@ -310,3 +310,29 @@ def test_masked_sequence_and_clearing_the_mask():
         assert torch.equal(u1, u0) and torch.equal(v1, v0)
     finally:
         ofv.ofv_destroy(h)
+
+
+def test_graph_replay_runs_the_variants_and_the_mask_like_compute(rankine):
+    """A CUDA graph recorded with the Gaussian window, the increment form and
+    a region mask replays bitwise the field of ofv_compute."""
+    I1, I2 = rankine
+    H, W = I1.shape
+    m = _disk_and_band_mask(H, W)
+    p = ofv.ofv_default_params(input=ofv.OFV_IN_F32, **_variant_params(gauss_sigma=2.5, inc=True))
+    h = ofv.ofv_create(H, W, p)
+    try:
+        ofv.ofv_set_mask(h, torch.from_numpy(m).to(DEV))
+        t1 = torch.from_numpy(I1).to(DEV); t2 = torch.from_numpy(I2).to(DEV)
+        u = torch.empty((H, W), device=DEV); v = torch.empty_like(u)
+        ofv.ofv_compute(h, t1, t2, u, v)
+        gu = torch.empty_like(u); gv = torch.empty_like(u)
+        g = ofv.ofv_graph_create(h, t1, t2, gu, gv)
+        try:
+            ofv.ofv_graph_launch(g)
+            torch.cuda.synchronize()
+        finally:
+            ofv.ofv_graph_destroy(g)
+        assert torch.equal(gu.nan_to_num(9.0), u.nan_to_num(9.0)) and torch.equal(gv.nan_to_num(9.0), v.nan_to_num(9.0))
+        assert torch.equal(gu.isnan().cpu(), torch.from_numpy(m == 0))
+    finally:
+        ofv.ofv_destroy(h)
