@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--frames", type=int, default=FRAMES1, help="frames in the 1 Mp stream (pairs + 1)")
+    ap.add_argument("--backward-only", action="store_true",
+                    help="time only the reverse mode on 1 Mp pairs of the stream (one JSON line)")
     return ap.parse_args()
 
 
@@ -316,6 +318,7 @@ def run_ours(args, ws, rank, local):
         line["variants_1Mp"] = variants(ofv, torch, synth, dev, stream, frames, u, v)
         line["paper_perf_set"] = paper_perf_set(ofv, torch, synth, dev, stream)
         line["batched_64_uneven"] = batched_uneven(ofv, torch, synth, dev, stream)
+        line["backward_1Mp"] = backward_1mp(ofv, torch, frames, dev, stream)
 
     ofv.ofv_destroy(h)
     del u, v, frames
@@ -725,11 +728,56 @@ def cpu_baseline(frames_h):
             "sample": f"{n} pairs of the 1 Mp stream, FP64 oracle with OpenMP over rows on all host cores"}
 
 
+def backward_1mp(ofv, torch, frames, dev, stream, n_pairs=20, reps=3):
+    """Reverse mode on 1 Mp pairs of the stream (12-bit, PSL 2, KR 4, IT 3,
+    5x5 pre-filter on): dL/dI1, dL/dI2 and dL/dw for random dL/du, dL/dv,
+    the forward pass recomputed inside; ms per pair by CUDA events."""
+    N = H1 * W1
+    h = ofv.ofv_create(H1, W1, ofv.ofv_default_params(prefilter=1))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    gu = torch.randn((H1, W1), device=dev, generator=gen)
+    gv = torch.randn((H1, W1), device=dev, generator=gen)
+    g1 = torch.empty((H1, W1), device=dev); g2 = torch.empty_like(g1); gw = torch.empty(25, device=dev)
+    try:
+        def run():
+            for k in range(n_pairs):
+                ofv.ofv_backward(h, frames[k], frames[k + 1], gu, gv, g1, g2, gw, stream)
+        run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (reps * n_pairs)
+    finally:
+        ofv.ofv_destroy(h)
+    return {"ms_per_pair": ms, "pairs_per_s": 1e3 / ms, "mvectors_per_s": N / 1e3 / ms,
+            "workload": "1024x1024 u16 stream pairs, PSL 2 KR 4 IT 3, pre-filter on; gradients w.r.t. both frames "
+                        "and the 25 weights, forward recomputed"}
+
+
+def run_backward_only(args):
+    import torch
+    import paper_2509_25924_gb300 as ofv
+    import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    frames = torch.from_numpy(synth.stream_frames(H1, W1, 21, seed=2)).to(dev)
+    print(json.dumps({"backward_1Mp": backward_1mp(ofv, torch, frames, dev, torch.cuda.current_stream(),
+                                                   reps=max(1, args.steps))}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.backward_only:
+        run_backward_only(args)
         return
     run_ours(args, ws, rank, local)
 
