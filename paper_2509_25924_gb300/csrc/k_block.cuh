@@ -43,8 +43,12 @@ struct BlockParams {
 };
 
 template <int KR> struct BlockShape {
-    static constexpr int TS = KR <= 5 ? 48 : 32;          // output tile edge
-    static constexpr int NT = KR <= 5 ? 512 : 256;        // threads
+    // KR 6..8: 32-px tiles, two CTAs per SM; KR 9, 10: 48-px tiles (less
+    // halo work), one CTA per SM (measured faster than the 32-px tiles
+    // there, slower at KR 6..8)
+    static constexpr int TS = (KR <= 5 || KR >= 9) ? 48 : 32;   // output tile edge
+    static constexpr int NT = (KR <= 5 || KR >= 9) ? 512 : 256; // threads
+    static constexpr int MINB = KR >= 9 ? 1 : 2;                // resident CTAs per SM (shared memory)
     static constexpr int RW = TS + 2 * KR;                // product region edge
     static constexpr int RWP = RW | 1;                    // odd row pitch of the product planes
     static constexpr int SH = RW + 2 * kBlockReach + 3;   // staged rows
@@ -698,7 +702,7 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
 
 // One tile per CTA; blockIdx.z selects the pair.  VAR: estimator variants.
 template <typename T, int KR, bool VAR>
-__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_block(const __grid_constant__ BlockParams prm)
+__global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_iter_block(const __grid_constant__ BlockParams prm)
 {
     extern __shared__ __align__(128) float4 smem_f4[];
     __shared__ __align__(8) uint64_t s_bar[StageShape<T, KR>::NBAND];
@@ -759,7 +763,7 @@ template <int TS>
 __device__ __forceinline__ int tiles_of(int H, int W) { return ((W + TS - 1) / TS) * ((H + TS - 1) / TS); }
 
 template <typename T, int KR, bool VAR>
-__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_iter_queue(const __grid_constant__ QueueParams q)
+__global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_iter_queue(const __grid_constant__ QueueParams q)
 {
     constexpr int TS = BlockShape<KR>::TS;
     extern __shared__ __align__(128) float4 smem_f4[];
@@ -861,6 +865,9 @@ template <typename T, bool VAR>
 int queue_occupancy_t(int kr);
 
 // Output tile edge of the block kernel for radius kr.
-inline int block_tile_size(int kr) { return kr <= 5 ? BlockShape<5>::TS : BlockShape<10>::TS; }
+inline int block_tile_size(int kr)
+{
+    return kr <= 5 ? BlockShape<5>::TS : kr <= 8 ? BlockShape<8>::TS : BlockShape<10>::TS;
+}
 
 }  // namespace ofv

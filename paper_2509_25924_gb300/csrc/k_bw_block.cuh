@@ -61,7 +61,7 @@ struct BwStageParams {
 };
 
 template <typename T, int KR>
-__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_bw_stage_S(const __grid_constant__ BwStageParams q)
+__global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_bw_stage_S(const __grid_constant__ BwStageParams q)
 {
     extern __shared__ __align__(128) float4 smem_f4[];
     block_tile<T, KR, false, BwSolveAdj>(q.a, V0_SAME, blockIdx.x, blockIdx.y, smem_f4, nullptr, nullptr, nullptr,
@@ -90,7 +90,7 @@ cudaError_t run_bw_stage_S(const BwStageParams &q, cudaStream_t s)
 // CTA: the (TS+2KR)^2 input region (zero outside the image) in shared
 // memory, then the forward kernel's horizontal and vertical passes.
 template <int KR>
-__global__ void __launch_bounds__(BlockShape<KR>::NT, 2) k_bw_box_tile(Planes5 in, Planes5 out, int H, int W)
+__global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_bw_box_tile(Planes5 in, Planes5 out, int H, int W)
 {
     using BS = BlockShape<KR>;
     constexpr int TS = BS::TS, NT = BS::NT, RW = BS::RW, RWP = BS::RWP, PLANE = RW * RWP;
