@@ -239,31 +239,6 @@ __device__ __forceinline__ Sample sample_staged(const T *__restrict__ st, int sx
     return s;
 }
 
-// Bilinear value and doubled gradient (undivided central differences) of a
-// staged 4x4 neighbourhood: rm points at the tap left of column x0 in row
-// y0-1.  Interpolation as a + f (b - a).
-template <typename T, int SP>
-__device__ __forceinline__ Sample bilin_staged(const T *__restrict__ rm, float fx, float fy)
-{
-    const T *r0 = rm + SP, *r1 = rm + 2 * SP, *rp = rm + 3 * SP;
-    const float e0 = to_f(rm[1]), e1 = to_f(rm[2]);
-    const float q00 = to_f(r0[0]), q01 = to_f(r0[1]), q02 = to_f(r0[2]), q03 = to_f(r0[3]);
-    const float q10 = to_f(r1[0]), q11 = to_f(r1[1]), q12 = to_f(r1[2]), q13 = to_f(r1[3]);
-    const float e2 = to_f(rp[1]), e3 = to_f(rp[2]);
-    Sample s;
-    const float v0 = fmaf(fx, q02 - q01, q01), v1 = fmaf(fx, q12 - q11, q11);
-    s.val = fmaf(fy, v1 - v0, v0);
-    const float da0 = q02 - q00, db0 = q03 - q01, da1 = q12 - q10, db1 = q13 - q11;
-    const float gx0 = fmaf(fx, db0 - da0, da0), gx1 = fmaf(fx, db1 - da1, da1);
-    s.gx = fmaf(fy, gx1 - gx0, gx0);
-    // row-interpolated values above and below: the row interpolation of the
-    // column differences equals the difference of row interpolations
-    const float vm = fmaf(fx, e1 - e0, e0), vp = fmaf(fx, e3 - e2, e2);
-    const float gy0 = v1 - vm, gy1 = vp - v0;
-    s.gy = fmaf(fy, gy1 - gy0, gy0);
-    return s;
-}
-
 // Packed FP32 (two lanes per instruction, each lane rounded as the scalar
 // operation): lane x carries frame 1, lane y frame 2.
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -274,10 +249,12 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 
 struct Sample2 { float2 val, gx, gy; };
 
-// bilin_staged for the two frames at once, with the same operations in the
-// same order per lane (so each lane equals bilin_staged bitwise): rm1, rm2
-// point at the tap left of column x0 in row y0-1 of each frame's staged
-// neighbourhood; f_x, f_y hold each frame's fractions.
+// Bilinear value and doubled gradient (undivided central differences) of a
+// staged 4x4 neighbourhood, for the two frames at once: rm1, rm2 point at
+// the tap left of column x0 in row y0-1 of each frame's staged tile; f_x,
+// f_y hold each frame's fractions.  Interpolation as a + f (b - a); the
+// row interpolation of the column differences equals the difference of row
+// interpolations (gy).  Each lane rounds as the scalar operations would.
 template <typename T, int SP>
 __device__ __forceinline__ Sample2 bilin_staged2(const T *__restrict__ rm1, const T *__restrict__ rm2, float2 f_x,
                                                  float2 f_y)
