@@ -144,6 +144,15 @@ def test_null_arguments_of_the_later_entry_points_are_rejected():
     assert lib.ofv_vorticity(0, 8, 1, dummy, dummy, 64, dummy, None) == ofv.OFV_ERR_SHAPE
     assert lib.ofv_vorticity(8, 8, 1, dummy, dummy, 63, dummy, None) == ofv.OFV_ERR_INVALID_ARG
     assert lib.ofv_recirculation_area(8, 8, 0, dummy, 64, None, dummy, None) == ofv.OFV_ERR_SHAPE
+    lib.ofv_probe.argtypes = [I, I, I, P, P, Z, I, P, P, P]
+    lib.ofv_probe.restype = I
+    assert lib.ofv_probe(8, 8, 1, None, dummy, 64, 4, dummy, dummy, None) == ofv.OFV_ERR_INVALID_ARG
+    assert lib.ofv_probe(8, 8, 1, dummy, dummy, 64, 0, dummy, dummy, None) == ofv.OFV_ERR_SHAPE
+    assert lib.ofv_probe(8, 8, 1, dummy, dummy, 63, 4, dummy, dummy, None) == ofv.OFV_ERR_INVALID_ARG
+    assert lib.ofv_probe(8, 8, 1, dummy, dummy, 64, 4, ctypes.c_void_p(20), dummy, None) == ofv.OFV_ERR_INVALID_ARG
+    lib.ofv_set_mask.argtypes = [P, P, P]
+    lib.ofv_set_mask.restype = I
+    assert lib.ofv_set_mask(None, dummy, None) == ofv.OFV_ERR_INVALID_ARG
 
 
 def test_status_strings():
