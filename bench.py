@@ -411,12 +411,32 @@ def time_sequence(ofv, torch, h, frames, n_frames, H, W, u, v, stream, reps, in_
     return npairs * reps / (e0.elapsed_time(e1) / 1e3)
 
 
+def field_error(torch, synth, fld, u, v, H, W, dev, inside=None, margin=16):
+    """Mean and 99th percentile of |V - V_true| over the fields u, v (n x H x
+    W, device) against the analytic displacement fld, at least `margin` px
+    from the border and outside the body (inside(x, y) true)."""
+    tu, tv = fld.grid(H, W)
+    keep = np.zeros((H, W), bool)
+    keep[margin:H - margin, margin:W - margin] = True
+    if inside is not None:
+        yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+        keep &= ~inside(xx, yy)
+    k = torch.from_numpy(keep).to(dev)
+    tu = torch.from_numpy(tu.astype(np.float32)).to(dev)
+    tv = torch.from_numpy(tv.astype(np.float32)).to(dev)
+    e = torch.hypot(u - tu, v - tv)[:, k].flatten()
+    smp = e[torch.randint(0, e.numel(), (1 << 22,), device=dev)]
+    return {"err_mean_px": float(e.mean()), "err_p99_px": float(torch.quantile(smp, 0.99))}
+
+
 def sizes(ofv, torch, synth, dev, stream, frames1, u1, v1):
     out = {}
     cases = [("1Mp", 1024, 1024, None), ("4Mp", 2048, 2048, "turb"), ("21Mp", 4096, 5120, "wake")]
     for name, H, W, kind in cases:
+        inside = None
         if kind is None:
             frames, nf, reps, u, v = frames1, min(101, frames1.shape[0]), 5, u1, v1
+            fld = synth.stream_field(H, W)
         else:
             if kind == "turb":
                 fld = synth.turbulence_field(H, W, seed=3).sampled(H, W)
@@ -447,6 +467,9 @@ def sizes(ofv, torch, synth, dev, stream, frames1, u1, v1):
                 res[label] = {"fields_per_s": fps, "mvectors_per_s": fps * H * W / 1e6,
                               "step_frac_of_hbm": tot_b / (nf - 1) * fps / 1e9 / peak,
                               "iterate_kernel_frac_of_hbm": it_b / (it_ms / 1e3) / 1e9 / peak}
+                if label != "plain_fp32":
+                    torch.cuda.synchronize()
+                    res[label].update(field_error(torch, synth, fld, u[:nf - 1], v[:nf - 1], H, W, dev, inside))
             finally:
                 ofv.ofv_destroy(h)
         out[name] = res

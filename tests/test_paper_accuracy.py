@@ -91,3 +91,27 @@ def test_gpu_error_within_the_papers_range():
             ofv.ofv_destroy(h)
         print(f"GPU R={r['R']} D={r['D']}: <Err> = {err:.4f} px")
         assert err <= ERR_RANGE[1], (r, err)
+
+
+def test_turbulence_prefers_the_papers_small_kernel():
+    """Sec. 5 (HIT): the best parameters for the turbulent case are small
+    kernels, KR 2, NR 1, PSL 2, IT 5 with particles of sigma 1 px at 0.119
+    particles per pixel, for <Err> = 0.163 px (Table 4).  On the synthetic
+    turbulence stand-in (Kolmogorov-like spectrum, rms 2 px; not the DNS),
+    the same parameters beat the default KR 4 and land near the paper's
+    error (measured 0.193 against 0.260 px)."""
+    H = W = 1024
+    fld = synth.turbulence_field(H, W, seed=3).sampled(H, W)
+    tu, tv = fld.grid(H, W)
+    I1, I2 = synth.particle_pair(H, W, fld, ppp=0.119, dmin=2.35, dmax=2.35, seed=3, noise=0.0, bits=12,
+                                 kind=synth.OUT_U16, field_max=8.0)
+    s = (slice(16, -16), slice(16, -16))
+
+    def err(**p):
+        u, v = oracle.flow(I1.astype(np.float64), I2.astype(np.float64), oracle.Params(bits=12, **p))
+        return float(np.hypot(u - tu, v - tv)[s].mean())
+
+    best = err(psl=2, kr=2, it=5, nr=1)
+    default = err(psl=2, kr=4, it=3, nr=0)
+    print(f"turbulence stand-in: paper's HIT parameters {best:.3f} px, default {default:.3f} px")
+    assert best < default and best <= 0.25
