@@ -29,8 +29,9 @@
  *     enqueued.  An asynchronous device error is reported as OFV_ERR_CUDA by
  *     the call that observes it.  ofv_last_error() describes the most recent
  *     failure in the calling thread.
- *   - A handle is not thread-safe.  Distinct handles on distinct streams are
- *     independent.
+ *   - A handle is not thread-safe, and work of one handle on different
+ *     streams must not overlap (the workspace is shared): order it, or use
+ *     one stream.  Distinct handles on distinct streams are independent.
  *   - The fused kernels stage image tiles with TMA copies and wait for them
  *     with a bound (2 s).  If a wait ever expires the kernel records it in a
  *     handle-owned word of page-locked host memory, and every later compute,
@@ -314,9 +315,11 @@ ofv_status ofv_queue_selftest(int timeout_us, int *error_word);
  * whole launch sequence of ofv_compute(h, I1, I2, u, v) for those fixed
  * buffers into a CUDA graph (after one eager run that prepares the kernels),
  * so each new pair costs one ofv_graph_launch instead of ~PSL + L*IT + 1
- * launches.  The graph uses the handle's workspace: the handle must outlive
- * it, and launches of graphs and compute calls of one handle must be
- * ordered (one stream).  Kernel timing is not recorded inside graphs. */
+ * launches.  ofv_graph_create synchronises the device first (the eager run
+ * uses the handle's workspace on a stream of its own).  The graph uses the
+ * handle's workspace: the handle must outlive it, and launches of graphs and
+ * compute calls of one handle must be ordered (one stream).  Kernel timing
+ * is not recorded inside graphs. */
 typedef struct ofv_graph ofv_graph;
 ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float *u, float *v, ofv_graph **out);
 ofv_status ofv_graph_launch(ofv_graph *g, ofv_stream_t s);

@@ -968,8 +968,12 @@ ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float
         return fail(OFV_ERR_INVALID_ARG, "handle, I1, I2, u, v must be non-NULL and u != v");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    // the eager run below uses the handle's workspace and claim counters on
+    // a stream of its own: earlier work on the handle must be finished
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for earlier work before recording");
     cudaStream_t cs = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "creating the capture stream");
     const bool prof = h->prof;
     h->prof = false;
