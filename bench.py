@@ -729,7 +729,8 @@ def batched_uneven(ofv, torch, synth, dev, stream, n_pairs=64, reps=5):
     return {"pairs": n_pairs, "mpix_per_batch": mpix, "batched_fields_per_s": batched,
             "batched_mvectors_per_s": batched * mpix / n_pairs, "sequential_fields_per_s": sequential,
             "backward_pairs_per_s": backward, "backward_mvectors_per_s": backward * mpix / n_pairs,
-            "tuning": tune, "timing": "host wall clock over 5 batches (the batched call synchronises)"}
+            "tuning": tune, "timing": "host wall clock over 5 batches, synchronised at the end (batched calls "
+                                      "after the tuning one are asynchronous)"}
 
 
 def cpu_baseline(frames_h):

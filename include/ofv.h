@@ -291,11 +291,17 @@ typedef struct {
  * (sorted sizes and parameters) runs the autotuner: each candidate schedule
  * (all pairs stage by stage, or groups of 8 pairs) and persistent grid (one
  * or two CTAs per SM) is timed on the batch itself and the fastest is kept
- * for later batches of that signature.  The call returns when the batch is
- * complete (it synchronises s).  A workspace for the batch is allocated on
- * first use and grown when a larger batch arrives.  Needs the fused path with
- * KR <= 10 (else OFV_ERR_UNSUPPORTED).  OFV_ERR_TIMEOUT if a dependency wait
- * expired (5 s). */
+ * for later batches of that signature (that first call waits for its
+ * timings).  Otherwise the call enqueues the batch on s and returns; the
+ * fields are valid once s reaches them, and the next call's host work
+ * overlaps this batch.  The schedule and the tensor maps of a layout are
+ * uploaded once and reused.  A workspace for the batch is allocated on first
+ * use and grown when a larger batch arrives (growing waits for s).  Needs the
+ * fused path with KR <= 10 (else OFV_ERR_UNSUPPORTED).  A dependency wait
+ * that expires (5 s) is recorded in a handle-owned word of page-locked host
+ * memory: the first batched call that observes it, and every later one,
+ * returns OFV_ERR_TIMEOUT without enqueuing work (the tuning call observes
+ * its own). */
 ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t s);
 
 /* Configuration used by the last ofv_compute_batched call: schedule (0 =

@@ -727,6 +727,7 @@ struct QueueParams {
     int spin_limit;
     const CUtensorMap *tmaps;  // [pair][16 levels][2 frames] for TMA staging, or null
     int *tma_err;              // set to 1 when a TMA wait expires, or null
+    int *host_err;             // mapped host word: 1 + the unit whose wait expired, or null
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -778,6 +779,7 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_it
             while (ld_acquire(cnt) < need) {
                 if (++spins > q.spin_limit || global_ns() - t0 > q.timeout_ns) {
                     atomicCAS(q.error, 0, 1 + unit);
+                    if (q.host_err) *reinterpret_cast<volatile int *>(q.host_err) = 1 + unit;
                     s_fail = 1;
                     break;
                 }

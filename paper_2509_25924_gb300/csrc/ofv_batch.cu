@@ -134,6 +134,18 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     }
     if (tma_expired(h))
         return fail_msg(OFV_ERR_TIMEOUT, "ofv_compute_batched: a TMA copy of an earlier launch did not complete");
+    if (!h->qerr_h) {
+        if (cudaHostAlloc(reinterpret_cast<void **>(&h->qerr_h), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->qerr_d), h->qerr_h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (h->qerr_h) cudaFreeHost(h->qerr_h);
+            h->qerr_h = h->qerr_d = nullptr;
+            return fail_msg(OFV_ERR_ALLOC, "ofv_compute_batched: page-locked error word");
+        }
+        *h->qerr_h = 0;
+    }
+    if (const int u = *static_cast<volatile int *>(h->qerr_h))
+        return fail_msg(OFV_ERR_TIMEOUT, "ofv_compute_batched: a dependency wait of work unit %d expired", u - 1);
 
     // workspace: per pair two pyramids and two fields, then the queue data
     std::vector<size_t> lvl_off(2 * (size_t)n * L), vb_off(2 * (size_t)n), tmp_off(2 * (size_t)n, 0);
@@ -174,6 +186,8 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
             h->batch_arena = nullptr;
             h->batch_bytes = 0;
         }
+        h->batch_sched_key.clear();  // nothing uploaded lives in the new arena
+        h->batch_maps_key.clear();
         e = cudaMalloc(&h->batch_arena, off);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -263,14 +277,17 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     e = cudaMemcpyAsync(base + pairs_off, bp.data(), sizeof(BatchPair) * n, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading pair descriptors");
 
-    // TMA tensor maps of every pair's level images (encoded once per layout:
-    // the arena, the pair sizes in order and the parameters fix the
-    // addresses); levels smaller than the staged box never use theirs
+    // layout of the arena: its address, the pair sizes in order and the
+    // parameters fix every address in it
+    std::string mkey = std::to_string(reinterpret_cast<uintptr_t>(base)) + "/" + std::to_string(p.storage) + "/" +
+                       std::to_string(KR) + "/" + std::to_string(L) + "/" + std::to_string(IT);
+    for (int i = 0; i < n; ++i) mkey += "/" + std::to_string(Hs[i][0]) + "x" + std::to_string(Ws[i][0]);
+
+    // TMA tensor maps of every pair's level images (encoded once per layout
+    // and uploaded when the layout changes); levels smaller than the staged
+    // box never use theirs
     bool use_tma = h->tma_err_d != nullptr;
     if (use_tma) {
-        std::string mkey = std::to_string(reinterpret_cast<uintptr_t>(base)) + "/" + std::to_string(p.storage) + "/" +
-                           std::to_string(KR) + "/" + std::to_string(L);
-        for (int i = 0; i < n; ++i) mkey += "/" + std::to_string(Hs[i][0]) + "x" + std::to_string(Ws[i][0]);
         auto mit = h->batch_maps.find(mkey);
         if (mit == h->batch_maps.end()) {
             std::vector<CUtensorMap> maps(32 * (size_t)n);
@@ -285,10 +302,11 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
                 mit = h->batch_maps.emplace(mkey, std::move(maps)).first;
             }
         }
-        if (use_tma) {
+        if (use_tma && h->batch_maps_key != mkey) {
             e = cudaMemcpyAsync(base + tmaps_off, mit->second.data(), sizeof(CUtensorMap) * mit->second.size(),
                                 cudaMemcpyHostToDevice, cs);
             if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading tensor maps");
+            h->batch_maps_key = mkey;
         }
     }
 
@@ -340,6 +358,7 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     q.spin_limit = kWaitSpinLimit;
     q.tmaps = use_tma ? reinterpret_cast<const CUtensorMap *>(base + tmaps_off) : nullptr;
     q.tma_err = h->tma_err_d;
+    q.host_err = h->qerr_d;
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tuning) {
@@ -353,9 +372,15 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
         build_schedule(cands[c].schedule, S, n, tiles, group, goff);
         q.ngroups = (int)group.size();
         q.total_units = goff.back();
-        e = cudaMemcpyAsync(base + goff_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(base + grp_off, group.data(), sizeof(int2) * group.size(), cudaMemcpyHostToDevice, cs);
+        const std::string skey = mkey + "#" + std::to_string(cands[c].schedule);
+        e = cudaSuccess;
+        if (h->batch_sched_key != skey) {  // the schedule of this layout is not in the arena yet
+            e = cudaMemcpyAsync(base + goff_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(base + grp_off, group.data(), sizeof(int2) * group.size(), cudaMemcpyHostToDevice,
+                                    cs);
+            h->batch_sched_key = e == cudaSuccess ? skey : std::string();
+        }
         if (e == cudaSuccess) e = cudaMemsetAsync(q.done, 0, sizeof(int) * (maxgroups + 2), cs);
         if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading the schedule");
         const int ctas = std::min(sms * cands[c].ctas_per_sm, std::max(1, q.total_units));
@@ -364,18 +389,16 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
         if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: persistent launch");
         if (tuning) {
             cudaEventRecord(e1, cs);
-            cudaEventSynchronize(e1);
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: timing a candidate");
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             cands[c].ms = ms;
             if (ms < cands[best].ms) best = (int)c;
+            if (const int u = *static_cast<volatile int *>(h->qerr_h))
+                return fail_msg(OFV_ERR_TIMEOUT, "ofv_compute_batched: a dependency wait of work unit %d expired",
+                                u - 1);
         }
-        int err = 0;
-        e = cudaMemcpyAsync(&err, q.error, sizeof(int), cudaMemcpyDeviceToHost, cs);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: completing the batch");
-        if (err != 0)
-            return fail_msg(OFV_ERR_TIMEOUT, "ofv_compute_batched: a dependency wait of work unit %d expired", err - 1);
     }
     if (tuning) {
         cudaEventDestroy(e0);

@@ -678,6 +678,7 @@ ofv_status ofv_destroy(ofv_handle *h)
         cudaStreamDestroy(h->hs_stream[1]);
     }
     if (h->mask_arena) cudaFree(h->mask_arena);
+    if (h->qerr_h) cudaFreeHost(h->qerr_h);
     if (h->arena) cudaFree(h->arena);
     delete h;
     return st;

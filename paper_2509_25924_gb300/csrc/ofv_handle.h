@@ -101,6 +101,11 @@ struct ofv_handle {
     uint8_t *mask_lvl[ofv::kMaxLevels];
     void *mask_arena;
     int mask_on;
+    // batched entry point: word a persistent launch sets when a dependency
+    // wait expires (page-locked, mapped), and the layouts whose schedule and
+    // tensor maps are in the batch arena
+    int *qerr_h, *qerr_d;
+    std::string batch_sched_key, batch_maps_key;
 };
 
 namespace ofv {
