@@ -311,8 +311,9 @@ ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm
 
 /* Test hook for the bounded waits of the persistent launch: runs one CTA
  * whose work unit depends on a counter nothing increments.  Expected result:
- * OFV_ERR_TIMEOUT after about timeout_us, *error_word = 1, the device still
- * usable. */
+ * OFV_ERR_TIMEOUT after about timeout_us, *error_word = 1 (the device word),
+ * the same value in the mapped host word that asynchronous batches report
+ * through (OFV_ERR_CUDA if it differs), the device still usable. */
 ofv_status ofv_queue_selftest(int timeout_us, int *error_word);
 
 /* ---- CUDA-graph replay (live loop) -------------------------------------

@@ -459,12 +459,24 @@ ofv_status ofv_queue_selftest(int timeout_us, int *error_word)
     q.error = q.done + 5;
     q.timeout_ns = (long long)timeout_us * 1000;
     q.spin_limit = kWaitSpinLimit;
-    if (e == cudaSuccess) e = launch_queue(OFV_STORE_F32, q, 4, 1, nullptr);
+    // the mapped host word through which asynchronous batches report
+    int *hw = nullptr, *hw_d = nullptr;
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&hw), sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&hw_d), hw, 0);
+    if (e == cudaSuccess) {
+        *hw = 0;
+        q.host_err = hw_d;
+        e = launch_queue(OFV_STORE_F32, q, 4, 1, nullptr);
+    }
     int err = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&err, q.error, sizeof(int), cudaMemcpyDeviceToHost);
+    const int host_word = hw ? *static_cast<volatile int *>(hw) : 0;
+    if (hw) cudaFreeHost(hw);
     cudaFree(mem);
     if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_queue_selftest");
     *error_word = err;
+    if (host_word != err)
+        return fail_msg(OFV_ERR_CUDA, "ofv_queue_selftest: host word %d, device word %d", host_word, err);
     return err ? fail_msg(OFV_ERR_TIMEOUT, "ofv_queue_selftest: wait expired as intended (unit %d)", err - 1)
                : OFV_OK;
 }
