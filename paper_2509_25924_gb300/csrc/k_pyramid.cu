@@ -4,6 +4,8 @@
 // Sec. 2 of the paper: step 1 is a local, pixel-centred intensity
 // normalization of radius NR; step 2 builds a Gaussian pyramid in which each
 // sub-level halves both image dimensions (Burt & Adelson's reduction).
+#include <algorithm>
+
 #include "ofv_common.cuh"
 
 namespace ofv {
@@ -14,16 +16,27 @@ template <> __device__ __forceinline__ float ld_in<uint8_t>(const uint8_t *p) { 
 template <> __device__ __forceinline__ float ld_in<uint16_t>(const uint16_t *p) { return (float)__ldg(p); }
 template <> __device__ __forceinline__ float ld_in<float>(const float *p) { return __ldg(p); }
 
-struct IngestPair { IngestArgs f[kMaxFramesPerLaunch]; float scale; };
+// The frames of one launch: a few passed by value, or any number in device
+// memory (the batched entry point); blockIdx.z selects the frame.
+struct IngestPair {
+    IngestArgs f[kMaxFramesPerLaunch];
+    float scale;
+    __device__ __forceinline__ const IngestArgs &get(int k) const { return f[k]; }
+};
+struct IngestList {
+    const IngestArgs *f;
+    float scale;
+    __device__ __forceinline__ const IngestArgs &get(int k) const { return f[k]; }
+};
 
 // Scaled intensity I = raw * scale (scale = 1/(2^bits - 1), or 1 for FP32
 // input), then, for NR > 0, (I - mu) / sqrt(var + eps_n^2) with mu and var
 // taken over the in-image part of the (2NR+1)^2 box.  Writes level 0 in the
 // storage type, or FP32 scratch when a pre-filter follows.
-template <typename TI, typename TS>
-__global__ void __launch_bounds__(256) k_ingest(IngestPair p)
+template <typename TI, typename TS, typename FR>
+__global__ void __launch_bounds__(256) k_ingest(const __grid_constant__ FR p)
 {
-    const IngestArgs &a = p.f[blockIdx.z];
+    const IngestArgs &a = p.get(blockIdx.z);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= a.H || j >= a.W) return;
@@ -98,10 +111,10 @@ __device__ __forceinline__ void store8(__nv_bfloat16 *d, const float f[8])
     *reinterpret_cast<uint4 *>(d) = *reinterpret_cast<const uint4 *>(h);
 }
 
-template <typename TI, typename TS>
-__global__ void __launch_bounds__(256) k_ingest8(const __grid_constant__ IngestPair p)
+template <typename TI, typename TS, typename FR>
+__global__ void __launch_bounds__(256) k_ingest8(const __grid_constant__ FR p)
 {
-    const IngestArgs &a = p.f[blockIdx.z];
+    const IngestArgs &a = p.get(blockIdx.z);
     const int W8 = a.W >> 3;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)W8 * a.H) return;
@@ -120,10 +133,10 @@ __global__ void __launch_bounds__(256) k_ingest8(const __grid_constant__ IngestP
 }
 
 // 5x5 correlation with clamp-to-edge: out(i,j) = sum w[a][b] I(i+a-2, j+b-2).
-template <typename TS>
-__global__ void __launch_bounds__(256) k_prefilter(IngestPair p)
+template <typename TS, typename FR>
+__global__ void __launch_bounds__(256) k_prefilter(const __grid_constant__ FR p)
 {
-    const IngestArgs &a = p.f[blockIdx.z];
+    const IngestArgs &a = p.get(blockIdx.z);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= a.H || j >= a.W) return;
@@ -137,30 +150,39 @@ __global__ void __launch_bounds__(256) k_prefilter(IngestPair p)
     st_store(static_cast<TS *>(a.out) + (int64_t)i * a.pitch + j, s);
 }
 
-template <typename TS>
-static cudaError_t ingest_t(const IngestPair &p, int nframes, cudaStream_t s)
+// f: the frames on the host (sizes, types and alignment decide the form and
+// the grid, which covers the largest frame); p: the same frames as the
+// kernels read them.
+template <typename TS, typename FR>
+static cudaError_t ingest_t(const FR &p, const IngestArgs *f, int nframes, cudaStream_t s)
 {
-    const IngestArgs &a = p.f[0];
-    bool vec = a.nr == 0 && !a.prefilter && a.W % 8 == 0;
-    for (int k = 0; k < nframes && vec; ++k) vec = (reinterpret_cast<uintptr_t>(p.f[k].raw) & 15u) == 0;
+    const IngestArgs &a = f[0];
+    bool vec = a.nr == 0 && !a.prefilter;
+    int64_t n8 = 0;
+    int H = 0, W = 0;
+    for (int k = 0; k < nframes; ++k) {
+        vec = vec && f[k].W % 8 == 0 && (reinterpret_cast<uintptr_t>(f[k].raw) & 15u) == 0;
+        n8 = std::max<int64_t>(n8, (int64_t)(f[k].W / 8) * f[k].H);
+        H = std::max(H, f[k].H);
+        W = std::max(W, f[k].W);
+    }
     if (vec) {
-        const int64_t n = (int64_t)(a.W / 8) * a.H;
-        dim3 grd((unsigned)((n + 255) / 256), 1, nframes);
+        dim3 grd((unsigned)((n8 + 255) / 256), 1, nframes);
         switch (a.in_type) {
-        case IN_U8: k_ingest8<uint8_t, TS><<<grd, 256, 0, s>>>(p); break;
-        case IN_U16: k_ingest8<uint16_t, TS><<<grd, 256, 0, s>>>(p); break;
-        default: k_ingest8<float, TS><<<grd, 256, 0, s>>>(p); break;
+        case IN_U8: k_ingest8<uint8_t, TS, FR><<<grd, 256, 0, s>>>(p); break;
+        case IN_U16: k_ingest8<uint16_t, TS, FR><<<grd, 256, 0, s>>>(p); break;
+        default: k_ingest8<float, TS, FR><<<grd, 256, 0, s>>>(p); break;
         }
         return cudaGetLastError();
     }
     dim3 blk(32, 8);
-    dim3 grd((a.W + 31) / 32, (a.H + 7) / 8, nframes);
+    dim3 grd((W + 31) / 32, (H + 7) / 8, nframes);
     switch (a.in_type) {
-    case IN_U8: k_ingest<uint8_t, TS><<<grd, blk, 0, s>>>(p); break;
-    case IN_U16: k_ingest<uint16_t, TS><<<grd, blk, 0, s>>>(p); break;
-    default: k_ingest<float, TS><<<grd, blk, 0, s>>>(p); break;
+    case IN_U8: k_ingest<uint8_t, TS, FR><<<grd, blk, 0, s>>>(p); break;
+    case IN_U16: k_ingest<uint16_t, TS, FR><<<grd, blk, 0, s>>>(p); break;
+    default: k_ingest<float, TS, FR><<<grd, blk, 0, s>>>(p); break;
     }
-    if (a.prefilter) k_prefilter<TS><<<grd, blk, 0, s>>>(p);
+    if (a.prefilter) k_prefilter<TS, FR><<<grd, blk, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -173,9 +195,22 @@ cudaError_t launch_ingest_frames(const IngestArgs *f, int nframes, int store, cu
     for (int k = 0; k < nframes; ++k) p.f[k] = f[k];
     p.scale = f[0].in_type == IN_F32 ? 1.0f : 1.0f / (float)((1u << f[0].bits) - 1u);
     switch (store) {
-    case ST_F16: return ingest_t<__half>(p, nframes, s);
-    case ST_BF16: return ingest_t<__nv_bfloat16>(p, nframes, s);
-    default: return ingest_t<float>(p, nframes, s);
+    case ST_F16: return ingest_t<__half>(p, f, nframes, s);
+    case ST_BF16: return ingest_t<__nv_bfloat16>(p, f, nframes, s);
+    default: return ingest_t<float>(p, f, nframes, s);
+    }
+}
+
+// Any number of frames (of any sizes) in one launch: f on the host, dev_f
+// the same descriptors in device memory (kept until the launch has run).
+cudaError_t launch_ingest_list(const IngestArgs *f, const IngestArgs *dev_f, int nframes, int store, cudaStream_t s)
+{
+    if (nframes < 1 || nframes > 65535) return cudaErrorInvalidValue;
+    IngestList p{dev_f, f[0].in_type == IN_F32 ? 1.0f : 1.0f / (float)((1u << f[0].bits) - 1u)};
+    switch (store) {
+    case ST_F16: return ingest_t<__half>(p, f, nframes, s);
+    case ST_BF16: return ingest_t<__nv_bfloat16>(p, f, nframes, s);
+    default: return ingest_t<float>(p, f, nframes, s);
     }
 }
 
@@ -183,7 +218,14 @@ cudaError_t launch_ingest_frames(const IngestArgs *f, int nframes, int store, cu
 // Pyramid reduction: out(i,j) = sum_{a,b=-2..2} c_a c_b P(2i+a, 2j+b),
 // c = [1 4 6 4 1]/16, clamp-to-edge, out size ceil(H/2) x ceil(W/2).
 // ---------------------------------------------------------------------------
-struct ReducePair { ReduceArgs f[kMaxFramesPerLaunch]; };
+struct ReducePair {
+    ReduceArgs f[kMaxFramesPerLaunch];
+    __device__ __forceinline__ const ReduceArgs &get(int k) const { return f[k]; }
+};
+struct ReduceList {
+    const ReduceArgs *f;
+    __device__ __forceinline__ const ReduceArgs &get(int k) const { return f[k]; }
+};
 
 // Two horizontally adjacent outputs j = 2t, 2t+1 per thread: they share
 // input columns 4t-2 .. 4t+4 (7 loads per row instead of 10), loaded as
@@ -210,10 +252,10 @@ __device__ __forceinline__ void load7<float>(const float *row, int c0, int Ws, b
     for (int k = 0; k < 7; ++k) v[k] = __ldg(row + clampi(c0 + k, 0, Ws - 1));
 }
 
-template <typename TS>
-__global__ void __launch_bounds__(256) k_reduce(ReducePair p)
+template <typename TS, typename FR>
+__global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ FR p)
 {
-    const ReduceArgs &a = p.f[blockIdx.z];
+    const ReduceArgs &a = p.get(blockIdx.z);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     const int j0 = 2 * t;
@@ -242,20 +284,39 @@ __global__ void __launch_bounds__(256) k_reduce(ReducePair p)
     if (j0 + 1 < a.Wd) st_store(dst + j0 + 1, acc1);
 }
 
+// The grid covers the largest output of the frames (each exits outside its own).
+template <typename FR>
+static cudaError_t reduce_t(const FR &p, const ReduceArgs *f, int nframes, int store, cudaStream_t s)
+{
+    int Hd = 0, Wd = 0;
+    for (int k = 0; k < nframes; ++k) {
+        Hd = std::max(Hd, f[k].Hd);
+        Wd = std::max(Wd, f[k].Wd);
+    }
+    dim3 blk(32, 8);
+    dim3 grd(((Wd + 1) / 2 + 31) / 32, (Hd + 7) / 8, nframes);
+    switch (store) {
+    case ST_F16: k_reduce<__half, FR><<<grd, blk, 0, s>>>(p); break;
+    case ST_BF16: k_reduce<__nv_bfloat16, FR><<<grd, blk, 0, s>>>(p); break;
+    default: k_reduce<float, FR><<<grd, blk, 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
 // Reduce one level of nframes (1 .. kMaxFramesPerLaunch) frames in one launch.
 cudaError_t launch_reduce_frames(const ReduceArgs *f, int nframes, int store, cudaStream_t s)
 {
     if (nframes < 1 || nframes > kMaxFramesPerLaunch) return cudaErrorInvalidValue;
     ReducePair p;
     for (int k = 0; k < nframes; ++k) p.f[k] = f[k];
-    dim3 blk(32, 8);
-    dim3 grd(((f[0].Wd + 1) / 2 + 31) / 32, (f[0].Hd + 7) / 8, nframes);
-    switch (store) {
-    case ST_F16: k_reduce<__half><<<grd, blk, 0, s>>>(p); break;
-    case ST_BF16: k_reduce<__nv_bfloat16><<<grd, blk, 0, s>>>(p); break;
-    default: k_reduce<float><<<grd, blk, 0, s>>>(p); break;
-    }
-    return cudaGetLastError();
+    return reduce_t(p, f, nframes, store, s);
+}
+
+// Any number of frames (of any sizes) in one launch (see launch_ingest_list).
+cudaError_t launch_reduce_list(const ReduceArgs *f, const ReduceArgs *dev_f, int nframes, int store, cudaStream_t s)
+{
+    if (nframes < 1 || nframes > 65535) return cudaErrorInvalidValue;
+    return reduce_t(ReduceList{dev_f}, f, nframes, store, s);
 }
 
 // Dense FP32 copy of a stored level (inspection).

@@ -179,6 +179,10 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     off = align_up(off + sizeof(int2) * maxgroups, 256);
     const size_t done_off = off;
     off = align_up(off + sizeof(int) * (maxgroups + 2), 256);  // done counters, head, error
+    const size_t ing_off = off;  // ingest descriptors of the 2n frames, then the reduce ones per level
+    off = align_up(off + sizeof(IngestArgs) * 2 * (size_t)n, 256);
+    const size_t red_off = off;
+    off = align_up(off + sizeof(ReduceArgs) * 2 * (size_t)n * (L > 1 ? L - 1 : 1), 256);
     if (off > h->batch_bytes) {
         if (h->batch_arena) {
             e = cudaStreamSynchronize(cs);
@@ -199,27 +203,15 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     char *base = static_cast<char *>(h->batch_arena);
     auto lvl = [&](int i, int f, int l) { return (void *)(base + lvl_off[((size_t)i * 2 + f) * L + l]); };
 
-    // steps 1-2: ingest and reduce, frames of equal size together
-    std::vector<int> order(n);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) {
-        return Hs[a][0] != Hs[b][0] ? Hs[a][0] < Hs[b][0] : Ws[a][0] < Ws[b][0];
-    });
-    for (size_t k0 = 0; k0 < order.size();) {
-        size_t k1 = k0;
-        while (k1 < order.size() && Hs[order[k1]][0] == Hs[order[k0]][0] && Ws[order[k1]][0] == Ws[order[k0]][0]) ++k1;
-        // frames of this size class, kMaxFramesPerLaunch at a time
-        std::vector<std::pair<int, int>> fr;  // (pair, frame)
-        for (size_t k = k0; k < k1; ++k) {
-            fr.push_back({order[k], 0});
-            fr.push_back({order[k], 1});
-        }
-        for (size_t c0 = 0; c0 < fr.size(); c0 += kMaxFramesPerLaunch) {
-            const int nf = (int)std::min<size_t>(kMaxFramesPerLaunch, fr.size() - c0);
-            IngestArgs ia[kMaxFramesPerLaunch];
-            for (int k = 0; k < nf; ++k) {
-                const int i = fr[c0 + k].first, f = fr[c0 + k].second;
-                IngestArgs &a = ia[k];
+    // steps 1-2: ingest every frame of the batch in one launch, then reduce
+    // each level of every frame in one launch (descriptors in the arena)
+    {
+        std::vector<IngestArgs> ia(2 * (size_t)n);
+        std::vector<ReduceArgs> ra(2 * (size_t)n * (L > 1 ? L - 1 : 1));
+        for (int i = 0; i < n; ++i)
+            for (int f = 0; f < 2; ++f) {
+                IngestArgs &a = ia[2 * i + f];
+                memset(&a, 0, sizeof a);
                 a.raw = f ? pairs[i].I2 : pairs[i].I1;
                 a.out = lvl(i, f, 0);
                 a.tmp = p.prefilter ? reinterpret_cast<float *>(base + tmp_off[2 * i + f]) : nullptr;
@@ -232,14 +224,8 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
                 a.nr = p.norm_radius;
                 a.eps_n = p.norm_eps;
                 a.prefilter = p.prefilter;
-            }
-            e = launch_ingest_frames(ia, nf, p.storage, cs);
-            if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: ingest launch");
-            for (int l = 1; l < L; ++l) {
-                ReduceArgs ra[kMaxFramesPerLaunch];
-                for (int k = 0; k < nf; ++k) {
-                    const int i = fr[c0 + k].first, f = fr[c0 + k].second;
-                    ReduceArgs &r = ra[k];
+                for (int l = 1; l < L; ++l) {
+                    ReduceArgs &r = ra[(size_t)(l - 1) * 2 * n + 2 * i + f];
                     r.src = lvl(i, f, l - 1);
                     r.Hs = Hs[i][l - 1];
                     r.Ws = Ws[i][l - 1];
@@ -249,11 +235,20 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
                     r.Wd = Ws[i][l];
                     r.dpitch = pitch_for(Ws[i][l]);
                 }
-                e = launch_reduce_frames(ra, nf, p.storage, cs);
-                if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: reduce launch");
             }
+        const IngestArgs *ia_d = reinterpret_cast<const IngestArgs *>(base + ing_off);
+        const ReduceArgs *ra_d = reinterpret_cast<const ReduceArgs *>(base + red_off);
+        e = cudaMemcpyAsync(base + ing_off, ia.data(), sizeof(IngestArgs) * ia.size(), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess && L > 1)
+            e = cudaMemcpyAsync(base + red_off, ra.data(), sizeof(ReduceArgs) * ra.size(), cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading frame descriptors");
+        e = launch_ingest_list(ia.data(), ia_d, 2 * n, p.storage, cs);
+        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: ingest launch");
+        for (int l = 1; l < L; ++l) {
+            const size_t o = (size_t)(l - 1) * 2 * n;
+            e = launch_reduce_list(ra.data() + o, ra_d + o, 2 * n, p.storage, cs);
+            if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: reduce launch");
         }
-        k0 = k1;
     }
 
     // pair descriptors

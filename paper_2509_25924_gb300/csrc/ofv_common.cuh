@@ -118,6 +118,11 @@ struct ReduceArgs {
 // Reduce one level of nframes (1 or 2) frames in one launch.
 cudaError_t launch_reduce_frames(const ReduceArgs *f, int nframes, int store, cudaStream_t s);
 
+// Any number of frames of any sizes in one launch: f on the host, dev_f the
+// same descriptors in device memory, valid until the launch has run.
+cudaError_t launch_ingest_list(const IngestArgs *f, const IngestArgs *dev_f, int nframes, int store, cudaStream_t s);
+cudaError_t launch_reduce_list(const ReduceArgs *f, const ReduceArgs *dev_f, int nframes, int store, cudaStream_t s);
+
 // Warm start: the starting field of the coarsest level from a level-0
 // field, out(i, j) = (u, v)(2^level i, 2^level j) / 2^level (pitch vpitch).
 struct SeedArgs {
