@@ -352,16 +352,25 @@ def e2e(args, ofv, torch, h, frames_h, dev, stream, barrier, max_over_ranks, ws)
     run()
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 5))
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     barrier()
     t0 = time.perf_counter()
+    c0 = time.process_time()
+    step_ms = []
     for _ in range(steps):
+        ts = time.perf_counter()
         run()
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        step_ms.append(1e3 * (time.perf_counter() - ts))
     dt = max_over_ranks(time.perf_counter() - t0)
+    cpu_s = time.process_time() - c0
+    clocks = sampler.stop()
     value = ws * npairs * steps / dt
     out = {"value": value, "unit": "fields/s", "h2d_bytes_per_step": (npairs + 1) * N * 2,
            "d2h_bytes_per_step": npairs * N * 8, "pairs_per_step": npairs, "steps": steps,
-           "api": "ofv_compute_sequence_host (host wall clock incl. H2D of every frame and D2H of every field)"}
+           "api": "ofv_compute_sequence_host (host wall clock incl. H2D of every frame and D2H of every field)",
+           "step_ms": step_ms, "host_cpu_s": cpu_s, "wall_s": dt, "clocks": clocks}
     # context: one ofv_compute_host call per pair (both frames up, field down, one stream)
     hp = min(100, npairs)
     ring = 8
