@@ -349,7 +349,8 @@ def e2e(args, ofv, torch, h, frames_h, dev, stream, barrier, max_over_ranks, ws)
     def run():
         ofv.ofv_compute_sequence_host(h, npairs + 1, host_frames, N * 2, hu, hv, N, stream)
 
-    run()
+    for _ in range(max(args.warmup, 1)):  # the same W warm-up steps as the device-resident leg
+        run()
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 5))
     sampler = ClockSampler(torch.cuda.current_device())
