@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=FRAMES1, help="frames in the 1 Mp stream (pairs + 1)")
     ap.add_argument("--backward-only", action="store_true",
                     help="time only the reverse mode on 1 Mp pairs of the stream (one JSON line)")
+    ap.add_argument("--paper-only", action="store_true",
+                    help="time only the paper's benchmark parameters (u8, NR 2, KR 10, IT 3) at 1 Mp (one JSON line)")
     return ap.parse_args()
 
 
@@ -564,12 +566,12 @@ def variants(ofv, torch, synth, dev, stream, frames, u, v, n_frames=201, reps=5)
     return out
 
 
-def paper_perf_set(ofv, torch, synth, dev, stream):
+def paper_perf_set(ofv, torch, synth, dev, stream, cases=None):
     """The paper's own benchmark parameters (8-bit input, NR 2, KR 10, IT 3,
     PSL 0/1/2) on synthetic 8-bit particle streams at 1, 4 and 21 Mp, for
     context beside its published rates (other hardware)."""
     out = {}
-    for name, H, W, nf in (("1Mp", 1024, 1024, 41), ("4Mp", 2048, 2048, 17), ("21Mp", 4096, 5120, 9)):
+    for name, H, W, nf in cases or (("1Mp", 1024, 1024, 41), ("4Mp", 2048, 2048, 17), ("21Mp", 4096, 5120, 9)):
         fr = synth.stream_frames(H, W, nf, seed=7, ppp=0.05, bits=8).astype(np.uint8)
         frames = torch.from_numpy(fr).to(dev)
         u = torch.empty((nf - 1, H, W), dtype=torch.float32, device=dev)
@@ -812,6 +814,15 @@ def main():
         return
     if args.backward_only:
         run_backward_only(args)
+        return
+    if args.paper_only:
+        import torch
+        import paper_2509_25924_gb300 as ofv
+        import synth
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"paper_perf_set": paper_perf_set(ofv, torch, synth, dev, torch.cuda.current_stream(),
+                                                           cases=(("1Mp", 1024, 1024, 41),))}), flush=True)
         return
     run_ours(args, ws, rank, local)
 

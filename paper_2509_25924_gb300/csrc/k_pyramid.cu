@@ -66,6 +66,56 @@ __global__ void __launch_bounds__(256) k_ingest(const __grid_constant__ FR p)
         st_store(static_cast<TS *>(a.out) + (int64_t)i * a.pitch + j, val);
 }
 
+// The same with the (2NR+1)^2 boxes read from shared memory: a CTA of 32 x 8
+// threads stages its 32 x 8 pixels and the NR halo (scaled values, zero
+// outside the image) once, then every thread sums its in-image box from
+// shared memory in the order of k_ingest, so the result is the same.
+template <typename TI, typename TS, typename FR>
+__global__ void __launch_bounds__(256) k_ingest_norm(const __grid_constant__ FR p)
+{
+    extern __shared__ float tile[];  // (8 + 2 NR) rows of (32 + 2 NR)
+    const IngestArgs &a = p.get(blockIdx.z);
+    const int nr = a.nr;
+    const int TW = 32 + 2 * nr, TH = 8 + 2 * nr;
+    const int bx0 = blockIdx.x * 32, by0 = blockIdx.y * 8;
+    if (bx0 >= a.W || by0 >= a.H) return;  // the whole CTA lies outside this frame
+    const int x0 = bx0 - nr, y0 = by0 - nr;
+    const TI *raw = static_cast<const TI *>(a.raw);
+    const float sc = p.scale;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int t = tid; t < TW * TH; t += 256) {
+        const int r = t / TW, c = t - r * TW;
+        const int gy = y0 + r, gx = x0 + c;
+        tile[t] = (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) ? ld_in(raw + (int64_t)gy * a.W + gx) * sc : 0.f;
+    }
+    __syncthreads();
+    const int j = bx0 + threadIdx.x, i = by0 + threadIdx.y;
+    if (i >= a.H || j >= a.W) return;
+    const int i0 = max(i - nr, 0), i1 = min(i + nr, a.H - 1);
+    const int j0 = max(j - nr, 0), j1 = min(j + nr, a.W - 1);
+    const float inv_n = 1.0f / (float)((i1 - i0 + 1) * (j1 - j0 + 1));
+    float s = 0.f;
+    for (int ii = i0; ii <= i1; ++ii) {
+        const float *row = tile + (ii - y0) * TW;
+        for (int jj = j0; jj <= j1; ++jj) s += row[jj - x0];
+    }
+    const float mu = s * inv_n;
+    float q = 0.f;
+    for (int ii = i0; ii <= i1; ++ii) {
+        const float *row = tile + (ii - y0) * TW;
+        for (int jj = j0; jj <= j1; ++jj) {
+            const float d = row[jj - x0] - mu;
+            q = fmaf(d, d, q);
+        }
+    }
+    const float var = q * inv_n;
+    const float val = (tile[(i - y0) * TW + (j - x0)] - mu) * rsqrtf(var + a.eps_n * a.eps_n);
+    if (a.prefilter)
+        a.tmp[(int64_t)i * a.pitch + j] = val;
+    else
+        st_store(static_cast<TS *>(a.out) + (int64_t)i * a.pitch + j, val);
+}
+
 // Ingest without normalization or pre-filter (the common case): I = raw *
 // scale stored directly, eight pixels per thread with 16-byte stores (rows
 // of W % 8 == 0 pixels, 16-byte aligned input).
@@ -177,10 +227,19 @@ static cudaError_t ingest_t(const FR &p, const IngestArgs *f, int nframes, cudaS
     }
     dim3 blk(32, 8);
     dim3 grd((W + 31) / 32, (H + 7) / 8, nframes);
-    switch (a.in_type) {
-    case IN_U8: k_ingest<uint8_t, TS, FR><<<grd, blk, 0, s>>>(p); break;
-    case IN_U16: k_ingest<uint16_t, TS, FR><<<grd, blk, 0, s>>>(p); break;
-    default: k_ingest<float, TS, FR><<<grd, blk, 0, s>>>(p); break;
+    if (a.nr > 0 && a.nr <= 16) {
+        const size_t smem = sizeof(float) * (size_t)(32 + 2 * a.nr) * (8 + 2 * a.nr);
+        switch (a.in_type) {
+        case IN_U8: k_ingest_norm<uint8_t, TS, FR><<<grd, blk, smem, s>>>(p); break;
+        case IN_U16: k_ingest_norm<uint16_t, TS, FR><<<grd, blk, smem, s>>>(p); break;
+        default: k_ingest_norm<float, TS, FR><<<grd, blk, smem, s>>>(p); break;
+        }
+    } else {
+        switch (a.in_type) {
+        case IN_U8: k_ingest<uint8_t, TS, FR><<<grd, blk, 0, s>>>(p); break;
+        case IN_U16: k_ingest<uint16_t, TS, FR><<<grd, blk, 0, s>>>(p); break;
+        default: k_ingest<float, TS, FR><<<grd, blk, 0, s>>>(p); break;
+        }
     }
     if (a.prefilter) k_prefilter<TS, FR><<<grd, blk, 0, s>>>(p);
     return cudaGetLastError();
