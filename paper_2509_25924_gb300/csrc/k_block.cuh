@@ -46,7 +46,7 @@ template <int KR> struct BlockShape {
     // KR 6..8: 32-px tiles, two CTAs per SM; KR 9, 10: 48-px tiles (less
     // halo work), one CTA per SM (measured faster than the 32-px tiles
     // there, slower at KR 6..8)
-    static constexpr int TS = (KR <= 5 || KR >= 9) ? 48 : 32;   // output tile edge
+    static constexpr int TS = KR >= 9 ? 64 : KR <= 5 ? 48 : 32; // output tile edge
     static constexpr int NT = (KR <= 5 || KR >= 9) ? 512 : 256; // threads
     static constexpr int MINB = KR >= 9 ? 1 : 2;                // resident CTAs per SM (shared memory)
     static constexpr int RW = TS + 2 * KR;                // product region edge
