@@ -43,12 +43,13 @@ struct BlockParams {
 };
 
 template <int KR> struct BlockShape {
-    // KR 6..8: 32-px tiles, two CTAs per SM; KR 9, 10: 48-px tiles (less
-    // halo work), one CTA per SM (measured faster than the 32-px tiles
-    // there, slower at KR 6..8)
-    static constexpr int TS = KR >= 9 ? 64 : KR <= 5 ? 48 : 32; // output tile edge
-    static constexpr int NT = (KR <= 5 || KR >= 9) ? 512 : 256; // threads
-    static constexpr int MINB = KR >= 9 ? 1 : 2;                // resident CTAs per SM (shared memory)
+    // Measured per radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles, two
+    // CTAs per SM (64-px tiles at one CTA per SM: -15..-18 %); KR 6: 32-px
+    // tiles, two CTAs per SM (64 px: -2.5 %); KR 7..10: 64-px tiles, one CTA
+    // per SM (less halo work: +21..26 % against 32 or 48 px).
+    static constexpr int TS = KR <= 5 ? 48 : KR == 6 ? 32 : 64;  // output tile edge
+    static constexpr int NT = KR == 6 ? 256 : 512;               // threads
+    static constexpr int MINB = KR <= 6 ? 2 : 1;                 // resident CTAs per SM (shared memory)
     static constexpr int RW = TS + 2 * KR;                // product region edge
     static constexpr int RWP = RW | 1;                    // odd row pitch of the product planes
     static constexpr int SH = RW + 2 * kBlockReach + 3;   // staged rows
@@ -846,7 +847,7 @@ int queue_occupancy_t(int kr);
 // Output tile edge of the block kernel for radius kr.
 inline int block_tile_size(int kr)
 {
-    return kr <= 5 ? BlockShape<5>::TS : kr <= 8 ? BlockShape<8>::TS : BlockShape<10>::TS;
+    return kr <= 5 ? BlockShape<5>::TS : kr == 6 ? BlockShape<6>::TS : BlockShape<10>::TS;
 }
 
 }  // namespace ofv
