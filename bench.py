@@ -243,12 +243,15 @@ def run_ours(args, ws, rank, local):
     def step():
         ofv.ofv_compute_sequence(h, nframes, frames, N * 2, u, v, N, stream)
 
+    # nvidia-smi starts before the warm-up: its first queries (NVML start-up)
+    # can hold up CUDA calls of this process for tens of ms, which must not
+    # fall into the timed steps; its samples cover warm-up and timed steps
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
 
-    sampler = ClockSampler(local)
-    sampler.start()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -351,12 +354,12 @@ def e2e(args, ofv, torch, h, frames_h, dev, stream, barrier, max_over_ranks, ws)
     def run():
         ofv.ofv_compute_sequence_host(h, npairs + 1, host_frames, N * 2, hu, hv, N, stream)
 
+    sampler = ClockSampler(torch.cuda.current_device())  # before the warm-up (see the device-resident leg)
+    sampler.start()
     for _ in range(max(args.warmup, 1)):  # the same W warm-up steps as the device-resident leg
         run()
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 5))
-    sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
     barrier()
     t0 = time.perf_counter()
     c0 = time.process_time()
