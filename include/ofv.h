@@ -282,7 +282,7 @@ typedef struct {
 
 /* Estimate n pairs of any sizes (each within the shape limits of
  * ofv_create for the handle's parameters; the handle's own H, W do not
- * matter) with the handle's parameters.  pairs is a HOST array.  The frames
+ * matter) with the handle's parameters, 1 <= n <= 32767.  pairs is a HOST array.  The frames
  * are ingested and reduced size class by size class, then every (level,
  * iteration, tile) of every pair runs in ONE persistent launch of the fused
  * kernel: CTAs take work units from a queue in the order of a schedule, and

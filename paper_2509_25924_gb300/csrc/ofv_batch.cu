@@ -94,7 +94,9 @@ extern "C" {
 ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t stream)
 {
     if (!h || !pairs) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: handle or pairs is NULL");
-    if (n < 1) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: n=%d must be >= 1", n);
+    if (n < 1 || n > 32767)
+        return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: n=%d outside 1..32767 (one launch ingests all 2n frames)",
+                        n);
     const ofv_params &p = h->p;
     if (p.path != OFV_PATH_FUSED || p.kernel_radius > 10)
         return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_compute_batched: needs the fused path with KR <= 10");
