@@ -227,9 +227,10 @@ ofv_status ofv_probe(int H, int W, int n, const float *u, const float *v, size_t
  * gradients with respect to the raw input values) and, when gw25 is not
  * NULL, gw25 = dL/dw (25 floats, device, row-major 5x5 pre-filter weights;
  * zeros when params.prefilter = 0).  The forward pass is recomputed from I1
- * and I2 with the fused kernels and each stage's fields are kept in a
- * handle-owned workspace (grown on demand: one float2 field per stage at its
- * level's size plus about 17 float planes of the level-0 size).  A pixel whose 2x2
+ * and I2 with the fused kernels and each stage's fields and window sums are
+ * kept in a handle-owned workspace (grown on demand: one float2 field and
+ * five float planes per stage at its level's size plus about 17 float planes
+ * of the level-0 size).  A pixel whose 2x2
  * system was guarded keeps V0, so its gradient passes to V0 unchanged; at a
  * bilinear cell boundary the derivative is that of the cell floor() picks.
  * Float atomics scatter the gradients, so the last bits vary between runs.

@@ -399,27 +399,18 @@ cudaError_t box_tile(int kr, Planes5 in, Planes5 out, int H, int W, cudaStream_t
 }
 }  // namespace
 
-// One stage of the adjoint.  Window radii 1..10: the forward block kernel's
-// tile again with the solve adjoint as its epilogue (gS into B, direct part
-// of gV0), the box-sum adjoint tile by tile (gS -> gprod in A), the samples
-// adjoint with the scatter accumulated per tile in shared memory.  Larger
-// radii: one pixel per thread throughout.
-cudaError_t bw_stage(const IterArgs &a, int store, Planes5 A, Planes5 B, const float2 *gV, float2 *gV0, float *gP1,
-                     float *gP2, int gpitch, cudaStream_t s)
+// One stage of the adjoint.  Window radii 1..10: the solve adjoint from the
+// window sums the forward pass kept (Sk; gS into B, direct part of gV0), the
+// box-sum adjoint tile by tile (gS -> gprod in A), the samples adjoint with
+// the scatter accumulated per tile in shared memory.  Larger radii: one
+// pixel per thread throughout.
+cudaError_t bw_stage(const IterArgs &a, int store, Planes5 Sk, Planes5 A, Planes5 B, const float2 *gV, float2 *gV0,
+                     float *gP1, float *gP2, int gpitch, cudaStream_t s)
 {
     const dim3 g = grid2(a.W, a.H), b(32, 8);
     if (block_supports(a.kr)) {
-        BwStageParams q;
-        q.a = a;
-        q.epi.gV = gV;
-        q.epi.gV0 = gV0;
-        q.epi.gS = B;
-        q.epi.vpitch = a.vpitch;
-        cudaError_t e = store == ST_F16    ? launch_bw_stage_S_f16(q, s)
-                        : store == ST_BF16 ? launch_bw_stage_S_bf16(q, s)
-                                           : launch_bw_stage_S_f32(q, s);
-        if (e != cudaSuccess) return e;
-        e = box_tile(a.kr, B, A, a.H, a.W, s);
+        k_bw_solve<<<g, b, 0, s>>>(Sk, gV, a.vpitch, a.H, a.W, a.eps_rel, a.eps_abs, B, gV0);
+        cudaError_t e = box_tile(a.kr, B, A, a.H, a.W, s);
         if (e != cudaSuccess) return e;
         const dim3 gt((a.W + kSampTS - 1) / kSampTS, (a.H + kSampTS - 1) / kSampTS);
         switch (store) {
@@ -501,6 +492,7 @@ struct BwDevGuard {
 // base is null).
 struct BwLayout {
     float2 *Vst[kMaxLevels * 64];
+    float *Sst[kMaxLevels * 64];  // five window-sum planes per stage (block path)
     float2 *V0in[kMaxLevels];
     Planes5 A, B;
     float2 *gV, *gV0;
@@ -520,6 +512,9 @@ size_t bw_layout(const ofv_handle *h, char *base, BwLayout *o)
     for (int s = 0; s < L * IT; ++s) {
         const int l = L - 1 - s / IT;
         o->Vst[s] = reinterpret_cast<float2 *>(take((size_t)h->Hs[l] * h->pitch[l] * sizeof(float2)));
+        o->Sst[s] = block_supports(h->p.kernel_radius)
+                        ? reinterpret_cast<float *>(take(5 * (size_t)h->Hs[l] * h->pitch[l] * sizeof(float)))
+                        : nullptr;
     }
     for (int l = 0; l < L; ++l)
         o->V0in[l] = reinterpret_cast<float2 *>(take((size_t)h->Hs[l] * h->pitch[l] * sizeof(float2)));
@@ -630,6 +625,11 @@ extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2
             BW_TRY(bw_v0(b, mode, w.V0in[l], s), "ofv_backward: stage input field");
         }
         a.Vout = w.Vst[sidx];
+        if (w.Sst[sidx]) {  // keep the window sums for the solve adjoint
+            a.s_out = w.Sst[sidx];
+            a.s_plane = (size_t)h->Hs[l] * h->pitch[l];
+            a.s_pitch = h->pitch[l];
+        }
         cudaError_t e = block_supports(p.kernel_radius) ? launch_iter_block(&a, 1, p.storage, V0_SAME, s)
                                                         : launch_iter_fused(a, p.storage, V0_SAME, s);
         BW_TRY(e, "ofv_backward: forward iteration");
@@ -645,9 +645,12 @@ extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2
     for (int sidx = S - 1; sidx >= 0; --sidx) {
         const int l = L - 1 - sidx / IT, t = sidx % IT;
         IterArgs a = stage_args(sidx);
-        Planes5 A = w.A, B = w.B;
-        A.pitch = B.pitch = h->pitch[l];
-        BW_TRY(bw_stage(a, p.storage, A, B, gV, gV0, w.gP1[l], w.gP2[l], h->pitch[l], s), "ofv_backward: stage adjoint");
+        Planes5 A = w.A, B = w.B, Sk = {};
+        A.pitch = B.pitch = Sk.pitch = h->pitch[l];
+        if (w.Sst[sidx])
+            for (int c = 0; c < 5; ++c) Sk.p[c] = w.Sst[sidx] + c * (size_t)h->Hs[l] * h->pitch[l];
+        BW_TRY(bw_stage(a, p.storage, Sk, A, B, gV, gV0, w.gP1[l], w.gP2[l], h->pitch[l], s),
+               "ofv_backward: stage adjoint");
         if (sidx == 0) break;
         if (t > 0) {
             float2 *tmp = gV;

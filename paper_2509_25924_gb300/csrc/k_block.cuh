@@ -483,6 +483,11 @@ struct SolveStoreT {
                 V.y += V0.y;
             }
         }
+        if (VAR && a.s_out) {  // reverse mode: keep the window sums for the solve adjoint
+            const size_t o = (size_t)gy * a.s_pitch + gx;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) a.s_out[c * a.s_plane + o] = S[c];
+        }
         if (a.u_out) {
             if (VAR && a.mask && !__ldg(a.mask + (int64_t)gy * a.W + gx)) V = make_float2(no_vector(), no_vector());
             a.u_out[(int64_t)gy * a.W + gx] = V.x;

@@ -36,7 +36,7 @@ cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode
         }
     }
     // the kernels with variant code only when a variant is on (uniform per launch)
-    const bool var = a[0].inc || a[0].gauss || a[0].mask;
+    const bool var = a[0].inc || a[0].gauss || a[0].mask || a[0].s_out;
     switch (store) {
     case ST_F16: return var ? launch_block_t<__half, true>(p, a[0].kr, npairs, s)
                             : launch_block_t<__half, false>(p, a[0].kr, npairs, s);

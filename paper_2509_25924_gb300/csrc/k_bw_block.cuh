@@ -1,9 +1,9 @@
 // Reverse mode on the block kernel's machinery (window radii 1..10).
 //
-// Per Gauss-Newton stage the adjoint needs the forward window sums S again.
-// k_bw_stage_S recomputes them with the forward kernel's phases 0-3 (same
-// staging, products and additions-only window sums, so the guard decisions
-// are those of the forward pass) and replaces the solve by its adjoint:
+// Per Gauss-Newton stage the adjoint needs the forward window sums S: the
+// forward pass that the reverse mode recomputes keeps them (five planes per
+// stage, written by the solve epilogue), so the guard decisions are those of
+// the forward pass, and an elementwise kernel applies the solve adjoint:
 //   V = H^-1 b  =>  lambda = H^-1 gV,
 //   gS = (-lambda_x V_x, -(lambda_x V_y + lambda_y V_x), -lambda_y V_y, lambda_x, lambda_y),
 // and a guarded pixel (V = V0) passes gV to V0.  k_bw_box_tile applies the
@@ -18,73 +18,6 @@ struct Planes5 {
     float *p[5];
     int pitch;  // elements
 };
-
-// Epilogue of the forward tile: adjoint of the guarded solve.  gV is the
-// gradient of the stage output, gV0 receives the direct part of the
-// gradient of the stage input, gS the gradient of the five window sums.
-struct BwSolveAdj {
-    const float2 *gV;
-    float2 *gV0;
-    Planes5 gS;
-    int vpitch;
-
-    template <bool COH>
-    __device__ __forceinline__ void apply(const IterArgs &a, int, int gx, int gy, const float (&S)[5]) const
-    {
-        const int64_t ov = (int64_t)gy * vpitch + gx, o = (int64_t)gy * gS.pitch + gx;
-        const float sa = S[0], sb = S[1], sc = S[2], sxr = S[3], syr = S[4];
-        const float tr = sa + sc, det = sa * sc - sb * sb;
-        const float2 g = gV[ov];
-        float r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        float2 direct = make_float2(0.f, 0.f);
-        if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr) {
-            direct = g;
-        } else {
-            const float inv = 1.f / det;
-            const float Vx = (sc * sxr - sb * syr) * inv, Vy = (sa * syr - sb * sxr) * inv;
-            const float lx = (sc * g.x - sb * g.y) * inv, ly = (sa * g.y - sb * g.x) * inv;
-            r[0] = -lx * Vx;
-            r[1] = -(lx * Vy + ly * Vx);
-            r[2] = -ly * Vy;
-            r[3] = lx;
-            r[4] = ly;
-        }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) gS.p[k][o] = r[k];
-        gV0[ov] = direct;
-    }
-};
-
-struct BwStageParams {
-    IterArgs a;  // the stage: level images, V0 plane (V0_SAME), sizes, guards
-    BwSolveAdj epi;
-};
-
-template <typename T, int KR>
-__global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_bw_stage_S(const __grid_constant__ BwStageParams q)
-{
-    extern __shared__ __align__(128) float4 smem_f4[];
-    block_tile<T, KR, false, BwSolveAdj>(q.a, V0_SAME, blockIdx.x, blockIdx.y, smem_f4, nullptr, nullptr, nullptr,
-                                         q.epi);
-}
-
-template <typename T, int KR>
-cudaError_t run_bw_stage_S(const BwStageParams &q, cudaStream_t s)
-{
-    constexpr size_t smem = block_smem_bytes<T, KR>();
-    constexpr int TS = BlockShape<KR>::TS;
-    static bool granted[64];  // shared-memory opt-in done, per device
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !granted[dev]) {
-        e = cudaFuncSetAttribute(k_bw_stage_S<T, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) granted[dev] = true;
-    }
-    k_bw_stage_S<T, KR><<<dim3((q.a.W + TS - 1) / TS, (q.a.H + TS - 1) / TS), BlockShape<KR>::NT, smem, s>>>(q);
-    return cudaGetLastError();
-}
 
 // Truncated (2KR+1)^2 box sums of five planes, one TS x TS output tile per
 // CTA: the (TS+2KR)^2 input region (zero outside the image) in shared
@@ -144,10 +77,5 @@ cudaError_t run_bw_box_tile(Planes5 in, Planes5 out, int H, int W, cudaStream_t 
     k_bw_box_tile<KR><<<dim3((W + BS::TS - 1) / BS::TS, (H + BS::TS - 1) / BS::TS), BS::NT, smem, s>>>(in, out, H, W);
     return cudaGetLastError();
 }
-
-// Launchers (one translation unit per storage type for the stage kernel).
-cudaError_t launch_bw_stage_S_f32(const BwStageParams &q, cudaStream_t s);
-cudaError_t launch_bw_stage_S_f16(const BwStageParams &q, cudaStream_t s);
-cudaError_t launch_bw_stage_S_bf16(const BwStageParams &q, cudaStream_t s);
 
 }  // namespace ofv

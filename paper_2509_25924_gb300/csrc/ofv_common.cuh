@@ -58,6 +58,9 @@ struct IterArgs {
     int kr;
     float eps_rel, eps_abs;
     const uint8_t *mask;  // region mask of the level (dense rows of W, 0 = masked), or null
+    float *s_out;         // reverse mode: the five window sums of every pixel, plane c at s_out + c s_plane
+    size_t s_plane;       //   (rows of s_pitch floats), or null
+    int s_pitch;
     int inc;              // 1: increment form, r = -It and V = V0(m) + H^-1 (Sxr, Syr)
     int gauss;            // 1: window tap (a, b) weighted wg[|a|] wg[|b|]; 0: uniform box
     float wg[kMaxWindowRadius + 1];  // Gaussian window weights exp(-d^2 / (2 sigma^2)), d = 0..KR
