@@ -336,3 +336,65 @@ def test_graph_replay_runs_the_variants_and_the_mask_like_compute(rankine):
         assert torch.equal(gu.isnan().cpu(), torch.from_numpy(m == 0))
     finally:
         ofv.ofv_destroy(h)
+
+
+def _random_variant_configs(n=14, seed=20251203):
+    r = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        psl, it = int(r.integers(0, 4)), int(r.integers(1, 4))
+        path = int(r.integers(0, 3))
+        kr = int(r.integers(1, 11)) if path != ofv.OFV_PATH_TILE or r.random() < 0.7 else 12
+        minsz = max(8, 2 * kr + 1) * (1 << psl)
+        H, W = int(r.integers(minsz, minsz + 120)), int(r.integers(minsz, minsz + 120))
+        dm = 0.9 if psl == 0 else 2.5
+        d = (float(r.uniform(-dm, dm)), float(r.uniform(-dm, dm)))
+        sigma = float(r.uniform(0.8, 4.0)) if r.random() < 0.5 else 0.0
+        inc = bool(r.random() < 0.5)
+        mask = bool(r.random() < 0.4)
+        store = int(r.integers(0, 3))
+        out.append((H, W, psl, kr, it, path, d, sigma, inc, mask, store, int(r.integers(0, 2**31))))
+    return out
+
+
+@pytest.mark.parametrize("H,W,psl,kr,it,path,d,sigma,inc,mask,store,seed", _random_variant_configs())
+def test_random_variant_configurations_match_oracle(H, W, psl, kr, it, path, d, sigma, inc, mask, store, seed):
+    """Seeded random shapes, pyramid depths, radii, iterations, paths,
+    displacements, storage types and combinations of the Gaussian window,
+    the increment form and a region mask: FP32 by the max rule on the pixels
+    FP32 data determines (an oracle-only perturbation mask, as in the
+    default-path test), FP16 / BF16 by the RMS rule; no vector exactly at the
+    masked pixels."""
+    I1, I2 = synth.translation_pair(H, W, d, seed=seed % 100000, kind=synth.OUT_F32)
+    m = _disk_and_band_mask(H, W) if mask else None
+    kw = dict(path=path, levels_psl=psl, kernel_radius=kr, iterations=it, storage=store,
+              **_variant_params(gauss_sigma=sigma, inc=inc))
+    if m is not None:
+        u, v = _gpu_masked(I1, I2, m, **kw)
+    else:
+        u, v = _gpu(I1, I2, **kw)
+    prm = dict(psl=psl, kr=kr, it=it, win_sigma=sigma, increment_form=inc, mask=m)
+    ou, ov, nd, _ = oracle.flow(I1.astype(np.float64), I2.astype(np.float64), oracle.Params(**prm),
+                                diagnostics=True)
+    valid = np.ones((H, W), bool) if m is None else (m != 0)
+    assert np.array_equal(np.isnan(u), ~valid) and np.array_equal(np.isnan(v), ~valid)
+    label = f"{H}x{W} psl={psl} kr={kr} it={it} path={path} sigma={sigma:.2f} inc={inc} mask={mask} store={store}"
+    sel = valid & (nd >= NDET_MIN)
+    if store == ofv.OFV_STORE_F32:
+        rng = np.random.default_rng(1234)
+        worst = np.zeros((H, W))
+        for _ in range(2):
+            a1 = I1.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(I1.shape))
+            a2 = I2.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(I2.shape))
+            pu, pv = oracle.flow(a1, a2, oracle.Params(**prm))
+            worst = np.maximum(worst, np.nan_to_num(np.hypot(pu - ou, pv - ov)))
+        sel &= worst <= 0.1 * FP32_TOL
+        masked = 1.0 - sel[valid].mean()
+        assert masked <= 0.05, f"{label}: {masked:.3%} excluded"
+        dmax = max(np.abs(u - ou)[sel].max(), np.abs(v - ov)[sel].max())
+        print(f"{label}: max|dV|={dmax:.3e} excluded={masked:.4%}")
+        assert dmax <= FP32_TOL, f"{label}: max |dV| {dmax:.3e}"
+    else:
+        rms = float(np.sqrt(np.mean(np.hypot(u - ou, v - ov)[sel] ** 2)))
+        print(f"{label}: rms={rms:.3e}")
+        assert rms <= 1e-2, f"{label}: rms {rms:.3e}"
