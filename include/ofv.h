@@ -317,6 +317,25 @@ ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm
  * through (OFV_ERR_CUDA if it differs), the device still usable. */
 ofv_status ofv_queue_selftest(int timeout_us, int *error_word);
 
+/* ---- debugging hooks -----------------------------------------------------
+ * For tests of the error paths and of workspace hygiene; no effect on the
+ * estimator otherwise.
+ *
+ * ofv_debug_fail_alloc(n): the n-th device allocation of the library from
+ * now on (workspaces of ofv_create, of the host-pointer, host-sequence,
+ * batched and reverse-mode entry points, the mask levels) fails as if the
+ * device were out of memory; n <= 0 cancels.  The entry point then returns
+ * OFV_ERR_ALLOC and leaves nothing allocated.
+ *
+ * ofv_debug_poison(h, s): fills the handle's scratch (pyramids, fields,
+ * staging, reverse-mode and batch workspaces) with all-ones bytes (NaN in
+ * every float) on stream s.  A compute call must then give bitwise the same
+ * result as before: no output depends on scratch it did not write first.
+ * The pre-filter weights and the region mask are state, not scratch, and
+ * are kept. */
+void ofv_debug_fail_alloc(int n);
+ofv_status ofv_debug_poison(ofv_handle *h, ofv_stream_t s);
+
 /* ---- CUDA-graph replay (live loop) -------------------------------------
  * A live acquisition hands the estimator a new pair into the same device
  * buffers at a fixed rate (Sec. 6, live mode).  ofv_graph_create records the

@@ -19,7 +19,8 @@ from . import build as _build
 __all__ = [
     "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_set_mask",
     "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host",
-    "ofv_compute_noalloc", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_probe", "ofv_level_shape",
+    "ofv_compute_noalloc", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_probe",
+    "ofv_debug_fail_alloc", "ofv_debug_poison", "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
     "Flow", "lib_path", "EXPORTED_SYMBOLS",
@@ -38,7 +39,7 @@ EXPORTED_SYMBOLS = [
     "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host", "ofv_compute_noalloc",
     "ofv_graph_create", "ofv_graph_launch",
     "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
-    "ofv_vorticity", "ofv_recirculation_area", "ofv_probe",
+    "ofv_vorticity", "ofv_recirculation_area", "ofv_probe", "ofv_debug_fail_alloc", "ofv_debug_poison",
     "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
@@ -90,6 +91,8 @@ def _load_library():
         "ofv_vorticity": ([I, I, I, P, P, Z, P, P], I),
         "ofv_recirculation_area": ([I, I, I, P, Z, P, P, P], I),
         "ofv_probe": ([I, I, I, P, P, Z, I, P, P, P], I),
+        "ofv_debug_fail_alloc": ([I], None),
+        "ofv_debug_poison": ([P, P], I),
         "ofv_level_shape": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "ofv_read_level": ([P, I, I, P, P], I),
         "ofv_profile_enable": ([P, I], I),
@@ -218,6 +221,16 @@ def ofv_probe(H: int, W: int, n: int, u, v, field_stride: int, npts: int, xy, ou
     out (n x npts x 2 float32, device), bilinear, clamp-to-edge."""
     _check(_lib.ofv_probe(H, W, n, _addr(u), _addr(v), field_stride, npts, _addr(xy), _addr(out), _stream(stream)),
            "ofv_probe")
+
+
+def ofv_debug_fail_alloc(n: int):
+    """Make the n-th device allocation of the library from now on fail (n <= 0 cancels)."""
+    _lib.ofv_debug_fail_alloc(n)
+
+
+def ofv_debug_poison(h: int, stream=None):
+    """Fill the handle's scratch with NaN bytes (state is kept)."""
+    _check(_lib.ofv_debug_poison(h, _stream(stream)), "ofv_debug_poison")
 
 
 def ofv_recirculation_area(H: int, W: int, n: int, u, field_stride: int, mask, counts, stream=None):

@@ -576,7 +576,7 @@ extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2
             h->bw_arena = nullptr;
             h->bw_bytes = 0;
         }
-        if (cudaMalloc(&h->bw_arena, need) != cudaSuccess) {
+        if (dev_alloc(&h->bw_arena, need) != cudaSuccess) {
             cudaGetLastError();
             h->bw_arena = nullptr;
             return fail_msg(OFV_ERR_ALLOC, "ofv_backward: cudaMalloc of %zu bytes failed", need);

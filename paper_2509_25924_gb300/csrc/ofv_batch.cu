@@ -194,7 +194,7 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
         }
         h->batch_sched_key.clear();  // nothing uploaded lives in the new arena
         h->batch_maps_key.clear();
-        e = cudaMalloc(&h->batch_arena, off);
+        e = dev_alloc(&h->batch_arena, off);
         if (e != cudaSuccess) {
             cudaGetLastError();
             h->batch_arena = nullptr;

@@ -8,7 +8,9 @@
 // the coarse levels from leaving the GPU idle.
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -187,6 +189,10 @@ ofv_status build_pyramids(ofv_handle *h, const void *const *frames, const int *s
 {
     const ofv_params &p = h->p;
     const int sb = store_bytes(p.storage), ib = input_bytes(p.input);
+    nvtxRangePushA("ofv ingest and pyramid");
+    struct RangePop {
+        ~RangePop() { nvtxRangePop(); }
+    } pop_at_return;
     IngestArgs ia[kMaxFramesPerLaunch];
     for (int k = 0; k < nf; ++k) {
         IngestArgs &a = ia[k];
@@ -258,7 +264,16 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
         if (st != OFV_OK) return st;
         have = true;  // vbuf[2k + 0] holds the starting field
     }
+    // NVTX ranges name each level's launches for profilers (no cost without one)
+    static const char *const kLevelRange[kMaxLevels] = {
+        "ofv level 0", "ofv level 1", "ofv level 2", "ofv level 3", "ofv level 4", "ofv level 5",
+        "ofv level 6", "ofv level 7", "ofv level 8", "ofv level 9", "ofv level 10", "ofv level 11",
+        "ofv level 12", "ofv level 13", "ofv level 14", "ofv level 15"};
     for (int l = h->L - 1; l >= 0; --l) {
+        nvtxRangePushA(kLevelRange[l]);
+        struct RangePop {
+            ~RangePop() { nvtxRangePop(); }
+        } pop_at_level_end;
         for (int t = 0; t < p.iterations; ++t) {
             int mode;
             if (t == 0 && l == h->L - 1) mode = have ? V0_SAME : V0_ZERO;
@@ -442,6 +457,22 @@ ofv_status pending_error(const ofv_handle *h, const char *where)
 }  // namespace
 
 namespace ofv {
+namespace {
+std::atomic<int> g_fail_alloc{0};  // > 0: that many allocations from now, the last one fails
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    int n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 // Record a failure message for ofv_last_error() from another translation unit.
 void set_error_message(const char *msg) { fail(OFV_OK, "%s", msg); }
 
@@ -591,7 +622,7 @@ ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)
         off = align_up(off + (size_t)H * h->vpitch * sizeof(float2), 256);
     }
     h->arena_bytes = off;
-    cudaError_t e = cudaMalloc(&h->arena, off);
+    cudaError_t e = dev_alloc(&h->arena, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -684,6 +715,27 @@ ofv_status ofv_destroy(ofv_handle *h)
     return st;
 }
 
+void ofv_debug_fail_alloc(int n) { g_fail_alloc.store(n > 0 ? n : 0); }
+
+ofv_status ofv_debug_poison(ofv_handle *h, ofv_stream_t s)
+{
+    if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(OFV_ERR_CUDA, "cannot select the handle's device");
+    cudaStream_t cs = (cudaStream_t)s;
+    char *base = static_cast<char *>(h->arena);
+    const size_t w0 = reinterpret_cast<char *>(h->w25) - base, w1 = align_up(w0 + 25 * sizeof(float), 256);
+    cudaError_t e = cudaMemsetAsync(base, 0xFF, w0, cs);  // all-ones bytes: NaN in every float
+    if (e == cudaSuccess && h->arena_bytes > w1) e = cudaMemsetAsync(base + w1, 0xFF, h->arena_bytes - w1, cs);
+    if (e == cudaSuccess && h->stage) e = cudaMemsetAsync(h->stage, 0xFF, h->stage_bytes, cs);
+    if (e == cudaSuccess && h->hs_stage) e = cudaMemsetAsync(h->hs_stage, 0xFF, h->hs_bytes, cs);
+    if (e == cudaSuccess && h->bw_arena) e = cudaMemsetAsync(h->bw_arena, 0xFF, h->bw_bytes, cs);
+    if (e == cudaSuccess && h->batch_arena) e = cudaMemsetAsync(h->batch_arena, 0xFF, h->batch_bytes, cs);
+    h->batch_sched_key.clear();  // the schedule and tensor maps in the batch arena are gone
+    h->batch_maps_key.clear();
+    return e == cudaSuccess ? OFV_OK : cuda_fail(e, "poisoning the workspace");
+}
+
 ofv_status ofv_set_mask(ofv_handle *h, const uint8_t *mask, ofv_stream_t s)
 {
     if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");
@@ -699,7 +751,7 @@ ofv_status ofv_set_mask(ofv_handle *h, const uint8_t *mask, ofv_stream_t s)
             off[l] = total;
             total += align_up((size_t)h->Hs[l] * h->Ws[l], 256);
         }
-        if (cudaMalloc(&h->mask_arena, total) != cudaSuccess) {
+        if (dev_alloc(&h->mask_arena, total) != cudaSuccess) {
             cudaGetLastError();
             h->mask_arena = nullptr;
             return fail(OFV_ERR_ALLOC, "cudaMalloc of %zu mask bytes failed", total);
@@ -753,7 +805,7 @@ ofv_status ofv_compute_host(ofv_handle *h, const void *I1, const void *I2, float
     const size_t out_b = align_up(N * sizeof(float), 256);
     const size_t need = 2 * in_b + 2 * out_b;
     if (!h->stage) {
-        cudaError_t e = cudaMalloc(&h->stage, need);
+        cudaError_t e = dev_alloc(&h->stage, need);
         if (e != cudaSuccess) {
             cudaGetLastError();
             h->stage = nullptr;
@@ -862,7 +914,7 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
             h->hs_stage = nullptr;
             h->hs_bytes = 0;
         }
-        if (cudaMalloc(&h->hs_stage, need) != cudaSuccess) {
+        if (dev_alloc(&h->hs_stage, need) != cudaSuccess) {
             cudaGetLastError();
             h->hs_stage = nullptr;
             return fail(OFV_ERR_ALLOC, "cudaMalloc of %zu ring bytes failed", need);

@@ -109,6 +109,10 @@ struct ofv_handle {
 };
 
 namespace ofv {
+// Device allocation of the library's workspaces: cudaMalloc, unless a
+// failure was scheduled by ofv_debug_fail_alloc (then
+// cudaErrorMemoryAllocation and nothing allocated).
+cudaError_t dev_alloc(void **p, size_t bytes);
 // Steps 1-2 into the handle's pyramid slots (defined with the C ABI).
 ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s);
 // Tensor map of a level image with the block kernel's TMA box.
