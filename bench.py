@@ -300,7 +300,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"1024x1024 u16 12-bit Rankine+shift stream of {nframes} frames ({npairs} pairs), "
                                "PSL2 KR4 IT3, FP32 storage, fused kernels, ofv_compute_sequence",
-                   "global_batch": npairs * ws, "pairs_per_rank": npairs, "parallelism": f"replicas{ws}",
+                   "pairs_total": npairs * ws, "pairs_per_rank": npairs, "parallelism": f"replicas{ws}",
                    "l2": f"inputs ({nframes * N * 2 / 1e9:.2f} GB of frames) larger than L2" if nframes * N * 2 > 129e6 else "inputs smaller than L2"},
         "mvectors_per_s": value * N / 1e6,
         "gpu_launches": launches_per_step * args.steps,
