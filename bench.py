@@ -539,6 +539,8 @@ def variants(ofv, torch, synth, dev, stream, frames, u, v, n_frames=201, reps=5)
         ("warm_d8_psl0_it2", dict(warm_start=8, levels_psl=0, iterations=2)),
         ("warm_d8_psl0_it1", dict(warm_start=8, levels_psl=0, iterations=1)),
         ("warm_d1_psl0_it2", dict(warm_start=1, levels_psl=0, iterations=2)),
+        ("warm_d16_psl0_it2", dict(warm_start=16, levels_psl=0, iterations=2)),
+        ("warm_d16_psl2_it3", dict(warm_start=16)),
         ("cold_psl0_it2", dict(levels_psl=0, iterations=2)),
         ("mask_disk_psl2_it3", dict(mask="disk")),
     ]

@@ -104,10 +104,12 @@ typedef struct {
     float window_sigma; /* OFV_WINDOW_GAUSS: sigma in px, finite and > 0 */
     int increment_form; /* 1: each Gauss-Newton step solves for the increment,
                            V(m) = V0(m) + H^-1 sum G (-It), instead of H V = sum G (G.V0 - It) */
-    int warm_start;     /* sequences only, 0..8: 0 = every pair starts from V = 0; d > 0 = pair k >= d
+    int warm_start;     /* sequences only, 0..56: 0 = every pair starts from V = 0; d > 0 = pair k >= d
                            starts its coarsest level from pair k-d's field sampled at that level's pixels,
-                           V_L(i, j) = V(2^L i, 2^L j) / 2^L (pairs k < d start from 0).  Pairs then run in
-                           groups of d per launch; d must not exceed the handle's pairs-per-launch. */
+                           V_L(i, j) = V(2^L i, 2^L j) / 2^L (pairs k < d start from 0).  d <= B (the
+                           pairs-per-launch): groups of d pairs, each waiting for the previous one.  A
+                           multiple d = m B (m <= 7, device sequences only): groups of B pairs, each
+                           waiting for the group m back, so the m - 1 groups between still overlap. */
 } ofv_params;
 
 typedef struct ofv_handle ofv_handle;
@@ -166,8 +168,9 @@ ofv_status ofv_compute_host(ofv_handle *h, const void *I1, const void *I2, float
    library-owned streams so that one group's coarse levels overlap another's
    fine levels.  Work queued on s before the call runs first, and s reaches
    the end of the call only when every field is written.  With
-   params.warm_start = d, pair k >= d starts from pair k-d's field (groups of
-   d pairs; OFV_ERR_INVALID_ARG if d exceeds the pairs-per-launch). */
+   params.warm_start = d, pair k >= d starts from pair k-d's field
+   (OFV_ERR_INVALID_ARG unless d <= B or d = m B with m <= 7; B = the
+   pairs-per-launch; the host-memory form below accepts d <= B only). */
 ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
                                 size_t frame_stride_bytes, float *u, float *v, size_t field_stride,
                                 ofv_stream_t s);

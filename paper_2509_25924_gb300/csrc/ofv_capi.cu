@@ -97,8 +97,8 @@ ofv_status check_params(const ofv_params *p)
                     (double)p->window_sigma);
     if (p->increment_form != 0 && p->increment_form != 1)
         return fail(OFV_ERR_INVALID_ARG, "increment_form=%d is not 0 or 1", p->increment_form);
-    if (p->warm_start < 0 || p->warm_start > kMaxBatch)
-        return fail(OFV_ERR_INVALID_ARG, "warm_start=%d outside 0..%d", p->warm_start, kMaxBatch);
+    if (p->warm_start < 0 || p->warm_start > 7 * kMaxBatch)
+        return fail(OFV_ERR_INVALID_ARG, "warm_start=%d outside 0..%d", p->warm_start, 7 * kMaxBatch);
     return OFV_OK;
 }
 
@@ -373,10 +373,11 @@ struct GroupRunner {
     // fr[k] = frame f0 + k (k = 0 .. np), device pointers; before_ingest
     // (optional) is an event the group's stream waits for first.  iu, iv
     // (warm start): pair k starts from the level-0 field iu[k], iv[k], which
-    // group g-1 wrote; the iterations then wait for group g-1.
+    // group g-lag wrote; the iterations then wait for group g-lag (lag <= 7,
+    // within the event ring).
     ofv_status group(int g, int f0, int np, const void *const *fr, float *const *uu, float *const *vv,
                      cudaEvent_t before_ingest = nullptr, const float *const *iu = nullptr,
-                     const float *const *iv = nullptr)
+                     const float *const *iv = nullptr, int lag = 1)
     {
         const int NS = h->nslots;
         cudaStream_t cs = stream_of(g);
@@ -399,8 +400,8 @@ struct GroupRunner {
             if (e == cudaSuccess && g >= 1) e = cudaStreamWaitEvent(cs, h->gev[ev(g - 1)][0], 0);
             if (e != cudaSuccess) return cuda_fail(e, "ordering a group");
         }
-        if (K > 1 && iu && g >= 1) {
-            e = cudaStreamWaitEvent(cs, h->gev[ev(g - 1)][1], 0);
+        if (K > 1 && iu && g >= lag) {
+            e = cudaStreamWaitEvent(cs, h->gev[ev(g - lag)][1], 0);
             if (e != cudaSuccess) return cuda_fail(e, "ordering a warm-started group");
         }
         int s1[kMaxBatch], s2[kMaxBatch];
@@ -431,15 +432,25 @@ struct GroupRunner {
     }
 };
 
-// Pairs per group of a sequence: the handle's pairs-per-launch, or d with
-// a warm start from the pair d steps back (which is then pair k of the
-// previous group).
-ofv_status group_size(const ofv_handle *h, int *gb)
+// Pairs per group of a sequence and, with a warm start from the pair d
+// steps back, how many groups back that pair lies (it is then pair k of
+// group g - lag): d <= B gives groups of d pairs and lag 1; a multiple d of
+// B (with allow_lag, up to 7 B) keeps groups of B and a lag of d / B groups,
+// so the groups in between overlap as without a warm start.
+ofv_status group_size(const ofv_handle *h, int *gb, int *lag, bool allow_lag)
 {
     const int d = h->p.warm_start;
-    if (d > h->B)
-        return fail(OFV_ERR_INVALID_ARG, "warm_start=%d exceeds the handle's %d pairs per launch", d, h->B);
-    *gb = d > 0 ? d : h->B;
+    *lag = 1;
+    if (d <= h->B) {
+        *gb = d > 0 ? d : h->B;
+        return OFV_OK;
+    }
+    if (!allow_lag || d % h->B != 0 || d / h->B > 7)
+        return fail(OFV_ERR_INVALID_ARG,
+                    "warm_start=%d: needs d <= %d (the pairs per launch)%s", d, h->B,
+                    allow_lag ? " or a multiple of it up to 7 times" : " for a sequence from host memory");
+    *gb = h->B;
+    *lag = d / h->B;
     return OFV_OK;
 }
 
@@ -846,8 +857,8 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
     cudaStream_t cs = (cudaStream_t)s;
     const char *fb = static_cast<const char *>(frames);
     const int npairs = n_frames - 1;
-    int GB;  // pairs per group
-    if ((st = group_size(h, &GB)) != OFV_OK) return st;
+    int GB, lag;  // pairs per group; groups back to a warm start's source
+    if ((st = group_size(h, &GB, &lag, true)) != OFV_OK) return st;
     const int d = h->p.warm_start;
     GroupRunner gr(h, cs);
     if ((st = gr.begin()) != OFV_OK) return st;
@@ -860,13 +871,14 @@ ofv_status ofv_compute_sequence(ofv_handle *h, int n_frames, const void *frames,
         for (int k = 0; k < np; ++k) {
             uu[k] = u + (size_t)(f0 + k) * field_stride;
             vv[k] = v + (size_t)(f0 + k) * field_stride;
-            if (d > 0 && f0 >= d) {  // pair f0+k-d is pair k of group g-1
+            if (d > 0 && f0 >= d) {  // pair f0+k-d is pair k of group g-lag
                 iu[k] = u + (size_t)(f0 + k - d) * field_stride;
                 iv[k] = v + (size_t)(f0 + k - d) * field_stride;
             }
         }
         const bool warm = d > 0 && f0 >= d;
-        if ((st = gr.group(g, f0, np, fr, uu, vv, nullptr, warm ? iu : nullptr, warm ? iv : nullptr)) != OFV_OK)
+        if ((st = gr.group(g, f0, np, fr, uu, vv, nullptr, warm ? iu : nullptr, warm ? iv : nullptr, lag)) !=
+            OFV_OK)
             return st;
     }
     return gr.end();
@@ -889,8 +901,8 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
     ofv_status st = pending_error(h, "error pending before ofv_compute_sequence_host");
     if (st != OFV_OK) return st;
     cudaStream_t cs = (cudaStream_t)s;
-    int B;  // pairs per group
-    if ((st = group_size(h, &B)) != OFV_OK) return st;
+    int B, lag;  // pairs per group; the warm start's source is the previous group (lag 1)
+    if ((st = group_size(h, &B, &lag, false)) != OFV_OK) return st;
     const int d = h->p.warm_start;
     // device ring: per slot B+1 frames and B fields (u and v)
     const size_t in_b = align_up(fb * (size_t)(B + 1), 256);

@@ -74,7 +74,7 @@ def test_params_struct_layout_matches_the_header(tmp_path):
     ("iterations", 0), ("iterations", 65), ("norm_radius", -1), ("input", 7), ("storage", 3),
     ("path", 3), ("prefilter", 2), ("bit_depth", 0), ("bit_depth", 17), ("det_rel_eps", float("nan")),
     ("norm_eps", 0.0), ("max_batch", -1), ("max_batch", 9), ("window", 2), ("window", -1),
-    ("increment_form", 2), ("warm_start", -1), ("warm_start", 9),
+    ("increment_form", 2), ("warm_start", -1), ("warm_start", 57),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(field, value):
     p = ofv.ofv_default_params(**{field: value})

@@ -167,10 +167,13 @@ def _oracle_chain(F, d, psl, kr, it):
 
 @pytest.mark.parametrize("d,batch,psl,it,path", [
     (1, 8, 0, 2, ofv.OFV_PATH_FUSED), (2, 2, 2, 3, ofv.OFV_PATH_FUSED), (3, 4, 1, 2, ofv.OFV_PATH_FUSED),
-    (1, 1, 1, 2, ofv.OFV_PATH_PLAIN),
+    (1, 1, 1, 2, ofv.OFV_PATH_PLAIN), (4, 2, 0, 2, ofv.OFV_PATH_FUSED), (6, 2, 1, 2, ofv.OFV_PATH_FUSED),
 ])
 def test_warm_started_sequence_matches_the_oracle_chain(d, batch, psl, it, path):
-    n, H, W, kr = 8, 96, 128, 4
+    """d <= batch: groups of d pairs; d = m batch: groups of batch pairs,
+    each started from the group m back (device sequence only; the host-memory
+    form refuses it)."""
+    n, H, W, kr = 11, 96, 128, 4
     F = synth.stream_frames(H, W, n, seed=5)
     p = ofv.ofv_default_params(levels_psl=psl, kernel_radius=kr, iterations=it, max_batch=batch, warm_start=d,
                                path=path)
@@ -180,11 +183,15 @@ def test_warm_started_sequence_matches_the_oracle_chain(d, batch, psl, it, path)
         us = torch.empty((n - 1, H, W), device=DEV); vs = torch.empty_like(us)
         ofv.ofv_compute_sequence(h, n, fr, H * W * 2, us, vs, H * W)
         torch.cuda.synchronize()
-        # the same sequence from host memory gives the same fields bitwise
         hu = torch.empty((n - 1, H, W)).pin_memory(); hv = torch.empty_like(hu).pin_memory()
-        ofv.ofv_compute_sequence_host(h, n, torch.from_numpy(F).pin_memory(), H * W * 2, hu, hv, H * W)
-        torch.cuda.synchronize()
-        assert torch.equal(hu, us.cpu()) and torch.equal(hv, vs.cpu())
+        if d <= batch:  # the same sequence from host memory gives the same fields bitwise
+            ofv.ofv_compute_sequence_host(h, n, torch.from_numpy(F).pin_memory(), H * W * 2, hu, hv, H * W)
+            torch.cuda.synchronize()
+            assert torch.equal(hu, us.cpu()) and torch.equal(hv, vs.cpu())
+        else:
+            with pytest.raises(ofv.OfvError) as ei:
+                ofv.ofv_compute_sequence_host(h, n, torch.from_numpy(F).pin_memory(), H * W * 2, hu, hv, H * W)
+            assert ei.value.status == ofv.OFV_ERR_INVALID_ARG
         ref = _oracle_chain(F, d, psl, kr, it)
         for k in range(n - 1):
             ou, ov, nd, _ = ref[k]
@@ -212,6 +219,7 @@ def test_warm_start_pairs_before_d_equal_the_cold_start():
 
 
 def test_warm_start_beyond_the_batch_is_rejected():
+    """d above the pairs per launch and not a multiple of it."""
     H, W = 96, 128
     h = ofv.ofv_create(H, W, ofv.ofv_default_params(max_batch=2, warm_start=3))
     try:
