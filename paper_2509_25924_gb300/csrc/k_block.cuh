@@ -64,6 +64,20 @@ __host__ __device__ constexpr int band_rows(int rows, int row_bytes)
     return b;
 }
 
+// Phase 1 gives consecutive lanes consecutive pixels of a product row; a
+// warp that runs past the end of a row goes on in the next row it visits.
+// Against a run of consecutive addresses its staged taps then jump by
+// SP - RW elements (rows visited top down) or by -(SP + RW) (bottom up).
+// The warp's loads stay on distinct banks when the jump is a whole number
+// of 32-bit words whose residue modulo the 32 banks keeps the two runs
+// apart (32 elements cover 8 sizeof(T) words).
+template <typename T>
+__host__ __device__ constexpr bool bank_clean_jump(int shift)
+{
+    return (shift * (int)sizeof(T)) % 4 == 0 &&
+           (((shift * (int)sizeof(T) / 4) % 32 + 32) % 32) <= 32 - 8 * (int)sizeof(T);
+}
+
 template <typename T, int KR> struct StageShape {
     static constexpr int VEC = 16 / (int)sizeof(T);
     static constexpr int SW = BlockShape<KR>::RW + 2 * kBlockReach + 3 + VEC - 1;  // incl. alignment slack
@@ -75,6 +89,17 @@ template <typename T, int KR> struct StageShape {
     static constexpr int SHT = NBAND * SHB;
     // elements per staged frame, rounded so the second frame starts 128-byte aligned
     static constexpr int STG = (SHT * SP * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
+};
+
+// Order of the product rows in phase 1: bottom up where only that order
+// keeps the row jumps bank-clean (FP32 staging at KR 4: SP 72, RW 56).
+// Bottom up, the staged box starts `slack` rows higher (the rows by which
+// the three bands exceed the SH rows the tile reads), so that the last band
+// is full and the first iterations need it alone.
+template <typename T, int KR> struct RowOrder {
+    static constexpr int SP = StageShape<T, KR>::SP, RW = BlockShape<KR>::RW;
+    static constexpr bool bottom_up = !bank_clean_jump<T>(SP - RW) && bank_clean_jump<T>(-(SP + RW));
+    static constexpr int slack = bottom_up ? StageShape<T, KR>::SHT - BlockShape<KR>::SH : 0;
 };
 
 // floats of the five product planes, rounded up so the staged images that
@@ -337,6 +362,18 @@ __host__ __device__ constexpr int first_iter_of_band(int b)
     return i;
 }
 
+// The same for rows visited bottom up (bands waited from the last to the
+// first): the lowest product row of iteration i is RW - 1 - ((i + 1) NT - 1)
+// over RW, and product row r reads staged rows from r + SLACK on.
+template <int KR, int SHB, int SLACK>
+__host__ __device__ constexpr int first_iter_of_band_up(int b)
+{
+    constexpr int NT = BlockShape<KR>::NT, RW = BlockShape<KR>::RW;
+    int i = 0;
+    while (i * NT < RW * RW && RW - 1 - ((i + 1) * NT - 1) / RW + SLACK >= (b + 1) * SHB) ++i;
+    return i;
+}
+
 // With bars (TMA staging in three bands), the loop waits for band b just
 // before the first iteration that can touch it, so the first rows of
 // products overlap the copies of the later bands.
@@ -349,12 +386,16 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
     using SS = StageShape<T, KR>;
     static_assert(SS::NBAND == 3, "three staging bands");
     constexpr int NT = BS::NT, RW = BS::RW, RWP = BS::RWP, PLANE = RW * RWP;
-    constexpr int DY = NT / RW, DX = NT % RW;
+    constexpr bool UP = RowOrder<T, KR>::bottom_up;
+    constexpr int DX = NT % RW, DY = UP ? -(NT / RW) : NT / RW, DW = UP ? -1 : 1;
     constexpr int I1 = first_iter_of_band<KR, SS::SHB>(1), I2 = first_iter_of_band<KR, SS::SHB>(2);
+    constexpr int J1 = first_iter_of_band_up<KR, SS::SHB, RowOrder<T, KR>::slack>(1);
+    constexpr int J0 = first_iter_of_band_up<KR, SS::SHB, RowOrder<T, KR>::slack>(0);
     const int tid = threadIdx.x;
     int ry = tid / RW, rx = tid - (tid / RW) * RW;
+    if (UP) ry = RW - 1 - ry;
     float2 V0n = make_float2(0.f, 0.f);
-    if (ry < RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
+    if (tid < RW * RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
     auto wait_band = [&](int b) {
         if (bars && !mbar_wait_bounded(bars + b, parity, 2000000000LL)) {
             // report; the tile's results are then undefined
@@ -370,7 +411,7 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
         ry += DY;
         if (rx >= RW) {
             rx -= RW;
-            ++ry;
+            ry += DW;
         }
         if (idx + NT < RW * RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
         float p[5];
@@ -383,11 +424,19 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
         q[4 * PLANE] = p[4];
     };
     int idx = tid;
-    wait_band(0);
-    for (; idx < RW * RW && idx < I1 * NT; idx += NT) pixel(idx);
-    wait_band(1);
-    for (; idx < RW * RW && idx < I2 * NT; idx += NT) pixel(idx);
-    wait_band(2);
+    if (UP) {
+        wait_band(2);
+        for (; idx < RW * RW && idx < J1 * NT; idx += NT) pixel(idx);
+        wait_band(1);
+        for (; idx < RW * RW && idx < J0 * NT; idx += NT) pixel(idx);
+        wait_band(0);
+    } else {
+        wait_band(0);
+        for (; idx < RW * RW && idx < I1 * NT; idx += NT) pixel(idx);
+        wait_band(1);
+        for (; idx < RW * RW && idx < I2 * NT; idx += NT) pixel(idx);
+        wait_band(2);
+    }
     for (; idx < RW * RW; idx += NT) pixel(idx);
 }
 
@@ -530,7 +579,8 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
     const int H = a.H, W = a.W, pitch = a.pitch;
     const int tx0 = bx * TS, ty0 = by * TS;
     const int px0 = tx0 - KR, py0 = ty0 - KR;                      // product region origin
-    const int sy0 = py0 - kBlockReach - 1;                         // staged row origin
+    constexpr bool UP = RowOrder<T, KR>::bottom_up;
+    const int sy0 = py0 - kBlockReach - 1 - RowOrder<T, KR>::slack;  // staged row origin
     const int sxn = px0 - kBlockReach - 1;
     const int sx0 = (sxn >= 0 ? sxn / VEC : -((-sxn + VEC - 1) / VEC)) * VEC;  // floor to a VEC multiple
     const T *P1 = static_cast<const T *>(a.P1);
@@ -551,7 +601,8 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
             // order earlier generic-proxy accesses of the buffer (a previous
             // tile of this CTA) before the copies
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            for (int b = 0; b < NBAND; ++b) {
+            for (int k = 0; k < NBAND; ++k) {
+                const int b = UP ? NBAND - 1 - k : k;  // the band phase 1 needs first, first
                 mbar_expect_tx(&tma_bars[b], (unsigned)(2 * SHB * SP * sizeof(T)));
                 tma_load_2d(stage + b * SHB * SP, tm1, sx0, sy0 + b * SHB, &tma_bars[b]);
                 tma_load_2d(stage + STG + b * SHB * SP, tm2, sx0, sy0 + b * SHB, &tma_bars[b]);
@@ -597,17 +648,19 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
         if (bars && tid == 0)
             for (int b = 0; b < NBAND; ++b) mbar_wait_bounded(&bars[b], parity, 1000000000LL);
     } else {
-        constexpr int DY = NT / RW, DX = NT % RW;  // index step in rows and columns
+        // index step in rows and columns (rows in the order of RowOrder)
+        constexpr int DX = NT % RW, DY = UP ? -(NT / RW) : NT / RW, DW = UP ? -1 : 1;
         int ry = tid / RW, rx = tid - (tid / RW) * RW;
+        if (UP) ry = RW - 1 - ry;
         // V0 of the thread's next pixel is loaded one iteration ahead
         float2 V0n = make_float2(0.f, 0.f);
-        if (ry < RW && py0 + ry >= 0 && py0 + ry < H && px0 + rx >= 0 && px0 + rx < W)
+        if (tid < RW * RW && py0 + ry >= 0 && py0 + ry < H && px0 + rx >= 0 && px0 + rx < W)
             V0n = fetch_v0_rt<COH>(a, mode, px0 + rx, py0 + ry);
         for (int idx = tid; idx < RW * RW; idx += NT) {
             const int gy = py0 + ry, gx = px0 + rx;
             const float2 V0c = V0n;
             int nry = ry + DY, nrx = rx + DX;
-            if (nrx >= RW) { nrx -= RW; ++nry; }
+            if (nrx >= RW) { nrx -= RW; nry += DW; }
             if (idx + NT < RW * RW && py0 + nry >= 0 && py0 + nry < H && px0 + nrx >= 0 && px0 + nrx < W)
                 V0n = fetch_v0_rt<COH>(a, mode, px0 + nrx, py0 + nry);
             float p[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
