@@ -326,9 +326,12 @@ __device__ __forceinline__ void products_interior(const T *__restrict__ st1, con
                                                  make_float2(fx1, fx2), make_float2(fy1, fy2));
         s1 = Sample{s12.val.x, s12.gx.x, s12.gy.x};
         s2 = Sample{s12.val.y, s12.gx.y, s12.gy.y};
-        // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4
-        Gx = 0.25f * (s1.gx + s2.gx);
-        Gy = 0.25f * (s1.gy + s2.gy);
+        // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4, as one
+        // packed add and multiply over (x, y)
+        const float2 G = __fmul2_rn(make_float2(0.25f, 0.25f), __fadd2_rn(make_float2(s1.gx, s1.gy),
+                                                                          make_float2(s2.gx, s2.gy)));
+        Gx = G.x;
+        Gy = G.y;
     } else {
         const T *P1 = static_cast<const T *>(a.P1), *P2 = static_cast<const T *>(a.P2);
         s1 = sample_global(P1, a.H, a.W, a.pitch, x, y, -hx, -hy);
@@ -338,11 +341,15 @@ __device__ __forceinline__ void products_interior(const T *__restrict__ st1, con
     }
     const float It = s2.val - s1.val;
     const float r = (VAR && a.inc) ? -It : Gx * V0.x + Gy * V0.y - It;
-    p[0] = Gx * Gx;
-    p[1] = Gx * Gy;
+    // (Gx Gx, Gx Gy) and (Gx r, Gy r) as packed multiplies (each lane one
+    // rounding, as the scalar product)
+    const float2 g = make_float2(Gx, Gy);
+    const float2 p01 = __fmul2_rn(make_float2(Gx, Gx), g), p34 = __fmul2_rn(make_float2(r, r), g);
+    p[0] = p01.x;
+    p[1] = p01.y;
     p[2] = Gy * Gy;
-    p[3] = Gx * r;
-    p[4] = Gy * r;
+    p[3] = p34.x;
+    p[4] = p34.y;
 }
 
 // Phase 1 of a tile whose staged box lies inside the image: every pixel of
