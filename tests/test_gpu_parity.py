@@ -464,6 +464,30 @@ def test_full_1mp_stream_pair_fp32():
     compare(u, v, ou, ov, nd, label="1Mp stream pair fp32")
 
 
+def test_full_1mp_stream_sequence_in_the_benchmark_launch_configuration():
+    """The 1 Mp stream as the benchmark times it: ofv_compute_sequence with
+    the default parameters (8 pairs per launch on the group streams).  17
+    frames are two full groups; the first and last pair of each group are
+    compared with the oracle, every field must be finite."""
+    H, W, n = 1024, 1024, 17
+    F = synth.stream_frames(H, W, n, seed=2)
+    h = ofv.ofv_create(H, W, ofv.ofv_default_params())
+    try:
+        fr = torch.from_numpy(F).to(DEV)
+        u = torch.empty((n - 1, H, W), dtype=torch.float32, device=DEV)
+        v = torch.empty_like(u)
+        ofv.ofv_compute_sequence(h, n, fr, H * W * 2, u, v, H * W)
+        torch.cuda.synchronize()
+        u, v = u.cpu().numpy(), v.cpu().numpy()
+    finally:
+        ofv.ofv_destroy(h)
+    assert np.isfinite(u).all() and np.isfinite(v).all()
+    for k in (0, 7, 8, 15):
+        ou, ov, nd, _ = oracle_flow(F[k], F[k + 1])
+        compare(u[k], v[k], ou, ov, nd, label=f"1Mp stream sequence pair {k}",
+                sens=fp32_sensitivity(F[k], F[k + 1]))
+
+
 def test_full_4mp_turbulence_fp16_and_fp32():
     I1, I2, _, _ = synth.turbulence_pair(2048, 2048, seed=3)
     ou, ov, nd, _ = oracle_flow(I1, I2)
