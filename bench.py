@@ -699,6 +699,18 @@ def batched_uneven(ofv, torch, synth, dev, stream, n_pairs=64, reps=5):
             ofv.ofv_compute_batched(h, pairs, stream)
         torch.cuda.synchronize()
         batched = n_pairs * reps / (time.perf_counter() - t0)
+        # the same batch recorded as a CUDA graph and replayed (no host work)
+        g = ofv.ofv_graph_create_batched(h, pairs)
+        try:
+            ofv.ofv_graph_launch(g, stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                ofv.ofv_graph_launch(g, stream)
+            torch.cuda.synchronize()
+            graph = n_pairs * reps / (time.perf_counter() - t0)
+        finally:
+            ofv.ofv_graph_destroy(g)
     finally:
         ofv.ofv_destroy(h)
     handles = {c: ofv.ofv_create(*classes[c], ofv.ofv_default_params()) for c in content}
@@ -743,10 +755,12 @@ def batched_uneven(ofv, torch, synth, dev, stream, n_pairs=64, reps=5):
         for hh in bh.values():
             ofv.ofv_destroy(hh)
     return {"pairs": n_pairs, "mpix_per_batch": mpix, "batched_fields_per_s": batched,
+            "batched_graph_fields_per_s": graph,
             "batched_mvectors_per_s": batched * mpix / n_pairs, "sequential_fields_per_s": sequential,
             "backward_pairs_per_s": backward, "backward_mvectors_per_s": backward * mpix / n_pairs,
             "tuning": tune, "timing": "host wall clock over 5 batches, synchronised at the end (batched calls "
-                                      "after the tuning one are asynchronous)"}
+                                      "after the tuning one are asynchronous; the graph rate replays the "
+                                      "recorded batch 5 times the same way)"}
 
 
 def cpu_baseline(frames_h):

@@ -355,6 +355,26 @@ ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float
 ofv_status ofv_graph_launch(ofv_graph *g, ofv_stream_t s);
 ofv_status ofv_graph_destroy(ofv_graph *g);
 
+/* The batched form for camera streams of uneven size (Sec. 6: several
+ * cameras or streams at fixed rates): records ofv_compute_batched(h, n,
+ * pairs) -- the ingest and reduce launches of every frame and the one
+ * persistent launch of all (level, iteration, tile) units -- into a CUDA
+ * graph, so a new set of pairs written into the same buffers costs one
+ * ofv_graph_launch and no host work.  pairs is a HOST array as for
+ * ofv_compute_batched; its buffers are the ones every launch reads and
+ * writes.  Synchronises the device, then runs the batch eagerly (tuning a new
+ * signature, as ofv_compute_batched does) before recording it.  The graph
+ * takes the handle's batch workspace and frees it in ofv_graph_destroy;
+ * later batched calls of the handle allocate a new one, so they and the
+ * graph do not overwrite each other's data.  The handle (its parameters,
+ * pre-filter weights and error words) must outlive the graph, and launches
+ * of graphs and compute calls of one handle must be ordered (one stream).
+ * Errors as ofv_compute_batched; nothing is recorded on failure and *out is
+ * NULL.  A dependency wait that expires in a replayed launch sets the
+ * handle's error word: the handle's next batched call returns
+ * OFV_ERR_TIMEOUT. */
+ofv_status ofv_graph_create_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_graph **out);
+
 /* Dimensions of pyramid level l (0 = full resolution). */
 ofv_status ofv_level_shape(const ofv_handle *h, int level, int *H, int *W);
 

@@ -19,7 +19,8 @@ from . import build as _build
 __all__ = [
     "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_set_mask",
     "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host",
-    "ofv_compute_noalloc", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_probe",
+    "ofv_compute_noalloc", "ofv_compute_batched", "ofv_batch_tuning", "ofv_graph_create",
+    "ofv_graph_create_batched", "ofv_graph_launch", "ofv_graph_destroy", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_probe",
     "ofv_debug_fail_alloc", "ofv_debug_poison", "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
@@ -37,7 +38,7 @@ OFV_NOALLOC_SCRATCH_BYTES = 64 << 20
 EXPORTED_SYMBOLS = [
     "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_set_mask", "ofv_compute",
     "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host", "ofv_compute_noalloc",
-    "ofv_graph_create", "ofv_graph_launch",
+    "ofv_graph_create", "ofv_graph_create_batched", "ofv_graph_launch",
     "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
     "ofv_vorticity", "ofv_recirculation_area", "ofv_probe", "ofv_debug_fail_alloc", "ofv_debug_poison",
     "ofv_level_shape",
@@ -81,6 +82,7 @@ def _load_library():
         "ofv_compute_sequence_host": ([P, I, P, Z, P, P, Z, P], I),
         "ofv_compute_noalloc": ([I, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
         "ofv_graph_create": ([P, P, P, P, P, ctypes.POINTER(P)], I),
+        "ofv_graph_create_batched": ([P, I, P, ctypes.POINTER(P)], I),
         "ofv_graph_launch": ([P, P], I),
         "ofv_graph_destroy": ([P], I),
         "ofv_compute_batched": ([P, I, P, P], I),
@@ -245,9 +247,7 @@ class Pair(ctypes.Structure):
                 ("u", ctypes.c_void_p), ("v", ctypes.c_void_p)]
 
 
-def ofv_compute_batched(h: int, pairs, stream=None):
-    """pairs: sequence of (I1, I2, u, v) CUDA tensors (each H x W) or Pair
-    structures; all pairs of the batch run in one persistent launch."""
+def _pair_array(pairs):
     arr = (Pair * len(pairs))()
     for k, p in enumerate(pairs):
         if isinstance(p, Pair):
@@ -256,8 +256,25 @@ def ofv_compute_batched(h: int, pairs, stream=None):
             I1, I2, u, v = p
             H, W = I1.shape[-2], I1.shape[-1]
             arr[k] = Pair(H, W, _addr(I1), _addr(I2), _addr(u), _addr(v))
+    return arr
+
+
+def ofv_compute_batched(h: int, pairs, stream=None):
+    """pairs: sequence of (I1, I2, u, v) CUDA tensors (each H x W) or Pair
+    structures; all pairs of the batch run in one persistent launch."""
+    arr = _pair_array(pairs)
     _check(_lib.ofv_compute_batched(h, len(pairs), ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
            "ofv_compute_batched")
+
+
+def ofv_graph_create_batched(h: int, pairs) -> int:
+    """Record ofv_compute_batched(h, pairs) for these fixed buffers as a CUDA
+    graph (it owns its workspace); replay it with ofv_graph_launch."""
+    arr = _pair_array(pairs)
+    g = ctypes.c_void_p()
+    _check(_lib.ofv_graph_create_batched(h, len(pairs), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(g)),
+           "ofv_graph_create_batched")
+    return g.value
 
 
 def ofv_batch_tuning(h: int):

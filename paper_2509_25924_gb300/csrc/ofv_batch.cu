@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <new>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -87,11 +88,12 @@ void build_schedule(int schedule, int S, int n, const std::vector<std::vector<in
     }
 }
 
-}  // namespace
-
-extern "C" {
-
-ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t stream)
+// One batch on stream cs.  record: the pass is being captured into a CUDA
+// graph right after an eager pass of the same batch on the same handle, so
+// every descriptor, the schedule and the tensor maps are already in the arena
+// and the tuning is cached: the pass issues device work only (no host copies,
+// no arena growth, no timing) and fails if anything would have to be uploaded.
+ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t stream, bool record)
 {
     if (!h || !pairs) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: handle or pairs is NULL");
     if (n < 1 || n > 32767)
@@ -186,6 +188,7 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     const size_t red_off = off;
     off = align_up(off + sizeof(ReduceArgs) * 2 * (size_t)n * (L > 1 ? L - 1 : 1), 256);
     if (off > h->batch_bytes) {
+        if (record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs a prepared arena");
         if (h->batch_arena) {
             e = cudaStreamSynchronize(cs);
             cudaFree(h->batch_arena);
@@ -240,10 +243,13 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
             }
         const IngestArgs *ia_d = reinterpret_cast<const IngestArgs *>(base + ing_off);
         const ReduceArgs *ra_d = reinterpret_cast<const ReduceArgs *>(base + red_off);
-        e = cudaMemcpyAsync(base + ing_off, ia.data(), sizeof(IngestArgs) * ia.size(), cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess && L > 1)
-            e = cudaMemcpyAsync(base + red_off, ra.data(), sizeof(ReduceArgs) * ra.size(), cudaMemcpyHostToDevice, cs);
-        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading frame descriptors");
+        if (!record) {
+            e = cudaMemcpyAsync(base + ing_off, ia.data(), sizeof(IngestArgs) * ia.size(), cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess && L > 1)
+                e = cudaMemcpyAsync(base + red_off, ra.data(), sizeof(ReduceArgs) * ra.size(), cudaMemcpyHostToDevice,
+                                    cs);
+            if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading frame descriptors");
+        }
         e = launch_ingest_list(ia.data(), ia_d, 2 * n, p.storage, cs);
         if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: ingest launch");
         for (int l = 1; l < L; ++l) {
@@ -271,8 +277,10 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
         b.v = pairs[i].v;
         b.vpitch = vpitch[i];
     }
-    e = cudaMemcpyAsync(base + pairs_off, bp.data(), sizeof(BatchPair) * n, cudaMemcpyHostToDevice, cs);
-    if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading pair descriptors");
+    if (!record) {
+        e = cudaMemcpyAsync(base + pairs_off, bp.data(), sizeof(BatchPair) * n, cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading pair descriptors");
+    }
 
     // layout of the arena: its address, the pair sizes in order and the
     // parameters fix every address in it
@@ -300,6 +308,7 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
             }
         }
         if (use_tma && h->batch_maps_key != mkey) {
+            if (record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs uploaded tensor maps");
             e = cudaMemcpyAsync(base + tmaps_off, mit->second.data(), sizeof(CUtensorMap) * mit->second.size(),
                                 cudaMemcpyHostToDevice, cs);
             if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading tensor maps");
@@ -309,7 +318,6 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
 
     int dev = h->device, sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int occ = std::max(1, queue_occupancy(p.storage, KR, p.window == OFV_WINDOW_GAUSS || p.increment_form));
 
     // batch signature for the autotuner
     std::vector<std::pair<int, int>> sizes;
@@ -322,7 +330,9 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
     std::vector<BatchTune> cands;
     auto it = h->tune.find(key);
     const bool tuning = it == h->tune.end();
+    if (tuning && record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs a tuned batch");
     if (tuning) {
+        const int occ = std::max(1, queue_occupancy(p.storage, KR, p.window == OFV_WINDOW_GAUSS || p.increment_form));
         for (int sch : {0, 8})
             for (int c : {occ, occ - 1})
                 if (c >= 1 && (sch == 0 || sch < n)) cands.push_back(BatchTune{sch, c, 0.0});
@@ -372,6 +382,7 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
         const std::string skey = mkey + "#" + std::to_string(cands[c].schedule);
         e = cudaSuccess;
         if (h->batch_sched_key != skey) {  // the schedule of this layout is not in the arena yet
+            if (record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs the uploaded schedule");
             e = cudaMemcpyAsync(base + goff_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice, cs);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(base + grp_off, group.data(), sizeof(int2) * group.size(), cudaMemcpyHostToDevice,
@@ -403,8 +414,76 @@ ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_
         h->tune[key] = cands[best];
         // the last candidate's outputs are already in place (all compute the same fields)
     }
-    h->last_tune = tuning ? cands[best] : cands[0];
-    h->last_tuned = tuning ? 1 : 0;
+    if (!record) {
+        h->last_tune = tuning ? cands[best] : cands[0];
+        h->last_tuned = tuning ? 1 : 0;
+    }
+    return OFV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t stream)
+{
+    return batched_impl(h, n, pairs, stream, false);
+}
+
+ofv_status ofv_graph_create_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_graph **out)
+{
+    if (!out) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_graph_create_batched: out is NULL");
+    *out = nullptr;
+    if (!h || !pairs) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_graph_create_batched: handle or pairs is NULL");
+    DevGuard dg(h->device);
+    // the eager passes use the handle's arena on a stream of their own:
+    // earlier work on the handle must be finished
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_graph_create_batched: waiting for earlier work");
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_graph_create_batched: creating the capture stream");
+    // eager pass: sizes the arena, uploads every descriptor, tunes a new
+    // signature; after tuning a second pass uploads the chosen schedule
+    ofv_status st = batched_impl(h, n, pairs, (ofv_stream_t)cs, false);
+    if (st == OFV_OK && h->last_tuned) st = batched_impl(h, n, pairs, (ofv_stream_t)cs, false);
+    if (st == OFV_OK) {
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) st = cuda_fail_msg(e, "ofv_graph_create_batched: eager pass");
+    }
+    cudaGraph_t graph = nullptr;
+    if (st == OFV_OK) {
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            st = cuda_fail_msg(e, "ofv_graph_create_batched: beginning stream capture");
+        } else {
+            st = batched_impl(h, n, pairs, (ofv_stream_t)cs, true);
+            e = cudaStreamEndCapture(cs, &graph);
+            if (st == OFV_OK && e != cudaSuccess) st = cuda_fail_msg(e, "ofv_graph_create_batched: ending stream capture");
+        }
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (st == OFV_OK) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) st = cuda_fail_msg(e, "ofv_graph_create_batched: instantiating the graph");
+    }
+    cudaStreamDestroy(cs);
+    ofv_graph *gr = nullptr;
+    if (st == OFV_OK) {
+        gr = new (std::nothrow) ofv_graph{h, graph, exec, h->batch_arena};
+        if (!gr) st = fail_msg(OFV_ERR_ALLOC, "ofv_graph_create_batched: host allocation of the graph handle failed");
+    }
+    if (st != OFV_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    // the graph takes the arena: later batches of the handle get a new one
+    h->batch_arena = nullptr;
+    h->batch_bytes = 0;
+    h->batch_sched_key.clear();
+    h->batch_maps_key.clear();
+    *out = gr;
     return OFV_OK;
 }
 

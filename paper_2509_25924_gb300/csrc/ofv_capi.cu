@@ -1017,12 +1017,6 @@ ofv_status ofv_compute_sequence_host(ofv_handle *h, int n_frames, const void *fr
 
 }  // extern "C"
 
-struct ofv_graph {
-    ofv_handle *h;
-    cudaGraph_t graph;
-    cudaGraphExec_t exec;
-};
-
 extern "C" {
 
 ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float *u, float *v, ofv_graph **out)
@@ -1070,7 +1064,7 @@ ofv_status ofv_graph_create(ofv_handle *h, const void *I1, const void *I2, float
         if (graph) cudaGraphDestroy(graph);
         return st;
     }
-    ofv_graph *gr = new (std::nothrow) ofv_graph{h, graph, exec};
+    ofv_graph *gr = new (std::nothrow) ofv_graph{h, graph, exec, nullptr};
     if (!gr) {
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
@@ -1096,6 +1090,7 @@ ofv_status ofv_graph_destroy(ofv_graph *g)
     DeviceGuard dg(g->h->device);
     cudaGraphExecDestroy(g->exec);
     cudaGraphDestroy(g->graph);
+    if (g->arena) cudaFree(g->arena);  // waits for the graph's last launch
     delete g;
     return OFV_OK;
 }

@@ -108,6 +108,16 @@ struct ofv_handle {
     std::string batch_sched_key, batch_maps_key;
 };
 
+// A recorded CUDA graph (ofv_graph_create, ofv_graph_create_batched).  A
+// batched graph owns the arena its launches read (pyramids, fields and the
+// batch descriptors); a single-pair graph uses the handle's workspace.
+struct ofv_graph {
+    ofv_handle *h;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    void *arena;
+};
+
 namespace ofv {
 // Device allocation of the library's workspaces: cudaMalloc, unless a
 // failure was scheduled by ofv_debug_fail_alloc (then

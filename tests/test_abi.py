@@ -183,3 +183,9 @@ def test_batched_rejects_bad_arguments_on_the_host():
     lib.ofv_compute_batched.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.ofv_compute_batched.restype = ctypes.c_int
     assert lib.ofv_compute_batched(None, 1, None, None) == ofv.OFV_ERR_INVALID_ARG
+    lib.ofv_graph_create_batched.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.ofv_graph_create_batched.restype = ctypes.c_int
+    out = ctypes.c_void_p(1)
+    assert lib.ofv_graph_create_batched(None, 1, None, None) == ofv.OFV_ERR_INVALID_ARG
+    assert lib.ofv_graph_create_batched(None, 1, None, ctypes.byref(out)) == ofv.OFV_ERR_INVALID_ARG
+    assert out.value is None  # *out is cleared on failure

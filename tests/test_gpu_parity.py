@@ -551,6 +551,55 @@ def test_batched_uneven_sizes_match_per_pair_compute_and_oracle(storage):
         ofv.ofv_destroy(h)
 
 
+def test_batched_graph_replays_the_batch_and_keeps_its_own_workspace():
+    """ofv_graph_create_batched records the batch; a replay gives bitwise the
+    eager batch's fields, follows new frames written into the same buffers,
+    and is not disturbed by eager batches of the same handle in between
+    (they run in a workspace of their own)."""
+    sizes = [(300, 420), (512, 640), (96, 130), (777, 1001), (200, 232)]
+    data = _uneven_pairs(sizes)
+    p = ofv.ofv_default_params(**PARAMS)
+    h = ofv.ofv_create(64, 64, p)
+    g = None
+    nan = float("nan")
+    try:
+        bufs = []
+        for (I1, I2), (H, W) in zip(data, sizes):
+            t1 = torch.from_numpy(I1).to(DEV); t2 = torch.from_numpy(I2).to(DEV)
+            bufs.append((t1, t2, torch.full((H, W), nan, device=DEV), torch.full((H, W), nan, device=DEV)))
+        ofv.ofv_compute_batched(h, bufs)
+        torch.cuda.synchronize()
+        ref = [(u.clone(), v.clone()) for _, _, u, v in bufs]
+
+        g = ofv.ofv_graph_create_batched(h, bufs)
+        for _, _, u, v in bufs:
+            u.fill_(nan); v.fill_(nan)
+        ofv.ofv_graph_launch(g)
+        torch.cuda.synchronize()
+        for (_, _, u, v), (ru, rv), hw in zip(bufs, ref, sizes):
+            assert torch.equal(u, ru) and torch.equal(v, rv), f"replay {hw}"
+
+        # new frames into the same buffers: the frames swapped
+        for t1, t2, _, _ in bufs:
+            tmp = t1.clone(); t1.copy_(t2); t2.copy_(tmp)
+        swapped = [(t1.clone(), t2.clone(), torch.full_like(u, nan), torch.full_like(v, nan)) for t1, t2, u, v in bufs]
+        ofv.ofv_compute_batched(h, swapped)  # eager, on the handle's new workspace
+        # an eager batch of another signature in between
+        other = [(bufs[0][0], bufs[0][1], torch.empty_like(bufs[0][2]), torch.empty_like(bufs[0][3]))]
+        ofv.ofv_compute_batched(h, other)
+        ofv.ofv_graph_launch(g)
+        torch.cuda.synchronize()
+        for (_, _, u, v), (_, _, su, sv), hw in zip(bufs, swapped, sizes):
+            assert torch.equal(u, su) and torch.equal(v, sv), f"replay after new frames {hw}"
+        I1, I2 = data[2]
+        ou, ov, nd, _ = oracle_flow(I2, I1)
+        compare(bufs[2][2].cpu().numpy(), bufs[2][3].cpu().numpy(), ou, ov, nd, label="batched graph, swapped 96x130")
+    finally:
+        if g is not None:
+            ofv.ofv_graph_destroy(g)
+        ofv.ofv_destroy(h)
+
+
 def test_batched_wait_timeout_is_reported_and_device_stays_usable():
     """The persistent launch's dependency wait is bounded: a unit that waits
     on a counter nothing increments gives up after the time limit, records
