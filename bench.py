@@ -130,6 +130,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def workload_config(nframes: int, ws: int) -> dict:
+    """The headline workload, named the same way on both arms."""
+    N = H1 * W1
+    npairs = nframes - 1
+    return {"workload": f"1024x1024 u16 12-bit Rankine+shift stream of {nframes} frames ({npairs} pairs), "
+                        "PSL2 KR4 IT3, FP32 storage, fused kernels, ofv_compute_sequence",
+            "pairs_total": npairs * ws, "pairs_per_rank": npairs, "parallelism": f"replicas{ws}",
+            "l2": f"inputs ({nframes * N * 2 / 1e9:.2f} GB of frames) larger than L2" if nframes * N * 2 > 129e6
+            else "inputs smaller than L2"}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -156,8 +167,8 @@ def run_reference(args, ws, rank):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "1024x1024 u16 12-bit Rankine+shift stream, PSL2 KR4 IT3",
-                   "step": "one image pair (bounded sample of the 1000-pair stream)"},
+        "config": dict(workload_config(args.frames, 1),
+                       step="one image pair of the stream (a bounded sample of it: the oracle at FP64)"),
         "cpu_baseline": {"value": value, "unit": "fields/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} pairs of the 1 Mp stream, FP64, OpenMP over rows"},
         "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -298,10 +309,7 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"1024x1024 u16 12-bit Rankine+shift stream of {nframes} frames ({npairs} pairs), "
-                               "PSL2 KR4 IT3, FP32 storage, fused kernels, ofv_compute_sequence",
-                   "pairs_total": npairs * ws, "pairs_per_rank": npairs, "parallelism": f"replicas{ws}",
-                   "l2": f"inputs ({nframes * N * 2 / 1e9:.2f} GB of frames) larger than L2" if nframes * N * 2 > 129e6 else "inputs smaller than L2"},
+        "config": workload_config(nframes, ws),
         "mvectors_per_s": value * N / 1e6,
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
