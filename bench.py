@@ -367,7 +367,11 @@ def e2e(args, ofv, torch, h, frames_h, dev, stream, barrier, max_over_ranks, ws)
     for _ in range(max(args.warmup, 1)):  # the same W warm-up steps as the device-resident leg
         run()
     torch.cuda.synchronize()
-    steps = max(1, min(args.steps, 5))
+    # 20 steps (about 0.55 s): single steps of this host-timed leg are
+    # sometimes held up for tens of ms (seen as 69 and 79 ms against 27 ms,
+    # with no sampler running), and a longer window weighs such a stall
+    # by its share of the sustained run
+    steps = max(1, min(args.steps, 20))
     barrier()
     t0 = time.perf_counter()
     c0 = time.process_time()
