@@ -189,3 +189,51 @@ def test_batched_rejects_bad_arguments_on_the_host():
     assert lib.ofv_graph_create_batched(None, 1, None, None) == ofv.OFV_ERR_INVALID_ARG
     assert lib.ofv_graph_create_batched(None, 1, None, ctypes.byref(out)) == ofv.OFV_ERR_INVALID_ARG
     assert out.value is None  # *out is cleared on failure
+
+
+def _prototypes():
+    """name -> list of parameter declarations of every ofv_* function in include/*.h."""
+    out = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(ofv_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", text):
+            params = [p.strip() for p in m.group(2).split(",")]
+            out[m.group(1)] = [] if params in ([""], ["void"]) else params
+    return out
+
+
+def _c_kind(decl):
+    if "*" in decl or "ofv_stream_t" in decl:
+        return "pointer"
+    if "size_t" in decl:
+        return "size_t"
+    if "double" in decl or "float" in decl:
+        return "float"
+    return "int"  # int and the enum types
+
+
+def _ctypes_kind(t):
+    if t is ctypes.c_void_p or t is ctypes.c_char_p or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "pointer"
+    if t is ctypes.c_size_t:
+        return "size_t"
+    if t in (ctypes.c_float, ctypes.c_double):
+        return "float"
+    return "int"
+
+
+def test_binding_argtypes_match_the_header_prototypes():
+    """Each bound entry point takes as many arguments as its prototype, of
+    the same kinds (pointer, size_t, int, floating point)."""
+    protos = _prototypes()
+    assert protos, "no prototypes found"
+    lib = ofv._lib
+    for name, params in protos.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None, f"{name}: no argtypes set"
+        assert len(argtypes) == len(params), f"{name}: {len(argtypes)} argtypes, prototype has {len(params)}"
+        for k, (decl, t) in enumerate(zip(params, argtypes)):
+            assert _c_kind(decl) == _ctypes_kind(t), f"{name} argument {k} ({decl!r}) bound as {t}"
