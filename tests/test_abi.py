@@ -53,20 +53,22 @@ def test_defaults_follow_the_documented_values():
     assert (p.window, p.window_sigma, p.increment_form, p.warm_start) == (ofv.OFV_WINDOW_BOX, 0.0, 0, 0)
 
 
-def test_params_struct_layout_matches_the_header(tmp_path):
-    """The ctypes mirror of ofv_params has the C struct's size and field
-    offsets (compiled against include/ofv.h with the host compiler)."""
-    names = [f[0] for f in ofv.Params._fields_]
+@pytest.mark.parametrize("cname,mirror", [("ofv_params", "Params"), ("ofv_pair", "Pair")])
+def test_struct_layout_matches_the_header(tmp_path, cname, mirror):
+    """The ctypes mirrors of ofv_params and ofv_pair have the C structs' size
+    and field offsets (compiled against include/ofv.h with the host compiler)."""
+    cls = getattr(ofv, mirror)
+    names = [f[0] for f in cls._fields_]
     src = tmp_path / "layout.c"
-    body = "".join(f'    printf("%zu\\n", offsetof(ofv_params, {n}));\n' for n in names)
+    body = "".join(f'    printf("%zu\\n", offsetof({cname}, {n}));\n' for n in names)
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "ofv.h"\nint main(void) {\n'
-                   '    printf("%zu\\n", sizeof(ofv_params));\n' + body + '    return 0;\n}\n')
+                   f'    printf("%zu\\n", sizeof({cname}));\n' + body + '    return 0;\n}\n')
     exe = tmp_path / "layout"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
     out = [int(x) for x in subprocess.check_output([str(exe)]).split()]
-    assert out[0] == ctypes.sizeof(ofv.Params)
-    assert out[1:] == [getattr(ofv.Params, n).offset for n in names]
+    assert out[0] == ctypes.sizeof(cls)
+    assert out[1:] == [getattr(cls, n).offset for n in names]
 
 
 @pytest.mark.parametrize("field,value", [
