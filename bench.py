@@ -167,7 +167,7 @@ def run_reference(args, ws, rank):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(args.frames, 1),
+        "config": dict(workload_config(args.frames, ws),
                        step="one image pair of the stream (a bounded sample of it: the oracle at FP64)"),
         "cpu_baseline": {"value": value, "unit": "fields/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} pairs of the 1 Mp stream, FP64, OpenMP over rows"},

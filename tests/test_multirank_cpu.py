@@ -77,3 +77,8 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the same workload config as the GPU arm's line at this rank count
+    import bench
+    cfg = dict(d["config"])
+    cfg.pop("step")
+    assert cfg == bench.workload_config(bench.FRAMES1, 2)
