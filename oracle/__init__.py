@@ -87,6 +87,8 @@ def _load():
             lib.orc_vorticity.argtypes = [I, I, P, P, P]
             lib.orc_recirculation_count.argtypes = [I, I, P, P]
             lib.orc_recirculation_count.restype = ctypes.c_int64
+            lib.orc_num_threads.argtypes = []
+            lib.orc_num_threads.restype = I
             _lib = lib
     return _lib
 
@@ -319,6 +321,11 @@ def flow_grad(I1, I2, params: Params, gu, gv):
     if rc:
         raise RuntimeError(f"orc_flow_grad failed ({rc})")
     return g1, g2, (gw.reshape(5, 5) if params.prefilter is not None else None), u, v
+
+
+def num_threads() -> int:
+    """Threads the oracle's OpenMP loops run on (OMP_NUM_THREADS, else the host's cores)."""
+    return int(_load().orc_num_threads())
 
 
 def vorticity(u, v):

@@ -53,6 +53,8 @@ int orc_flow(int H, int W, const double *raw1, const double *raw2, const orc_par
              double *u, double *v, double *ndet, unsigned char *guard0);
 void orc_vorticity(int H, int W, const double *u, const double *v, double *omega);
 int64_t orc_recirculation_count(int H, int W, const double *u, const unsigned char *mask);
+/* threads the OpenMP loops of the oracle run on (1 when built without OpenMP) */
+int orc_num_threads(void);
 /* reverse mode (ofv_oracle_adjoint.c): gw25 accumulates (zero it first) */
 int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const orc_params *p,
                   const double *gu, const double *gv, double *g1, double *g2, double *gw25,

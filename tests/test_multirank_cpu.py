@@ -76,6 +76,7 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] == 4  # the threads the oracle ran on (OMP_NUM_THREADS above)
     assert d["e2e"]["h2d_bytes_per_step"] == 0
     # the same workload config as the GPU arm's line at this rank count
     import bench
