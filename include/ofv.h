@@ -246,17 +246,21 @@ ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2, const flo
 
 /* ---- allocation-free variant -------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
- * cannot call cudaMalloc: code that records work into a CUDA graph by stream
- * capture and must not add allocation nodes, host applications whose device
- * memory is owned by another allocator, and real-time loops that forbid any
- * allocation once running.
+ * cannot call cudaMalloc: host applications whose device memory belongs to
+ * another allocator (a framework's caching allocator, or a pool sized at
+ * start-up that a cudaMalloc behind its back would starve), and real-time
+ * acquisition loops that forbid allocation once running (cudaMalloc may
+ * block the host thread and synchronise the device).
  *
- * ofv_compute_noalloc computes the same field as ofv_create + ofv_compute
- * with the same kernels (fused path only; params->path must be
- * OFV_PATH_FUSED, else OFV_ERR_UNSUPPORTED) but allocates nothing: its
- * workspace is a fixed device array of OFV_NOALLOC_SCRATCH_BYTES inside the
- * library, which every GPU that loads the library holds until the process
- * exits.  The caller passes the frames I1, I2 (H x W, params->input type),
+ * ofv_compute_noalloc computes the same field as ofv_create + ofv_compute,
+ * bitwise, with the same iteration kernels (fused path only; params->path
+ * must be OFV_PATH_FUSED, else OFV_ERR_UNSUPPORTED), but allocates nothing:
+ * its workspace is a fixed device array of OFV_NOALLOC_SCRATCH_BYTES inside
+ * the library, which every GPU that loads the library holds until the
+ * process exits.  It keeps no TMA tensor maps, so the iteration kernel
+ * stages its image tiles by cp.async (same arithmetic, so the same field).
+ * params->max_batch and params->warm_start are range-checked as ofv_create
+ * checks them and otherwise ignored.  The caller passes the frames I1, I2 (H x W, params->input type),
  * the outputs u, v (H x W float) and, when params->prefilter = 1, the 25
  * pre-filter weights w25 (device, row-major 5x5; may be NULL otherwise).
  * A request whose workspace would exceed the array (about 27 bytes per pixel

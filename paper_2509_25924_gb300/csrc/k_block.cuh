@@ -302,54 +302,75 @@ __device__ __forceinline__ Sample2 bilin_staged2(const T *__restrict__ rm1, cons
     return s;
 }
 
+// Bilinear value and doubled gradient (undivided central differences) of a
+// staged 4x4 neighbourhood for the two frames at once, with each
+// interpolation written (1 - f) a + f b, which is exact at f = 0 and f = 1:
+// a sample taken at the tap to the left with fraction 1 equals the sample at
+// the next tap with fraction 0.  rm1, rm2 point at the tap left of column x0
+// in row y0-1 of each frame's staged tile; w0 = 1 - f and w1 = f hold the
+// two frames' weights (lane x frame 1, lane y frame 2); each lane rounds as
+// the scalar operations would.
+template <typename T, int SP>
+__device__ __forceinline__ Sample2 bilin_weighted2(const T *__restrict__ rm1, const T *__restrict__ rm2, float2 wx0,
+                                                   float2 wx1, float2 wy0, float2 wy1)
+{
+    auto ld2 = [&](int off) { return make_float2(to_f(rm1[off]), to_f(rm2[off])); };
+    auto lerp = [](float2 w0, float2 w1, float2 a, float2 b) { return fma2(w1, b, __fmul2_rn(w0, a)); };
+    const float2 e0 = ld2(1), e1 = ld2(2);
+    const float2 q00 = ld2(SP), q01 = ld2(SP + 1), q02 = ld2(SP + 2), q03 = ld2(SP + 3);
+    const float2 q10 = ld2(2 * SP), q11 = ld2(2 * SP + 1), q12 = ld2(2 * SP + 2), q13 = ld2(2 * SP + 3);
+    const float2 e2 = ld2(3 * SP + 1), e3 = ld2(3 * SP + 2);
+    Sample2 s;
+    const float2 v0 = lerp(wx0, wx1, q01, q02), v1 = lerp(wx0, wx1, q11, q12);
+    s.val = lerp(wy0, wy1, v0, v1);
+    const float2 gx0 = lerp(wx0, wx1, sub2(q02, q00), sub2(q03, q01));
+    const float2 gx1 = lerp(wx0, wx1, sub2(q12, q10), sub2(q13, q11));
+    s.gx = lerp(wy0, wy1, gx0, gx1);
+    const float2 vm = lerp(wx0, wx1, e0, e1), vp = lerp(wx0, wx1, e2, e3);
+    s.gy = lerp(wy0, wy1, sub2(v1, vm), sub2(vp, v0));
+    return s;
+}
+
 // Products of one pixel (x, y) of a tile whose staged region lies inside
 // the image: no clamping or border remap is needed while the warp stays
-// within REACH px.  The frame-1 offset -h and frame-2 offset +h share their
-// fractional part: floor(-h) = -floor(h) - 1 and frac(-h) = 1 - frac(h)
-// unless h is an integer.  Farther warps take the general sampler.
+// within REACH px.  Frame 2 samples at k + h with integer part (ix, iy) =
+// floor(h) and fraction f; frame 1 at k - h, taken as integer part
+// -(ix, iy) - 1 with fraction 1 - f, which is floor(-h) and its fraction
+// unless a component of h is an integer, where the weight 1 on the next tap
+// gives the same sample exactly.  Both stencils then lie within REACH + 1 px
+// and one integer test checks both.  Farther warps take the general sampler.
 template <typename T, int SP, bool VAR = false>
 __device__ __forceinline__ void products_interior(const T *__restrict__ st1, const T *__restrict__ st2, int sx0,
                                                   int sy0, const IterArgs &a, int x, int y, float2 V0, float p[5])
 {
     const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
     const float flx = floorf(hx), fly = floorf(hy);
-    Sample s1, s2;
-    float Gx, Gy;
-    if (flx >= -kBlockReach && flx <= kBlockReach - 1 && fly >= -kBlockReach && fly <= kBlockReach - 1) {
-        const int ix = (int)flx, iy = (int)fly;
+    const int ix = (int)flx, iy = (int)fly;
+    float Gx, Gy, It;
+    if (((unsigned)(ix + kBlockReach) | (unsigned)(iy + kBlockReach)) < (unsigned)(2 * kBlockReach)) {
         const float fx2 = hx - flx, fy2 = hy - fly;
-        const bool zx = fx2 == 0.f, zy = fy2 == 0.f;
-        const int ix1 = zx ? -ix : -ix - 1, iy1 = zy ? -iy : -iy - 1;
-        const float fx1 = zx ? 0.f : 1.f - fx2, fy1 = zy ? 0.f : 1.f - fy2;
-        const int base = (y - 1 - sy0) * SP + (x - 1 - sx0);
-        const Sample2 s12 = bilin_staged2<T, SP>(st1 + base + iy1 * SP + ix1, st2 + base + iy * SP + ix,
-                                                 make_float2(fx1, fx2), make_float2(fy1, fy2));
-        s1 = Sample{s12.val.x, s12.gx.x, s12.gy.x};
-        s2 = Sample{s12.val.y, s12.gx.y, s12.gy.y};
-        // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4, as one
-        // packed add and multiply over (x, y)
-        const float2 G = __fmul2_rn(make_float2(0.25f, 0.25f), __fadd2_rn(make_float2(s1.gx, s1.gy),
-                                                                          make_float2(s2.gx, s2.gy)));
-        Gx = G.x;
-        Gy = G.y;
+        const int base = (y - 1 - sy0) * SP + (x - 1 - sx0), off = iy * SP + ix;
+        const Sample2 s12 = bilin_weighted2<T, SP>(st1 + (base - off - SP - 1), st2 + (base + off),
+                                                   make_float2(fx2, 1.f - fx2), make_float2(1.f - fx2, fx2),
+                                                   make_float2(fy2, 1.f - fy2), make_float2(1.f - fy2, fy2));
+        // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4
+        Gx = 0.25f * (s12.gx.x + s12.gx.y);
+        Gy = 0.25f * (s12.gy.x + s12.gy.y);
+        It = s12.val.y - s12.val.x;
     } else {
         const T *P1 = static_cast<const T *>(a.P1), *P2 = static_cast<const T *>(a.P2);
-        s1 = sample_global(P1, a.H, a.W, a.pitch, x, y, -hx, -hy);
-        s2 = sample_global(P2, a.H, a.W, a.pitch, x, y, hx, hy);
+        const Sample s1 = sample_global(P1, a.H, a.W, a.pitch, x, y, -hx, -hy);
+        const Sample s2 = sample_global(P2, a.H, a.W, a.pitch, x, y, hx, hy);
         Gx = 0.5f * (s1.gx + s2.gx);
         Gy = 0.5f * (s1.gy + s2.gy);
+        It = s2.val - s1.val;
     }
-    const float It = s2.val - s1.val;
     const float r = (VAR && a.inc) ? -It : Gx * V0.x + Gy * V0.y - It;
-    // (Gx Gx, Gx Gy) and (Gx r, Gy r) as packed multiplies (each lane one
-    // rounding, as the scalar product)
-    const float2 g = make_float2(Gx, Gy);
-    const float2 p01 = __fmul2_rn(make_float2(Gx, Gx), g), p34 = __fmul2_rn(make_float2(r, r), g);
-    p[0] = p01.x;
-    p[1] = p01.y;
+    p[0] = Gx * Gx;
+    p[1] = Gx * Gy;
     p[2] = Gy * Gy;
-    p[3] = p34.x;
-    p[4] = p34.y;
+    p[3] = Gx * r;
+    p[4] = Gy * r;
 }
 
 // Phase 1 of a tile whose staged box lies inside the image: every pixel of
@@ -531,7 +552,11 @@ struct SolveStoreT {
         if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr) {
             V = fetch_v0_rt<COH>(a, mode, gx, gy);
         } else {
-            const float inv = __frcp_rn(det);  // one correctly rounded reciprocal, two products
+            // reciprocal: the MUFU approximation and one Newton step
+            // y1 = y0 + y0 (1 - det y0), without a slow path
+            float y0;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(det));
+            const float inv = fmaf(y0, fmaf(-det, y0, 1.f), y0);
             V = make_float2((syy * sxr - sxy * syr) * inv, (sxx * syr - sxy * sxr) * inv);
             if (VAR && a.inc) {  // increment form: V = V0(m) + H^-1 (Sxr, Syr)
                 const float2 V0 = fetch_v0_rt<COH>(a, mode, gx, gy);

@@ -1,10 +1,10 @@
 // Allocation-free variant of ofv_compute for callers that cannot allocate
-// device memory: code running inside a CUDA stream capture that must not
-// create memory nodes, plug-in hosts whose device memory is owned by someone
+// device memory: plug-in hosts whose device memory is owned by someone
 // else's allocator, or real-time loops that forbid any allocation after
-// start-up.  It runs the same kernels as ofv_compute, but its workspace
-// (pyramids of both frames and the two ping-pong fields) lives in one
-// file-scope device array of fixed size instead of a handle's cudaMalloc.
+// start-up.  It runs the same kernels as ofv_compute (image tiles staged by
+// cp.async, as it keeps no TMA tensor maps), but its workspace (pyramids of
+// both frames and the two ping-pong fields) lives in one file-scope device
+// array of fixed size instead of a handle's cudaMalloc.
 //
 // The array is a module global: every GPU on which this library's kernels
 // are loaded holds OFV_NOALLOC_SCRATCH_BYTES of it until the process exits.
@@ -84,7 +84,8 @@ extern "C" ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *p, con
         !(p->det_abs_eps >= 0.f) || !std::isfinite(p->det_abs_eps) || !(p->norm_eps > 0.f) ||
         !std::isfinite(p->norm_eps) || (p->window != OFV_WINDOW_BOX && p->window != OFV_WINDOW_GAUSS) ||
         (p->window == OFV_WINDOW_GAUSS && (!(p->window_sigma > 0.f) || !std::isfinite(p->window_sigma))) ||
-        (p->increment_form != 0 && p->increment_form != 1))
+        (p->increment_form != 0 && p->increment_form != 1) || p->max_batch < 0 ||
+        p->max_batch > kMaxPairsPerLaunch || p->warm_start < 0 || p->warm_start > 7 * kMaxPairsPerLaunch)
         return na_fail(OFV_ERR_INVALID_ARG, "ofv_compute_noalloc: parameter out of range (see ofv_params)");
     if (p->path != OFV_PATH_FUSED)
         return na_fail(OFV_ERR_UNSUPPORTED, "ofv_compute_noalloc: only the fused path is available without allocation");
