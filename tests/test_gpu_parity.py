@@ -26,6 +26,16 @@ DEV = torch.device("cuda:0")
 FP32_TOL = 1e-3
 REDUCED_RMS_TOL = 1e-2
 NDET_MIN = 1e-3
+# Largest share of pixels the comparison may leave out (oracle determinant
+# below NDET_MIN, or moved by FP32-sized input noise).  Measured on every
+# case here with the oracle alone: 0 % for KR >= 2; 0.05-0.14 % for the KR 1
+# cases, whose 3x3 windows leave some pixels nearly singular.
+MASK_MAX = 1e-3
+MASK_MAX_KR1 = 5e-3
+
+
+def mask_max(kr):
+    return MASK_MAX_KR1 if kr == 1 else MASK_MAX
 
 _IN = {np.dtype(np.float32): ofv.OFV_IN_F32, np.dtype(np.uint16): ofv.OFV_IN_U16,
        np.dtype(np.uint8): ofv.OFV_IN_U8}
@@ -78,7 +88,7 @@ def fp32_sensitivity(I1, I2, draws=2, rel=1e-7, **kw):
     return worst
 
 
-def compare(u, v, ou, ov, nd, tol=FP32_TOL, rms_tol=None, max_masked=0.01, label="", sens=None):
+def compare(u, v, ou, ov, nd, tol=FP32_TOL, rms_tol=None, max_masked=MASK_MAX, label="", sens=None):
     m = nd >= NDET_MIN
     if sens is not None:
         m &= sens <= 0.1 * tol
@@ -222,7 +232,7 @@ def test_ragged_shapes_and_minimum_levels(H, W, psl, kr, it):
     u, v = gpu_flow(I1, I2, levels_psl=psl, kernel_radius=kr, iterations=it)
     ou, ov, nd, _ = oracle_flow(I1, I2, psl=psl, kr=kr, it=it)
     sens = fp32_sensitivity(I1, I2, psl=psl, kr=kr, it=it)
-    compare(u, v, ou, ov, nd, label=f"{H}x{W} psl={psl} kr={kr} it={it}", max_masked=0.05, sens=sens)
+    compare(u, v, ou, ov, nd, label=f"{H}x{W} psl={psl} kr={kr} it={it}", max_masked=mask_max(kr), sens=sens)
 
 
 def _random_configs(n=12, seed=20250930):
@@ -250,9 +260,9 @@ def test_random_configurations_match_oracle(H, W, psl, kr, it, d, store, seed):
     label = f"{H}x{W} psl={psl} kr={kr} it={it} d={d[0]:.2f},{d[1]:.2f} store={store}"
     if store == ofv.OFV_STORE_F32:
         sens = fp32_sensitivity(I1, I2, psl=psl, kr=kr, it=it)
-        compare(u, v, ou, ov, nd, label=label, max_masked=0.05, sens=sens)
+        compare(u, v, ou, ov, nd, label=label, max_masked=mask_max(kr), sens=sens)
     else:
-        compare(u, v, ou, ov, nd, rms_tol=REDUCED_RMS_TOL, label=label, max_masked=0.05)
+        compare(u, v, ou, ov, nd, rms_tol=REDUCED_RMS_TOL, label=label, max_masked=mask_max(kr))
 
 
 @pytest.mark.parametrize("path", [ofv.OFV_PATH_FUSED, ofv.OFV_PATH_TILE])
@@ -275,7 +285,7 @@ def test_every_window_radius(kr):
     u, v = gpu_flow(I1, I2, levels_psl=1, kernel_radius=kr, iterations=2)
     ou, ov, nd, _ = oracle_flow(I1, I2, psl=1, kr=kr, it=2)
     sens = fp32_sensitivity(I1, I2, psl=1, kr=kr, it=2) if kr <= 2 else None
-    compare(u, v, ou, ov, nd, label=f"kr={kr}", max_masked=0.05, sens=sens)
+    compare(u, v, ou, ov, nd, label=f"kr={kr}", max_masked=mask_max(kr), sens=sens)
 
 
 def test_u8_input_with_paper_benchmark_parameters():
@@ -501,7 +511,7 @@ def test_full_21mp_wake_fp32():
     I1, I2, _, inside = synth.wake_pair(seed=4)
     u, v = gpu_flow(I1, I2, **PARAMS)
     ou, ov, nd, _ = oracle_flow(I1, I2)
-    compare(u, v, ou, ov, nd, label="21Mp wake fp32", max_masked=0.05)
+    compare(u, v, ou, ov, nd, label="21Mp wake fp32")
 
 
 # --------------------------------------------------------------------------
@@ -543,7 +553,7 @@ def test_batched_uneven_sizes_match_per_pair_compute_and_oracle(storage):
             u.fill_(float("nan")); v.fill_(float("nan"))
         ofv.ofv_compute_batched(h, dev_pairs)
         assert not ofv.ofv_batch_tuning(h)["tuned"]
-        for (I1, I2), (t1, t2, u, v) in list(zip(data, dev_pairs))[:3]:
+        for (I1, I2), (t1, t2, u, v) in zip(data, dev_pairs):  # every pair against the oracle
             ou, ov, nd, _ = oracle_flow(I1, I2)
             kw = dict(rms_tol=REDUCED_RMS_TOL) if storage != ofv.OFV_STORE_F32 else {}
             compare(u.cpu().numpy(), v.cpu().numpy(), ou, ov, nd, label=f"batched {I1.shape}", **kw)
