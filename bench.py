@@ -597,10 +597,13 @@ def variants(ofv, torch, synth, dev, stream, frames, u, v, n_frames=201, reps=5)
 
 def paper_perf_set(ofv, torch, synth, dev, stream, cases=None):
     """The paper's own benchmark parameters (8-bit input, NR 2, KR 10, IT 3,
-    PSL 0/1/2) on synthetic 8-bit particle streams at 1, 4 and 21 Mp, for
-    context beside its published rates (other hardware)."""
+    PSL 0/1/2) on synthetic 8-bit particle streams at 1, 4, 10 and 21 Mp, for
+    context beside its published rates (other hardware).  The paper gives no
+    dimensions for its 10 Mp images; 5120 x 2048 is the 21 Mp camera's full
+    width at half height."""
     out = {}
-    for name, H, W, nf in cases or (("1Mp", 1024, 1024, 41), ("4Mp", 2048, 2048, 17), ("21Mp", 4096, 5120, 9)):
+    for name, H, W, nf in cases or (("1Mp", 1024, 1024, 41), ("4Mp", 2048, 2048, 17), ("10Mp", 2048, 5120, 9),
+                                    ("21Mp", 4096, 5120, 9)):
         fr = synth.stream_frames(H, W, nf, seed=7, ppp=0.05, bits=8).astype(np.uint8)
         frames = torch.from_numpy(fr).to(dev)
         u = torch.empty((nf - 1, H, W), dtype=torch.float32, device=dev)

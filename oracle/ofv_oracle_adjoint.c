@@ -221,15 +221,72 @@ static void reduce_T(int H, int W, const double *gc, double *g)
         }
 }
 
+/* Adjoint of the local normalization of Sec. 2 (step 1, orc_normalize):
+   J(m) = (I(m) - mu(m)) / s(m), s = sqrt(var(m) + eps_n^2), where mu(m) and
+   var(m) are the mean and variance of I over the in-image part B(m) of the
+   (2NR+1)^2 box centred on m, of n(m) pixels.  By the chain rule, with
+   a = dL/dJ and var = sum_B I^2 / n - mu^2,
+     dL/dI(k) = a(k) / s(k)
+                - sum_{m : k in B(m)} a(m) [1 / (s(m) n(m))
+                                            + J(m) (I(k) - mu(m)) / (s(m)^2 n(m))],
+   and k lies in B(m) exactly when m lies in B(k).  gI receives dL/dI. */
+static int normalize_T(int H, int W, const double *I, int nr, double eps_n, const double *gJ, double *gI)
+{
+    const int64_t N = (int64_t)H * W;
+    double *mu = (double *)malloc(sizeof(double) * N), *sd = (double *)malloc(sizeof(double) * N);
+    double *cnt = (double *)malloc(sizeof(double) * N);
+    if (!mu || !sd || !cnt) { free(mu); free(sd); free(cnt); return 1; }
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double sum = 0.0;
+            int n = 0;
+            for (int a = -nr; a <= nr; ++a)
+                for (int b = -nr; b <= nr; ++b) {
+                    const int ii = i + a, jj = j + b;
+                    if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
+                    sum += I[(int64_t)ii * W + jj];
+                    ++n;
+                }
+            const double m = sum / n;
+            double q = 0.0;
+            for (int a = -nr; a <= nr; ++a)
+                for (int b = -nr; b <= nr; ++b) {
+                    const int ii = i + a, jj = j + b;
+                    if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
+                    const double d = I[(int64_t)ii * W + jj] - m;
+                    q += d * d;
+                }
+            mu[(int64_t)i * W + j] = m;
+            sd[(int64_t)i * W + j] = sqrt(q / n + eps_n * eps_n);
+            cnt[(int64_t)i * W + j] = (double)n;
+        }
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            const int64_t k = (int64_t)i * W + j;
+            double g = gJ[k] / sd[k];
+            for (int a = -nr; a <= nr; ++a)
+                for (int b = -nr; b <= nr; ++b) {
+                    const int ii = i + a, jj = j + b;
+                    if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
+                    const int64_t m = (int64_t)ii * W + jj;
+                    const double Jm = (I[m] - mu[m]) / sd[m];
+                    g -= gJ[m] / (sd[m] * cnt[m]) + gJ[m] * Jm * (I[k] - mu[m]) / (sd[m] * sd[m] * cnt[m]);
+                }
+            gI[k] = g;
+        }
+    free(mu); free(sd); free(cnt);
+    return 0;
+}
+
 /* Gradients of L with respect to raw1, raw2 (H x W) and, when the
    pre-filter is on, its 25 weights (gw25, nullable), given gu = dL/du and
-   gv = dL/dv.  u, v (nullable) receive the forward field.  Returns 0, or 3
-   when NR > 0, 2 for bad parameters, 1 when out of memory. */
+   gv = dL/dv.  u, v (nullable) receive the forward field.  Returns 0, 3 for
+   an estimator variant (it covers the direct form, box window, from V = 0,
+   no mask), 2 for bad parameters, 1 when out of memory. */
 int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const orc_params *p, const double *gu,
                   const double *gv, double *g1, double *g2, double *gw25, double *u, double *v)
 {
     if (H < 1 || W < 1 || p->psl < 0 || p->psl > 15 || p->kr < 0 || p->it < 1) return 2;
-    if (p->nr > 0) return 3;
     /* the reverse mode covers the direct form with the uniform box, from V = 0 */
     if (p->increment_form || p->win_sigma > 0.0 || p->u_init || p->v_init || p->mask) return 3;
     const int L = p->psl + 1, S = L * p->it;
@@ -244,6 +301,7 @@ int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const or
     double *gu_c = (double *)calloc((size_t)N, sizeof(double)), *gv_c = (double *)calloc((size_t)N, sizeof(double));
     double *gu_n = (double *)calloc((size_t)N, sizeof(double)), *gv_n = (double *)calloc((size_t)N, sizeof(double));
     double *t = (double *)malloc(sizeof(double) * N);
+    double *N1 = NULL, *N2 = NULL;
     if (!I1 || !I2 || !V || !V0 || !gu_c || !gv_c || !gu_n || !gv_n || !t) { rc = 1; goto done; }
     for (int l = 0; l < L; ++l) {
         const int64_t n = (int64_t)Hs[l] * Ws[l];
@@ -263,15 +321,24 @@ int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const or
         }
     }
 
-    /* forward, keeping every stage's input and output field */
+    /* forward, keeping every stage's input and output field; I1, I2 hold the
+       scaled frames, N1, N2 the normalized ones (the pre-filter's input) */
     orc_scale(N, raw1, p->bits, I1);
     orc_scale(N, raw2, p->bits, I2);
+    if (p->nr > 0) {
+        N1 = (double *)malloc(sizeof(double) * N);
+        N2 = (double *)malloc(sizeof(double) * N);
+        if (!N1 || !N2) { rc = 1; goto done; }
+        orc_normalize(H, W, I1, p->nr, p->eps_n, N1);
+        orc_normalize(H, W, I2, p->nr, p->eps_n, N2);
+    }
+    const double *F1 = p->nr > 0 ? N1 : I1, *F2 = p->nr > 0 ? N2 : I2;
     if (p->prefilter) {
-        orc_prefilter(H, W, I1, p->w25, pyr1[0]);
-        orc_prefilter(H, W, I2, p->w25, pyr2[0]);
+        orc_prefilter(H, W, F1, p->w25, pyr1[0]);
+        orc_prefilter(H, W, F2, p->w25, pyr2[0]);
     } else {
-        memcpy(pyr1[0], I1, sizeof(double) * N);
-        memcpy(pyr2[0], I2, sizeof(double) * N);
+        memcpy(pyr1[0], F1, sizeof(double) * N);
+        memcpy(pyr2[0], F2, sizeof(double) * N);
     }
     for (int l = 1; l < L; ++l) {
         orc_reduce(Hs[l - 1], Ws[l - 1], pyr1[l - 1], pyr1[l]);
@@ -315,11 +382,13 @@ int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const or
         reduce_T(Hs[l - 1], Ws[l - 1], gp1[l], gp1[l - 1]);
         reduce_T(Hs[l - 1], Ws[l - 1], gp2[l], gp2[l - 1]);
     }
-    /* pre-filter: J(i,j) = sum w[a][b] I(i+a, j+b) (clamped) */
+    /* pre-filter: J(i,j) = sum w[a][b] F(i+a, j+b) (clamped), F the
+       normalized frame (or the scaled one when NR = 0); then the
+       normalization adjoint and the input scale */
     for (int f = 0; f < 2; ++f) {
         const double *gJ = f ? gp2[0] : gp1[0];
-        const double *I = f ? I2 : I1;
-        double *gI = f ? g2 : g1;
+        const double *I = f ? F2 : F1;
+        double *gI = p->nr > 0 ? t : (f ? g2 : g1);
         if (p->prefilter) {
             memset(gI, 0, sizeof(double) * N);
             for (int i = 0; i < H; ++i)
@@ -335,14 +404,18 @@ int orc_flow_grad(int H, int W, const double *raw1, const double *raw2, const or
         } else {
             memcpy(gI, gJ, sizeof(double) * N);
         }
+        if (p->nr > 0) {
+            gI = f ? g2 : g1;
+            if (normalize_T(H, W, f ? I2 : I1, p->nr, p->eps_n, t, gI)) { rc = 1; goto done; }
+        }
         if (p->bits > 0) {
             const double sc = 1.0 / (double)((1ULL << p->bits) - 1ULL);
             for (int64_t k = 0; k < N; ++k) gI[k] *= sc;
         }
     }
-    (void)t;
 
 done:
+    free(N1); free(N2);
     for (int l = 0; l < 16; ++l) { free(pyr1[l]); free(pyr2[l]); free(gp1[l]); free(gp2[l]); }
     if (V) for (int s = 0; s < 2 * S; ++s) free(V[s]);
     if (V0) for (int s = 0; s < 2 * S; ++s) free(V0[s]);

@@ -1,7 +1,7 @@
 """Pins of the FP64 oracle's reverse mode (CPU only).
 
 The paper defines no derivative of the estimator; the reverse mode is the
-chain rule through the forward steps.  It is pinned against the forward
+chain rule through the forward steps, local normalization included.  It is pinned against the forward
 oracle itself by central finite differences of L = sum(gu*u + gv*v) along
 random directions (a check that shares no arithmetic with the reverse code),
 and by facts any gradient must satisfy: linearity in (gu, gv), the input
@@ -25,6 +25,9 @@ def _fd_dir(fun, x, d, h):
     c1 = (fun(x + h * d) - fun(x - h * d)) / (2 * h)
     c2 = (fun(x + 0.5 * h * d) - fun(x - 0.5 * h * d)) / h
     return (4.0 * c2 - c1) / 3.0
+
+
+H_NR = 1e-7  # finite-difference step with local normalization
 
 
 def _case(H, W, seed, shift=(0.7, -0.4)):
@@ -143,7 +146,57 @@ def test_constant_frames_give_zero_gradient():
     assert not g1.any() and not g2.any() and not gw.any()
 
 
-def test_normalization_has_no_reverse_mode():
-    I1, I2, gu, gv, _ = _case(20, 20, seed=1)
-    with pytest.raises(RuntimeError):
-        oracle.flow_grad(I1, I2, oracle.Params(psl=1, kr=2, it=1, nr=3), gu, gv)
+@pytest.mark.parametrize("nr,with_prefilter", [(1, False), (2, False), (2, True)])
+def test_normalization_gradients_match_finite_differences(nr, with_prefilter):
+    """Local normalization (Sec. 2, step 1; radius NR) in the chain: frame
+    gradients along random directions and single pixels at the corner, the
+    border and inside, and the pre-filter weights, whose input is then the
+    normalized frame.  Normalization divides by the local deviation (a few
+    hundredths here), which magnifies an input step by up to ~100 at the
+    warped samples; the step is 1e-7 so that the finite difference stays
+    inside one bilinear cell (at 1e-6 one direction crosses a cell edge)."""
+    H, W = 30, 34
+    I1, I2, gu, gv, rng = _case(H, W, seed=40 + nr)
+    w = None
+    if with_prefilter:
+        w = np.zeros((5, 5))
+        w[2, 2] = 0.7
+        w[1:4, 1:4] += 0.04
+        w += 0.01 * rng.standard_normal((5, 5))
+    p = oracle.Params(psl=1, kr=2, it=2, nr=nr, prefilter=w)
+    g1, g2, gw, u, v = oracle.flow_grad(I1, I2, p, gu, gv)
+    u0, v0 = oracle.flow(I1, I2, p)
+    assert np.array_equal(u, u0) and np.array_equal(v, v0)
+    for frame in (0, 1):
+        d = rng.standard_normal((H, W))
+        if frame == 0:
+            fd = _fd_dir(lambda X: _loss(X, I2, p, gu, gv), I1, d, H_NR)
+            an = float(np.sum(g1 * d))
+        else:
+            fd = _fd_dir(lambda X: _loss(I1, X, p, gu, gv), I2, d, H_NR)
+            an = float(np.sum(g2 * d))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (frame, fd, an)
+    for (i, j) in [(0, 0), (H - 1, 5), (15, 17)]:
+        d = np.zeros((H, W))
+        d[i, j] = 1.0
+        fd = _fd_dir(lambda X: _loss(X, I2, p, gu, gv), I1, d, H_NR)
+        assert abs(fd - g1[i, j]) <= 1e-6 * max(1.0, abs(g1[i, j])), (i, j, fd, g1[i, j])
+    if with_prefilter:
+        def lw(wx):
+            return _loss(I1, I2, oracle.Params(psl=1, kr=2, it=2, nr=nr, prefilter=wx), gu, gv)
+        d = rng.standard_normal((5, 5))
+        fd = _fd_dir(lw, w, d, 1e-6)
+        an = float(np.sum(gw * d))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+def test_normalization_adjoint_of_a_constant_offset_is_zero():
+    """Normalization removes the local mean: adding a constant to a frame
+    changes nothing, so the gradient sums to zero over every box-closed
+    direction -- in particular along the constant direction."""
+    H, W = 26, 28
+    I1, I2, gu, gv, _ = _case(H, W, seed=9)
+    p = oracle.Params(psl=1, kr=2, it=2, nr=2)
+    g1, g2, _, _, _ = oracle.flow_grad(I1, I2, p, gu, gv)
+    assert abs(g1.sum()) <= 1e-9 * np.abs(g1).sum()
+    assert abs(g2.sum()) <= 1e-9 * np.abs(g2).sum()
