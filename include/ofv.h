@@ -238,9 +238,11 @@ ofv_status ofv_probe(int H, int W, int n, const float *u, const float *v, size_t
  * bilinear cell boundary the derivative is that of the cell floor() picks.
  * Float atomics scatter the gradients, so the last bits vary between runs.
  * The handle's pyramid slots are overwritten (as by ofv_compute).
- * OFV_ERR_UNSUPPORTED when local normalization is on (NR > 0), with the
- * Gaussian window or with the increment form (the reverse mode covers the
- * direct form with the uniform box). */
+ * Local normalization (NR > 0) is differentiated: its statistics are
+ * recomputed per frame and the adjoint of (I - mu) / s over the in-image box
+ * takes three more box sums.  OFV_ERR_UNSUPPORTED with the Gaussian window,
+ * the increment form or a region mask (the reverse mode covers the direct
+ * form with the uniform box). */
 ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2, const float *gu,
                         const float *gv, float *gI1, float *gI2, float *gw25, ofv_stream_t s);
 

@@ -358,6 +358,107 @@ __global__ void k_bw_copy_scaled(const float *gJ, int pitch, int H, int W, float
     gI[(int64_t)i * W + j] = scale * gJ[(int64_t)i * pitch + j];
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the local normalization (Sec. 2 step 1).  Forward:
+// J(m) = (I(m) - mu(m)) / s(m), s = sqrt(var + eps_n^2), mu and var over the
+// in-image part B(m) of the (2NR+1)^2 box, n(m) pixels.  With a = dL/dJ:
+//   dL/dI(k) = a(k)/s(k) - A(k) - I(k) B(k) + C(k),
+// where A, B, C are the truncated box sums of alpha = a / (s n),
+// beta = a J / (s^2 n) and beta mu (B(m) holds k exactly when B(k) holds m).
+// Planes here are dense H x W floats.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int box_count(int i, int j, int H, int W, int nr)
+{
+    return (min(i + nr, H - 1) - max(i - nr, 0) + 1) * (min(j + nr, W - 1) - max(j - nr, 0) + 1);
+}
+
+// Per pixel: mu, s and the normalized value J of the scaled input I = raw *
+// scale (mean, then the centred variance, as the forward ingest).
+template <typename TI>
+__global__ void k_bw_norm_stats(const TI *raw, float scale, int H, int W, int nr, float eps_n, float *J, float *mu,
+                                float *sd)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= H || j >= W) return;
+    const int i0 = max(i - nr, 0), i1 = min(i + nr, H - 1), j0 = max(j - nr, 0), j1 = min(j + nr, W - 1);
+    float sum = 0.f;
+    for (int ii = i0; ii <= i1; ++ii)
+        for (int jj = j0; jj <= j1; ++jj) sum += ld_raw(raw + (int64_t)ii * W + jj) * scale;
+    const float n = (float)((i1 - i0 + 1) * (j1 - j0 + 1));
+    const float m = sum / n;
+    float q = 0.f;
+    for (int ii = i0; ii <= i1; ++ii)
+        for (int jj = j0; jj <= j1; ++jj) {
+            const float d = ld_raw(raw + (int64_t)ii * W + jj) * scale - m;
+            q = fmaf(d, d, q);
+        }
+    const float sv = sqrtf(q / n + eps_n * eps_n);
+    const int64_t k = (int64_t)i * W + j;
+    mu[k] = m;
+    sd[k] = sv;
+    J[k] = (ld_raw(raw + k) * scale - m) / sv;
+}
+
+// alpha = a / (s n), beta = a J / (s^2 n), gamma = beta mu.
+__global__ void k_bw_norm_coef(const float *a, const float *J, const float *mu, const float *sd, int H, int W, int nr,
+                               float *alpha, float *beta, float *gamma)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= H || j >= W) return;
+    const int64_t k = (int64_t)i * W + j;
+    const float sn = sd[k] * (float)box_count(i, j, H, W, nr);
+    const float al = a[k] / sn;
+    const float be = al * J[k] / sd[k];
+    alpha[k] = al;
+    beta[k] = be;
+    gamma[k] = be * mu[k];
+}
+
+// Truncated box sums of radius nr of three planes along rows (dir 0) or
+// columns (dir 1).
+__global__ void k_bw_box3(const float *x0, const float *x1, const float *x2, int H, int W, int nr, int dir, float *y0,
+                          float *y1, float *y2)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= H || j >= W) return;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    if (dir == 0) {
+        const int64_t r = (int64_t)i * W;
+        for (int jj = max(j - nr, 0); jj <= min(j + nr, W - 1); ++jj) {
+            s0 += x0[r + jj];
+            s1 += x1[r + jj];
+            s2 += x2[r + jj];
+        }
+    } else {
+        for (int ii = max(i - nr, 0); ii <= min(i + nr, H - 1); ++ii) {
+            const int64_t o = (int64_t)ii * W + j;
+            s0 += x0[o];
+            s1 += x1[o];
+            s2 += x2[o];
+        }
+    }
+    const int64_t k = (int64_t)i * W + j;
+    y0[k] = s0;
+    y1[k] = s1;
+    y2[k] = s2;
+}
+
+// dL/draw = scale (a/s - A - I B + C), I = raw * scale.
+template <typename TI>
+__global__ void k_bw_norm_out(const float *a, const float *sd, const TI *raw, float scale, const float *A,
+                              const float *B, const float *C, int H, int W, float *gI)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= H || j >= W) return;
+    const int64_t k = (int64_t)i * W + j;
+    const float I = ld_raw(raw + k) * scale;
+    gI[k] = scale * (a[k] / sd[k] - A[k] - I * B[k] + C[k]);
+}
+
 // Dense planar (gu, gv) into an interleaved field of pitch vpitch.
 __global__ void k_bw_pack(const float *gu, const float *gv, int H, int W, float2 *out, int vpitch)
 {
@@ -449,6 +550,45 @@ cudaError_t bw_reduce_T(const float *gc, int cpitch, int Hc, int Wc, float *g, i
 {
     k_bw_reduce_T<<<grid2(Wc, Hc), dim3(32, 8), 0, s>>>(gc, cpitch, Hc, Wc, g, pitch, H, W);
     return cudaGetLastError();
+}
+
+// Reverse of ingest with local normalization: J (pyramid level 0) = pre-filter
+// (optional) of the normalized frame N; gJ -> gN (pre-filter transpose, weight
+// gradient against N) -> gI through the normalization adjoint.  t[0..9]:
+// dense H x W scratch planes.
+template <typename TI>
+cudaError_t bw_input_norm_t(const float *gJ, int pitch, int H, int W, const TI *raw, float scale, int nr, float eps_n,
+                            const float *w25, int prefilter, float *gI, float *gw, float *const *t, cudaStream_t s)
+{
+    const dim3 g = grid2(W, H), b(32, 8);
+    float *N = t[0], *mu = t[1], *sd = t[2], *gN = t[3];
+    k_bw_norm_stats<TI><<<g, b, 0, s>>>(raw, scale, H, W, nr, eps_n, N, mu, sd);
+    if (prefilter) {
+        cudaError_t e = cudaMemsetAsync(gN, 0, (size_t)H * W * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        k_bw_prefilter<float><<<g, b, 0, s>>>(gJ, pitch, H, W, N, 1.f, w25, gN, gw);
+    } else {
+        k_bw_copy_scaled<<<g, b, 0, s>>>(gJ, pitch, H, W, 1.f, gN);
+    }
+    k_bw_norm_coef<<<g, b, 0, s>>>(gN, N, mu, sd, H, W, nr, t[4], t[5], t[6]);
+    k_bw_box3<<<g, b, 0, s>>>(t[4], t[5], t[6], H, W, nr, 0, t[7], t[8], t[9]);
+    k_bw_box3<<<g, b, 0, s>>>(t[7], t[8], t[9], H, W, nr, 1, t[4], t[5], t[6]);
+    k_bw_norm_out<TI><<<g, b, 0, s>>>(gN, sd, raw, scale, t[4], t[5], t[6], H, W, gI);
+    return cudaGetLastError();
+}
+
+cudaError_t bw_input_norm(const float *gJ, int pitch, int H, int W, const void *raw, int in_type, float scale, int nr,
+                          float eps_n, const float *w25, int prefilter, float *gI, float *gw, float *const *t,
+                          cudaStream_t s)
+{
+    switch (in_type) {
+    case IN_U8: return bw_input_norm_t(gJ, pitch, H, W, static_cast<const uint8_t *>(raw), scale, nr, eps_n, w25,
+                                       prefilter, gI, gw, t, s);
+    case IN_U16: return bw_input_norm_t(gJ, pitch, H, W, static_cast<const uint16_t *>(raw), scale, nr, eps_n, w25,
+                                        prefilter, gI, gw, t, s);
+    default: return bw_input_norm_t(gJ, pitch, H, W, static_cast<const float *>(raw), scale, nr, eps_n, w25,
+                                    prefilter, gI, gw, t, s);
+    }
 }
 
 cudaError_t bw_input(const float *gJ, int pitch, int H, int W, const void *raw, int in_type, float scale,
@@ -549,8 +689,6 @@ extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2
         return fail_msg(OFV_ERR_INVALID_ARG, "ofv_backward: I1, I2, gu, gv, gI1 and gI2 must be non-NULL");
     if (gI1 == gI2) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_backward: gI1 and gI2 must be distinct buffers");
     const ofv_params &p = h->p;
-    if (p.norm_radius > 0)
-        return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_backward: local normalization (NR=%d) has no adjoint", p.norm_radius);
     if (p.window != OFV_WINDOW_BOX || p.increment_form || h->mask_on)
         return fail_msg(OFV_ERR_UNSUPPORTED,
                         "ofv_backward: covers the direct form with the uniform box window and no region mask only");
@@ -680,6 +818,21 @@ extern "C" ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2
         BW_TRY(cudaMemsetAsync(gw, 0, 25 * sizeof(float), s), "ofv_backward: memset");
     } else if (gw25) {
         BW_TRY(cudaMemsetAsync(gw25, 0, 25 * sizeof(float), s), "ofv_backward: memset");
+    }
+    if (p.norm_radius > 0) {
+        // the ten level-0 planes of A and B are free now: dense H x W scratch
+        float *t[10];
+        for (int c = 0; c < 5; ++c) {
+            t[c] = w.A.p[c];
+            t[5 + c] = w.B.p[c];
+        }
+        BW_TRY(bw_input_norm(w.gP1[0], h->pitch[0], h->H, h->W, I1, p.input, scale, p.norm_radius, p.norm_eps,
+                             h->w25, p.prefilter, gI1, gw, t, s),
+               "ofv_backward: normalization adjoint");
+        BW_TRY(bw_input_norm(w.gP2[0], h->pitch[0], h->H, h->W, I2, p.input, scale, p.norm_radius, p.norm_eps,
+                             h->w25, p.prefilter, gI2, gw, t, s),
+               "ofv_backward: normalization adjoint");
+        return OFV_OK;
     }
     BW_TRY(bw_input(w.gP1[0], h->pitch[0], h->H, h->W, I1, p.input, scale, h->w25, p.prefilter, gI1, gw, s),
            "ofv_backward: input adjoint");

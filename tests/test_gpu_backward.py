@@ -60,9 +60,9 @@ def gpu_grad(I1, I2, gu, gv, w25=None, bits=12, **kw):
         ofv.ofv_destroy(h)
 
 
-def oracle_grad(I1, I2, gu, gv, w25=None, bits=12, psl=2, kr=4, it=3):
+def oracle_grad(I1, I2, gu, gv, w25=None, bits=12, psl=2, kr=4, it=3, nr=0):
     b = bits if I1.dtype != np.float32 else 0
-    p = oracle.Params(psl=psl, kr=kr, it=it, bits=b, prefilter=w25)
+    p = oracle.Params(psl=psl, kr=kr, it=it, nr=nr, bits=b, prefilter=w25)
     g1, g2, gw, _, _ = oracle.flow_grad(I1.astype(np.float64), I2.astype(np.float64), p, gu, gv)
     return g1, g2, gw
 
@@ -163,18 +163,37 @@ def test_zero_output_gradient_gives_zero():
     assert not g1.any() and not g2.any() and not gw.any()
 
 
-def test_normalization_is_unsupported():
-    H, W = 64, 64
-    h = ofv.ofv_create(H, W, ofv.ofv_default_params(norm_radius=3, input=ofv.OFV_IN_F32))
-    try:
-        t = torch.zeros((H, W), dtype=torch.float32, device=DEV)
-        g = torch.empty_like(t)
-        g2 = torch.empty_like(t)
-        with pytest.raises(ofv.OfvError) as e:
-            ofv.ofv_backward(h, t, t, t, t, g, g2)
-        assert e.value.status == ofv.OFV_ERR_UNSUPPORTED
-    finally:
-        ofv.ofv_destroy(h)
+@pytest.mark.parametrize("nr,with_prefilter", [(1, False), (2, False), (2, True)])
+def test_normalization_gradients_match_oracle(nr, with_prefilter):
+    """Reverse mode through local normalization (Sec. 2 step 1): frames and
+    pre-filter weights against the FP64 reverse mode."""
+    H, W = 72, 84
+    I1, I2, gu, gv = _smooth(H, W, seed=30 + nr)
+    w = None
+    if with_prefilter:
+        w = np.zeros((5, 5), np.float32)
+        w[2, 2] = 0.7
+        w[1:4, 1:4] += 0.04
+    g1, g2, gw = gpu_grad(I1, I2, gu, gv, w25=w, norm_radius=nr, levels_psl=1, kernel_radius=3, iterations=2)
+    o1, o2, ow = oracle_grad(I1, I2, gu, gv, w25=None if w is None else w.astype(np.float64), psl=1, kr=3, it=2,
+                             nr=nr)
+    assert _rel(g1, o1) <= 1e-4, _rel(g1, o1)
+    assert _rel(g2, o2) <= 1e-4, _rel(g2, o2)
+    if with_prefilter:
+        assert _rel(gw, ow) <= 1e-4, _rel(gw, ow)
+
+
+def test_paper_parameters_gradient_matches_oracle():
+    """8-bit particle images with the paper's benchmark parameters (NR 2,
+    KR 10, IT 3; Sec. 6), PSL 1."""
+    I1, I2 = synth.particle_pair(150, 170, synth.rankine_field(150, 170), ppp=0.05, dmin=2.5, dmax=2.5, seed=8,
+                                 noise=0.01, kind=synth.OUT_U8, bits=8, field_max=3.0)
+    rng = np.random.default_rng(8)
+    gu, gv = rng.standard_normal(I1.shape), rng.standard_normal(I1.shape)
+    g1, g2, _ = gpu_grad(I1, I2, gu, gv, bits=8, norm_radius=2, levels_psl=1, kernel_radius=10, iterations=3)
+    o1, o2, _ = oracle_grad(I1, I2, gu, gv, bits=8, psl=1, kr=10, it=3, nr=2)
+    assert _rel(g1, o1) <= 1e-4, _rel(g1, o1)
+    assert _rel(g2, o2) <= 1e-4, _rel(g2, o2)
 
 
 def test_autograd_function_matches_c_abi_and_oracle():
