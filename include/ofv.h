@@ -246,6 +246,36 @@ ofv_status ofv_probe(int H, int W, int n, const float *u, const float *v, size_t
 ofv_status ofv_backward(ofv_handle *h, const void *I1, const void *I2, const float *gu,
                         const float *gv, float *gI1, float *gI2, float *gw25, ofv_stream_t s);
 
+/* ---- one field as horizontal strips (multi-GPU decomposition) -----------
+ * The paper names spreading the computation over 2 or 3 GPUs as the way to
+ * raise the rate further (Conclusions).  ofv_compute_strips computes one
+ * field as nstrips horizontal strips, each with a workspace of its own (here
+ * all on the handle's device, one strip after another on stream s): at
+ * every level a strip owns whole tile rows of the block kernel's tile grid
+ * and computes the rows of its pyramids it reads (own rows plus a redundant
+ * halo, from the input rows around them), so images need no exchange; after
+ * every Gauss-Newton iteration it copies from their owners the rows of the
+ * new field its next iteration reads (the window halo, or the coarse rows
+ * the next level's up-sampling reads).  The field equals ofv_compute's
+ * bitwise while no warp reaches farther than max_disp px (level-0 units);
+ * max_disp only sizes the image halo.  Fused path with KR 1..10, no region
+ * mask (else OFV_ERR_UNSUPPORTED); nstrips 1..64.  Workspace: nstrips full
+ * pyramids and two fields, grown on demand and owned by the handle; I1, I2,
+ * u, v as for ofv_compute. */
+typedef struct {
+    int own_row0, own_row1;       /* rows of the level the strip outputs (whole tile rows) */
+    int img_row0, img_row1;       /* rows of the level's images it computes (own rows and the halo) */
+    int fld_row0, fld_row1;       /* rows of the level's field its iterations read */
+    int up_row0, up_row1;         /* rows of the next coarser level's field read when up-sampling to this level */
+    int ingest_row0, ingest_row1; /* level 0: input rows it ingests (0, 0 at other levels) */
+} ofv_strip_rows;
+/* The rows strip `strip` of `nstrips` works on at `level` (host only, no
+   device work): for checking the decomposition. */
+ofv_status ofv_strip_plan(int H, int W, const ofv_params *params, int nstrips, int max_disp, int level, int strip,
+                          ofv_strip_rows *out);
+ofv_status ofv_compute_strips(ofv_handle *h, int nstrips, int max_disp, const void *I1, const void *I2, float *u,
+                              float *v, ofv_stream_t s);
+
 /* ---- allocation-free variant -------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot call cudaMalloc: host applications whose device memory belongs to

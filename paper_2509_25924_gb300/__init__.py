@@ -19,7 +19,8 @@ from . import build as _build
 __all__ = [
     "OfvError", "Params", "ofv_default_params", "ofv_create", "ofv_destroy", "ofv_set_prefilter", "ofv_set_mask",
     "ofv_compute", "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host",
-    "ofv_compute_noalloc", "ofv_compute_batched", "ofv_batch_tuning", "ofv_graph_create",
+    "ofv_compute_noalloc", "ofv_compute_strips", "ofv_strip_plan", "ofv_compute_batched", "ofv_batch_tuning",
+    "ofv_graph_create",
     "ofv_graph_create_batched", "ofv_graph_launch", "ofv_graph_destroy", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_probe",
     "ofv_debug_fail_alloc", "ofv_debug_poison", "ofv_level_shape",
     "ofv_read_level",
@@ -40,6 +41,7 @@ EXPORTED_SYMBOLS = [
     "ofv_compute_host", "ofv_compute_sequence", "ofv_compute_sequence_host", "ofv_compute_noalloc",
     "ofv_graph_create", "ofv_graph_create_batched", "ofv_graph_launch",
     "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
+    "ofv_compute_strips", "ofv_strip_plan",
     "ofv_vorticity", "ofv_recirculation_area", "ofv_probe", "ofv_debug_fail_alloc", "ofv_debug_poison",
     "ofv_level_shape",
     "ofv_read_level",
@@ -66,6 +68,12 @@ class Params(ctypes.Structure):
     ]
 
 
+class StripRows(ctypes.Structure):
+    """Mirror of ofv_strip_rows (include/ofv.h)."""
+    _fields_ = [(n, ctypes.c_int) for n in ("own_row0", "own_row1", "img_row0", "img_row1", "fld_row0", "fld_row1",
+                                            "up_row0", "up_row1", "ingest_row0", "ingest_row1")]
+
+
 def _load_library():
     path = _build.build_library()  # no-op when the library is up to date
     lib = ctypes.CDLL(path)
@@ -86,6 +94,8 @@ def _load_library():
         "ofv_graph_launch": ([P, P], I),
         "ofv_graph_destroy": ([P], I),
         "ofv_compute_batched": ([P, I, P, P], I),
+        "ofv_compute_strips": ([P, I, I, P, P, P, P, P], I),
+        "ofv_strip_plan": ([I, I, ctypes.POINTER(Params), I, I, I, I, ctypes.POINTER(StripRows)], I),
         "ofv_batch_tuning": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(I)], I),
         "ofv_queue_selftest": ([I, ctypes.POINTER(I)], I),
@@ -203,6 +213,24 @@ def ofv_compute_noalloc(H: int, W: int, params: Params, w25, I1, I2, u, v, strea
     array (OFV_NOALLOC_SCRATCH_BYTES).  See include/ofv.h for its limits."""
     _check(_lib.ofv_compute_noalloc(H, W, ctypes.byref(params), _addr(w25), _addr(I1), _addr(I2), _addr(u),
                                     _addr(v), _stream(stream)), "ofv_compute_noalloc")
+
+
+def ofv_compute_strips(h: int, nstrips: int, max_disp: int, I1, I2, u, v, stream=None):
+    """One field computed as nstrips horizontal strips with their own
+    workspaces and halo exchanges (the multi-GPU decomposition, run on the
+    handle's device); bitwise ofv_compute's field while warps stay within
+    max_disp px."""
+    _check(_lib.ofv_compute_strips(h, nstrips, max_disp, _addr(I1), _addr(I2), _addr(u), _addr(v), _stream(stream)),
+           "ofv_compute_strips")
+
+
+def ofv_strip_plan(H: int, W: int, params: Params, nstrips: int, max_disp: int, level: int, strip: int) -> dict:
+    """Rows strip `strip` works on at `level` (host only): own, img, fld, up
+    and ingest as (first, end) pairs."""
+    r = StripRows()
+    _check(_lib.ofv_strip_plan(H, W, ctypes.byref(params), nstrips, max_disp, level, strip, ctypes.byref(r)),
+           "ofv_strip_plan")
+    return {k: (getattr(r, k + "_row0"), getattr(r, k + "_row1")) for k in ("own", "img", "fld", "up", "ingest")}
 
 
 def ofv_backward(h: int, I1, I2, gu, gv, gI1, gI2, gw25=None, stream=None):

@@ -23,7 +23,7 @@ LIB = os.path.join(LIBDIR, "libofv.so")
 SOURCES = ["ofv_capi.cu", "k_pyramid.cu", "k_fused.cu", "k_plain.cu", "ofv_noalloc.cu", "k_block_launch.cu",
            "k_backward.cu", "k_derived.cu",
            "k_block_f32.cu", "k_block_f16.cu", "k_block_bf16.cu",
-           "k_block_var_f32.cu", "k_block_var_f16.cu", "k_block_var_bf16.cu", "ofv_batch.cu"]
+           "k_block_var_f32.cu", "k_block_var_f16.cu", "k_block_var_bf16.cu", "ofv_batch.cu", "ofv_strips.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
               "--expt-relaxed-constexpr"]

@@ -39,6 +39,7 @@ struct BlockParams {
     int mode;                    // V0Mode, uniform per launch
     int use_tma;                 // 1: tm[k] maps the two level images of pair k
     int *err;                    // error word (set to 1 when a TMA wait expires), or null
+    int by0;                     // first tile row of the launch (blockIdx.y + by0)
     CUtensorMap tm[kBlockMaxBatch][2];
 };
 
@@ -776,11 +777,12 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_it
     __shared__ __align__(8) uint64_t s_bar[StageShape<T, KR>::NBAND];
     const int z = blockIdx.z;
     if (prm.use_tma) {
-        block_tile<T, KR, false, SolveStoreT<VAR>, VAR>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4,
+        block_tile<T, KR, false, SolveStoreT<VAR>, VAR>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y + prm.by0, smem_f4,
                                                         &prm.tm[z][0], &prm.tm[z][1], prm.err, SolveStoreT<VAR>(),
                                                         s_bar, 0u, true);
     } else {
-        block_tile<T, KR, false, SolveStoreT<VAR>, VAR>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y, smem_f4);
+        block_tile<T, KR, false, SolveStoreT<VAR>, VAR>(prm.a[z], prm.mode, blockIdx.x, blockIdx.y + prm.by0,
+                                                        smem_f4);
     }
 }
 
@@ -928,7 +930,7 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_it
 // variant flag VAR in k_block_{f32,f16,bf16}.cu (VAR = false, plus the
 // reverse-mode stage kernel) and k_block_var_{f32,f16,bf16}.cu (VAR = true).
 template <typename T, bool VAR>
-cudaError_t launch_block_t(const BlockParams &p, int kr, int npairs, cudaStream_t s);
+cudaError_t launch_block_t(const BlockParams &p, int kr, int npairs, cudaStream_t s, int nrows = 0);
 template <typename T, bool VAR>
 cudaError_t launch_queue_t(const QueueParams &q, int kr, int ctas, cudaStream_t s);
 template <typename T, bool VAR>

@@ -22,18 +22,20 @@ cudaError_t run_block(const BlockParams &p, dim3 grid, int dev, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// nrows: tile rows of the launch from p.by0 on (0: to the bottom of the level)
 template <typename T, bool VAR>
-cudaError_t launch_block_t(const BlockParams &p, int kr, int npairs, cudaStream_t s)
+cudaError_t launch_block_t(const BlockParams &p, int kr, int npairs, cudaStream_t s, int nrows)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const IterArgs &a = p.a[0];
     switch (kr) {
-#define OFV_BLOCK_CASE(K)                                                                          \
-    case K: {                                                                                      \
-        constexpr int TS = BlockShape<K>::TS;                                                      \
-        return run_block<T, K, VAR>(p, dim3((a.W + TS - 1) / TS, (a.H + TS - 1) / TS, npairs), dev, s); \
+#define OFV_BLOCK_CASE(K)                                                                                  \
+    case K: {                                                                                              \
+        constexpr int TS = BlockShape<K>::TS;                                                              \
+        const int nby = nrows > 0 ? nrows : (a.H + TS - 1) / TS - p.by0;                                   \
+        return run_block<T, K, VAR>(p, dim3((a.W + TS - 1) / TS, nby, npairs), dev, s);                    \
     }
     OFV_BLOCK_CASE(1) OFV_BLOCK_CASE(2) OFV_BLOCK_CASE(3) OFV_BLOCK_CASE(4) OFV_BLOCK_CASE(5)
     OFV_BLOCK_CASE(6) OFV_BLOCK_CASE(7) OFV_BLOCK_CASE(8) OFV_BLOCK_CASE(9) OFV_BLOCK_CASE(10)
@@ -101,7 +103,7 @@ int queue_occupancy_t(int kr)
 }
 
 #define OFV_INSTANTIATE_BLOCK_LAUNCHERS(T, VAR)                                                     \
-    template cudaError_t launch_block_t<T, VAR>(const BlockParams &, int, int, cudaStream_t);      \
+    template cudaError_t launch_block_t<T, VAR>(const BlockParams &, int, int, cudaStream_t, int); \
     template cudaError_t launch_queue_t<T, VAR>(const QueueParams &, int, int, cudaStream_t);      \
     template int queue_occupancy_t<T, VAR>(int);
 

@@ -5,17 +5,17 @@
 
 namespace ofv {
 
-extern template cudaError_t launch_block_t<float, false>(const BlockParams &, int, int, cudaStream_t);
-extern template cudaError_t launch_block_t<float, true>(const BlockParams &, int, int, cudaStream_t);
-extern template cudaError_t launch_block_t<__half, false>(const BlockParams &, int, int, cudaStream_t);
-extern template cudaError_t launch_block_t<__half, true>(const BlockParams &, int, int, cudaStream_t);
-extern template cudaError_t launch_block_t<__nv_bfloat16, false>(const BlockParams &, int, int, cudaStream_t);
-extern template cudaError_t launch_block_t<__nv_bfloat16, true>(const BlockParams &, int, int, cudaStream_t);
+extern template cudaError_t launch_block_t<float, false>(const BlockParams &, int, int, cudaStream_t, int);
+extern template cudaError_t launch_block_t<float, true>(const BlockParams &, int, int, cudaStream_t, int);
+extern template cudaError_t launch_block_t<__half, false>(const BlockParams &, int, int, cudaStream_t, int);
+extern template cudaError_t launch_block_t<__half, true>(const BlockParams &, int, int, cudaStream_t, int);
+extern template cudaError_t launch_block_t<__nv_bfloat16, false>(const BlockParams &, int, int, cudaStream_t, int);
+extern template cudaError_t launch_block_t<__nv_bfloat16, true>(const BlockParams &, int, int, cudaStream_t, int);
 
 bool block_supports(int kr) { return kr >= 1 && kr <= kBlockMaxKR; }
 
 cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s,
-                              const CUtensorMap *const *tm, int *err)
+                              const CUtensorMap *const *tm, int *err, int by0, int nby)
 {
     if (npairs < 1 || npairs > kBlockMaxBatch || !block_supports(a[0].kr)) return cudaErrorInvalidValue;
     BlockParams p;
@@ -23,6 +23,7 @@ cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode
     for (int k = 0; k < npairs; ++k) p.a[k] = a[k];
     p.mode = mode;
     p.err = err;
+    p.by0 = by0;
     p.use_tma = 0;
     if (tm) {
         p.use_tma = 1;
@@ -38,12 +39,12 @@ cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode
     // the kernels with variant code only when a variant is on (uniform per launch)
     const bool var = a[0].inc || a[0].gauss || a[0].mask || a[0].s_out;
     switch (store) {
-    case ST_F16: return var ? launch_block_t<__half, true>(p, a[0].kr, npairs, s)
-                            : launch_block_t<__half, false>(p, a[0].kr, npairs, s);
-    case ST_BF16: return var ? launch_block_t<__nv_bfloat16, true>(p, a[0].kr, npairs, s)
-                             : launch_block_t<__nv_bfloat16, false>(p, a[0].kr, npairs, s);
-    default: return var ? launch_block_t<float, true>(p, a[0].kr, npairs, s)
-                        : launch_block_t<float, false>(p, a[0].kr, npairs, s);
+    case ST_F16: return var ? launch_block_t<__half, true>(p, a[0].kr, npairs, s, nby)
+                            : launch_block_t<__half, false>(p, a[0].kr, npairs, s, nby);
+    case ST_BF16: return var ? launch_block_t<__nv_bfloat16, true>(p, a[0].kr, npairs, s, nby)
+                             : launch_block_t<__nv_bfloat16, false>(p, a[0].kr, npairs, s, nby);
+    default: return var ? launch_block_t<float, true>(p, a[0].kr, npairs, s, nby)
+                        : launch_block_t<float, false>(p, a[0].kr, npairs, s, nby);
     }
 }
 

@@ -705,6 +705,7 @@ ofv_status ofv_destroy(ofv_handle *h)
     if (h->stage) cudaFree(h->stage);
     if (h->batch_arena) cudaFree(h->batch_arena);
     if (h->bw_arena) cudaFree(h->bw_arena);
+    if (h->strip_arena) cudaFree(h->strip_arena);
     if (h->tma_err_h) cudaFreeHost(h->tma_err_h);
     for (int k = 0; k < kGroupStreams; ++k)
         if (h->gs[k]) cudaStreamDestroy(h->gs[k]);
@@ -741,6 +742,7 @@ ofv_status ofv_debug_poison(ofv_handle *h, ofv_stream_t s)
     if (e == cudaSuccess && h->stage) e = cudaMemsetAsync(h->stage, 0xFF, h->stage_bytes, cs);
     if (e == cudaSuccess && h->hs_stage) e = cudaMemsetAsync(h->hs_stage, 0xFF, h->hs_bytes, cs);
     if (e == cudaSuccess && h->bw_arena) e = cudaMemsetAsync(h->bw_arena, 0xFF, h->bw_bytes, cs);
+    if (e == cudaSuccess && h->strip_arena) e = cudaMemsetAsync(h->strip_arena, 0xFF, h->strip_bytes, cs);
     if (e == cudaSuccess && h->batch_arena) e = cudaMemsetAsync(h->batch_arena, 0xFF, h->batch_bytes, cs);
     h->batch_sched_key.clear();  // the schedule and tensor maps in the batch arena are gone
     h->batch_maps_key.clear();

@@ -85,8 +85,9 @@ cudaError_t launch_iter_fused(const IterArgs &a, int store, int mode, cudaStream
 // staged box lies inside the image are then loaded by TMA.  err (optional):
 // device-visible word set to 1 if a TMA wait expires.
 bool block_supports(int kr);
+// by0, nby: tile rows by0 .. by0+nby-1 only (nby 0: to the bottom of the level).
 cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s,
-                              const CUtensorMap *const *tm = nullptr, int *err = nullptr);
+                              const CUtensorMap *const *tm = nullptr, int *err = nullptr, int by0 = 0, int nby = 0);
 // TMA box of the block kernel's staging (columns, rows of one band) for this
 // storage and radius.
 void block_stage_box(int store, int kr, int *cols, int *rows);

@@ -84,6 +84,10 @@ struct ofv_handle {
     // reverse mode: grow-only workspace (stage fields, sums, gradients)
     void *bw_arena;
     size_t bw_bytes;
+    // strip-decomposed field (ofv_compute_strips): grow-only workspace of
+    // every strip's pyramids and fields
+    void *strip_arena;
+    size_t strip_bytes;
     // TMA tensor maps of every (slot, level) image for the block kernel's
     // staged box, and the word a kernel sets when a TMA wait expires
     // (page-locked host memory mapped into the device)
