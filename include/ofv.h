@@ -110,6 +110,13 @@ typedef struct {
                            pairs-per-launch): groups of d pairs, each waiting for the previous one.  A
                            multiple d = m B (m <= 7, device sequences only): groups of B pairs, each
                            waiting for the group m back, so the m - 1 groups between still overlap. */
+    int tile_edge;      /* fused block kernel (KR 1..10) output tile edge in px: 0 = the radius's default
+                           (48 for KR <= 5, 32 for KR 6, 64 for KR 7..10); or its alternative (32 for
+                           KR != 6, 64 for KR 6).  With 0, ofv_compute_batched's autotuner picks one of
+                           the two per batch signature (ofv_batch_tuning reports it); nonzero fixes it.
+                           The window sums' rounding follows the tile grid, so fields of different tile
+                           edges agree to FP32 rounding, not bitwise.  The estimator variants (Gaussian
+                           window, increment form, region mask) and the reverse mode run the default. */
 } ofv_params;
 
 typedef struct ofv_handle ofv_handle;
@@ -345,9 +352,16 @@ typedef struct {
 ofv_status ofv_compute_batched(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_t s);
 
 /* Configuration used by the last ofv_compute_batched call: schedule (0 =
- * stage-major over all pairs, else group size), persistent CTAs per SM,
- * duration of its persistent launch in ms, and whether that call tuned. */
-ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm, double *ms, int *tuned);
+ * stage-major over all pairs, else group size), persistent CTAs per SM, the
+ * output tile edge of the block kernel in px (with ofv_params.tile_edge = 0
+ * the autotuner tries the radius's default and alternative edges, except
+ * with the Gaussian window or the increment form, which have the default
+ * only; a nonzero tile_edge fixes the edge),
+ * duration of its persistent launch in ms, and whether that call tuned.  A
+ * handle created with tile_edge set to the reported edge computes, through
+ * ofv_compute, bitwise the fields the batch computed. */
+ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm, int *tile_edge, double *ms,
+                            int *tuned);
 
 /* Test hook for the bounded waits of the persistent launch: runs one CTA
  * whose work unit depends on a counter nothing increments.  Expected result:

@@ -64,7 +64,7 @@ class Params(ctypes.Structure):
         ("det_rel_eps", ctypes.c_float), ("det_abs_eps", ctypes.c_float), ("norm_eps", ctypes.c_float),
         ("max_batch", ctypes.c_int),
         ("window", ctypes.c_int), ("window_sigma", ctypes.c_float), ("increment_form", ctypes.c_int),
-        ("warm_start", ctypes.c_int),
+        ("warm_start", ctypes.c_int), ("tile_edge", ctypes.c_int),
     ]
 
 
@@ -96,8 +96,8 @@ def _load_library():
         "ofv_compute_batched": ([P, I, P, P], I),
         "ofv_compute_strips": ([P, I, I, P, P, P, P, P], I),
         "ofv_strip_plan": ([I, I, ctypes.POINTER(Params), I, I, I, I, ctypes.POINTER(StripRows)], I),
-        "ofv_batch_tuning": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double),
-                              ctypes.POINTER(I)], I),
+        "ofv_batch_tuning": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)], I),
         "ofv_queue_selftest": ([I, ctypes.POINTER(I)], I),
         "ofv_backward": ([P, P, P, P, P, P, P, P, P], I),
         "ofv_vorticity": ([I, I, I, P, P, Z, P, P], I),
@@ -306,11 +306,12 @@ def ofv_graph_create_batched(h: int, pairs) -> int:
 
 
 def ofv_batch_tuning(h: int):
-    s, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    s, c, te, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     ms = ctypes.c_double()
-    _check(_lib.ofv_batch_tuning(h, ctypes.byref(s), ctypes.byref(c), ctypes.byref(ms), ctypes.byref(t)),
-           "ofv_batch_tuning")
-    return {"schedule": s.value, "ctas_per_sm": c.value, "ms": ms.value, "tuned": bool(t.value)}
+    _check(_lib.ofv_batch_tuning(h, ctypes.byref(s), ctypes.byref(c), ctypes.byref(te), ctypes.byref(ms),
+                                 ctypes.byref(t)), "ofv_batch_tuning")
+    return {"schedule": s.value, "ctas_per_sm": c.value, "tile_edge": te.value, "ms": ms.value,
+            "tuned": bool(t.value)}
 
 
 def ofv_queue_selftest(timeout_us: int):

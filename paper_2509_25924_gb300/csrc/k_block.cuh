@@ -43,15 +43,31 @@ struct BlockParams {
     CUtensorMap tm[kBlockMaxBatch][2];
 };
 
-template <int KR> struct BlockShape {
-    // Measured per radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles, two
-    // CTAs per SM (64-px tiles at one CTA per SM: -15..-18 %); KR 6: 32-px
-    // tiles, two CTAs per SM (64 px: -2.5 %); KR 7..10: 64-px tiles, one CTA
-    // per SM (less halo work: +21..26 % against 32 or 48 px).
-    static constexpr int TS = KR <= 5 ? 48 : KR == 6 ? 32 : 64;  // output tile edge
-    static constexpr int NT = KR == 6 ? 256 : 512;               // threads
-    static constexpr int MINB = KR <= 6 ? 2 : 1;                 // resident CTAs per SM (shared memory)
-    static constexpr int RW = TS + 2 * KR;                // product region edge
+// The block kernels' templates take KS = KR + 16 V: the window radius KR
+// (1 .. 10) and the tile shape V (0: the default shape of the radius, 1: its
+// alternative, which the batched autotuner tries and ofv_params.tile_edge
+// selects).
+__host__ __device__ constexpr int ks_radius(int ks) { return ks & 15; }
+__host__ __device__ constexpr int ks_shape(int ks) { return ks >> 4; }
+
+// Output tile edge of shape v for radius kr.  Default shapes, measured per
+// radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles, two CTAs per SM
+// (64-px tiles at one CTA per SM: -15..-18 %); KR 6: 32-px tiles, two CTAs
+// per SM (64 px: -2.5 %); KR 7..10: 64-px tiles, one CTA per SM (less halo
+// work: +21..26 % against 32 or 48 px).  Alternatives: 32-px tiles of 256
+// threads (KR 6: 64-px tiles of 512 threads).
+__host__ __device__ constexpr int block_tile_edge(int kr, int v)
+{
+    return v == 0 ? (kr <= 5 ? 48 : kr == 6 ? 32 : 64) : (kr == 6 ? 64 : 32);
+}
+
+template <int KS> struct BlockShape {
+    static constexpr int R = ks_radius(KS);                // window radius
+    static constexpr int TS = block_tile_edge(R, ks_shape(KS));  // output tile edge
+    static constexpr int NT = TS == 32 ? 256 : 512;              // threads
+    // resident CTAs per SM (shared memory)
+    static constexpr int MINB = TS == 32 ? (R <= 5 ? 3 : 2) : TS == 48 ? 2 : (R <= 6 && ks_shape(KS) == 0 ? 2 : 1);
+    static constexpr int RW = TS + 2 * R;                 // product region edge
     static constexpr int RWP = RW | 1;                    // odd row pitch of the product planes
     static constexpr int SH = RW + 2 * kBlockReach + 3;   // staged rows
 };
@@ -611,7 +627,8 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
     const int tid = threadIdx.x;
     const int H = a.H, W = a.W, pitch = a.pitch;
     const int tx0 = bx * TS, ty0 = by * TS;
-    const int px0 = tx0 - KR, py0 = ty0 - KR;                      // product region origin
+    constexpr int R = BS::R;                                       // window radius
+    const int px0 = tx0 - R, py0 = ty0 - R;                        // product region origin
     constexpr bool UP = RowOrder<T, KR>::bottom_up;
     const int sy0 = py0 - kBlockReach - 1 - RowOrder<T, KR>::slack;  // staged row origin
     const int sxn = px0 - kBlockReach - 1;
@@ -733,12 +750,12 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
     if (VAR && a.gauss) {
         for (int t = tid; t < 5 * RW; t += NT) {
             const int c = t / RW, row = t - c * RW;
-            window_wsums_inplace<KR, TS>(prod + c * PLANE + row * RWP, 1, a.wg);
+            window_wsums_inplace<R, TS>(prod + c * PLANE + row * RWP, 1, a.wg);
         }
     } else {
         for (int t = tid; t < 5 * RW; t += NT) {
             const int c = t / RW, row = t - c * RW;
-            window_sums_inplace<KR, TS>(prod + c * PLANE + row * RWP, 1);
+            window_sums_inplace<R, TS>(prod + c * PLANE + row * RWP, 1);
         }
     }
     __syncthreads();
@@ -747,12 +764,12 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
     if (VAR && a.gauss) {
         for (int t = tid; t < 5 * TS; t += NT) {
             const int c = t / TS, col = t - c * TS;
-            window_wsums_inplace<KR, TS>(prod + c * PLANE + col, RWP, a.wg);
+            window_wsums_inplace<R, TS>(prod + c * PLANE + col, RWP, a.wg);
         }
     } else {
         for (int t = tid; t < 5 * TS; t += NT) {
             const int c = t / TS, col = t - c * TS;
-            window_sums_inplace<KR, TS>(prod + c * PLANE + col, RWP);
+            window_sums_inplace<R, TS>(prod + c * PLANE + col, RWP);
         }
     }
     __syncthreads();
@@ -929,17 +946,16 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_it
 // Host launchers, explicitly instantiated per level storage type T and
 // variant flag VAR in k_block_{f32,f16,bf16}.cu (VAR = false, plus the
 // reverse-mode stage kernel) and k_block_var_{f32,f16,bf16}.cu (VAR = true).
+// shape: the tile shape v (the estimator variants, VAR = true, have the
+// default shape only)
 template <typename T, bool VAR>
-cudaError_t launch_block_t(const BlockParams &p, int kr, int npairs, cudaStream_t s, int nrows = 0);
+cudaError_t launch_block_t(const BlockParams &p, int kr, int npairs, cudaStream_t s, int nrows = 0, int shape = 0);
 template <typename T, bool VAR>
-cudaError_t launch_queue_t(const QueueParams &q, int kr, int ctas, cudaStream_t s);
+cudaError_t launch_queue_t(const QueueParams &q, int kr, int ctas, cudaStream_t s, int shape = 0);
 template <typename T, bool VAR>
-int queue_occupancy_t(int kr);
+int queue_occupancy_t(int kr, int shape = 0);
 
-// Output tile edge of the block kernel for radius kr.
-inline int block_tile_size(int kr)
-{
-    return kr <= 5 ? BlockShape<5>::TS : kr == 6 ? BlockShape<6>::TS : BlockShape<10>::TS;
-}
+// Output tile edge of the block kernel for radius kr and tile shape v.
+inline int block_tile_size(int kr, int v = 0) { return block_tile_edge(kr, v); }
 
 }  // namespace ofv

@@ -17,8 +17,8 @@
 
 namespace ofv {
 #define OFV_EXTERN_QUEUE(T, VAR)                                                                   \
-    extern template cudaError_t launch_queue_t<T, VAR>(const QueueParams &, int, int, cudaStream_t); \
-    extern template int queue_occupancy_t<T, VAR>(int);
+    extern template cudaError_t launch_queue_t<T, VAR>(const QueueParams &, int, int, cudaStream_t, int); \
+    extern template int queue_occupancy_t<T, VAR>(int, int);
 OFV_EXTERN_QUEUE(float, false)
 OFV_EXTERN_QUEUE(float, true)
 OFV_EXTERN_QUEUE(__half, false)
@@ -36,25 +36,31 @@ constexpr long long kWaitTimeoutNs = 5000000000LL;  // 5 s
 constexpr int kWaitSpinLimit = 200000000;
 
 // The kernels with variant code run only when a variant is on.
-cudaError_t launch_queue(int store, const QueueParams &q, int kr, int ctas, cudaStream_t s)
+// shape: the block kernel's tile shape (0 default, 1 alternative; the
+// variant kernels have the default only).
+cudaError_t launch_queue(int store, const QueueParams &q, int kr, int ctas, cudaStream_t s, int shape)
 {
     const bool var = q.inc || q.gauss;
     switch (store) {
-    case OFV_STORE_F16: return var ? launch_queue_t<__half, true>(q, kr, ctas, s)
-                                   : launch_queue_t<__half, false>(q, kr, ctas, s);
-    case OFV_STORE_BF16: return var ? launch_queue_t<__nv_bfloat16, true>(q, kr, ctas, s)
-                                    : launch_queue_t<__nv_bfloat16, false>(q, kr, ctas, s);
-    default: return var ? launch_queue_t<float, true>(q, kr, ctas, s) : launch_queue_t<float, false>(q, kr, ctas, s);
+    case OFV_STORE_F16: return var ? launch_queue_t<__half, true>(q, kr, ctas, s, shape)
+                                   : launch_queue_t<__half, false>(q, kr, ctas, s, shape);
+    case OFV_STORE_BF16: return var ? launch_queue_t<__nv_bfloat16, true>(q, kr, ctas, s, shape)
+                                    : launch_queue_t<__nv_bfloat16, false>(q, kr, ctas, s, shape);
+    default:
+        return var ? launch_queue_t<float, true>(q, kr, ctas, s, shape)
+                   : launch_queue_t<float, false>(q, kr, ctas, s, shape);
     }
 }
 
-int queue_occupancy(int store, int kr, bool var)
+int queue_occupancy(int store, int kr, bool var, int shape)
 {
     switch (store) {
-    case OFV_STORE_F16: return var ? queue_occupancy_t<__half, true>(kr) : queue_occupancy_t<__half, false>(kr);
+    case OFV_STORE_F16:
+        return var ? queue_occupancy_t<__half, true>(kr, shape) : queue_occupancy_t<__half, false>(kr, shape);
     case OFV_STORE_BF16:
-        return var ? queue_occupancy_t<__nv_bfloat16, true>(kr) : queue_occupancy_t<__nv_bfloat16, false>(kr);
-    default: return var ? queue_occupancy_t<float, true>(kr) : queue_occupancy_t<float, false>(kr);
+        return var ? queue_occupancy_t<__nv_bfloat16, true>(kr, shape)
+                   : queue_occupancy_t<__nv_bfloat16, false>(kr, shape);
+    default: return var ? queue_occupancy_t<float, true>(kr, shape) : queue_occupancy_t<float, false>(kr, shape);
     }
 }
 
@@ -106,9 +112,18 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
         return fail_msg(OFV_ERR_UNSUPPORTED, "ofv_compute_batched: a region mask is set (it has the handle's size)");
     const int L = h->L, IT = p.iterations, S = L * IT, KR = p.kernel_radius;
     const int minsz = 2 * KR + 1 > 8 ? 2 * KR + 1 : 8;
-    const int TS = block_tile_size(KR);
     const int sb = store_bytes(p.storage);
-    std::vector<std::vector<int>> Hs(n, std::vector<int>(L)), Ws(n, std::vector<int>(L)), tiles(n, std::vector<int>(S));
+    const bool var = p.window == OFV_WINDOW_GAUSS || p.increment_form;
+    // tile shapes the tuner may pick: the one tile_edge names, else both
+    // (the variant kernels have the default shape only)
+    std::vector<int> shapes;
+    if (p.tile_edge != 0 || var)
+        shapes.push_back(std::max(tile_shape_of(p), 0));
+    else
+        shapes = {0, 1};
+    std::vector<std::vector<int>> Hs(n, std::vector<int>(L)), Ws(n, std::vector<int>(L));
+    std::vector<std::vector<int>> tiles[2];  // [shape][pair][stage]: tiles of the stage's level
+    for (int t : shapes) tiles[t].assign(n, std::vector<int>(S));
     for (int i = 0; i < n; ++i) {
         const ofv_pair &q = pairs[i];
         if (!q.I1 || !q.I2 || !q.u || !q.v || q.u == q.v)
@@ -124,9 +139,12 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
         if (Hs[i][L - 1] < minsz || Ws[i][L - 1] < minsz)
             return fail_msg(OFV_ERR_SHAPE, "ofv_compute_batched: pair %d (%dx%d): coarsest level below %d", i, q.H,
                             q.W, minsz);
-        for (int s = 0; s < S; ++s) {
-            const int l = L - 1 - s / IT;
-            tiles[i][s] = ((Ws[i][l] + TS - 1) / TS) * ((Hs[i][l] + TS - 1) / TS);
+        for (int t : shapes) {
+            const int TS = block_tile_size(KR, t);
+            for (int s = 0; s < S; ++s) {
+                const int l = L - 1 - s / IT;
+                tiles[t][i][s] = ((Ws[i][l] + TS - 1) / TS) * ((Hs[i][l] + TS - 1) / TS);
+            }
         }
     }
     DevGuard dg(h->device);
@@ -288,33 +306,43 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
                        std::to_string(KR) + "/" + std::to_string(L) + "/" + std::to_string(IT);
     for (int i = 0; i < n; ++i) mkey += "/" + std::to_string(Hs[i][0]) + "x" + std::to_string(Ws[i][0]);
 
-    // TMA tensor maps of every pair's level images (encoded once per layout
-    // and uploaded when the layout changes); levels smaller than the staged
-    // box never use theirs
-    bool use_tma = h->tma_err_d != nullptr;
-    if (use_tma) {
-        auto mit = h->batch_maps.find(mkey);
+    // TMA tensor maps of every pair's level images for one tile shape (its
+    // staged box): encoded once per layout and shape, uploaded when they
+    // change; levels smaller than the staged box never use theirs.  Returns
+    // false (cp.async staging) when no map could be encoded.
+    ofv_status mst = OFV_OK;
+    auto ensure_maps = [&](int shape) -> bool {
+        if (!h->tma_err_d) return false;
+        const std::string k = mkey + "/t" + std::to_string(shape);
+        auto mit = h->batch_maps.find(k);
         if (mit == h->batch_maps.end()) {
             std::vector<CUtensorMap> maps(32 * (size_t)n);
             memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
-            for (int i = 0; i < n && use_tma; ++i)
-                for (int l = 0; l < L && use_tma; ++l)
-                    for (int f = 0; f < 2 && use_tma; ++f)
-                        use_tma = encode_block_map(&maps[((size_t)i * 16 + l) * 2 + f], lvl(i, f, l), Ws[i][l], Hs[i][l],
-                                                   pitch_for(Ws[i][l]), p.storage, KR);
-            if (use_tma) {
-                if (h->batch_maps.size() > 64) h->batch_maps.clear();
-                mit = h->batch_maps.emplace(mkey, std::move(maps)).first;
-            }
+            bool ok = true;
+            for (int i = 0; i < n && ok; ++i)
+                for (int l = 0; l < L && ok; ++l)
+                    for (int f = 0; f < 2 && ok; ++f)
+                        ok = encode_block_map(&maps[((size_t)i * 16 + l) * 2 + f], lvl(i, f, l), Ws[i][l], Hs[i][l],
+                                              pitch_for(Ws[i][l]), p.storage, KR, shape);
+            if (!ok) return false;
+            if (h->batch_maps.size() > 64) h->batch_maps.clear();
+            mit = h->batch_maps.emplace(k, std::move(maps)).first;
         }
-        if (use_tma && h->batch_maps_key != mkey) {
-            if (record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs uploaded tensor maps");
+        if (h->batch_maps_key != k) {
+            if (record) {
+                mst = fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs uploaded tensor maps");
+                return false;
+            }
             e = cudaMemcpyAsync(base + tmaps_off, mit->second.data(), sizeof(CUtensorMap) * mit->second.size(),
                                 cudaMemcpyHostToDevice, cs);
-            if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading tensor maps");
-            h->batch_maps_key = mkey;
+            if (e != cudaSuccess) {
+                mst = cuda_fail_msg(e, "ofv_compute_batched: uploading tensor maps");
+                return false;
+            }
+            h->batch_maps_key = k;
         }
-    }
+        return true;
+    };
 
     int dev = h->device, sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -324,7 +352,8 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
     for (int i = 0; i < n; ++i) sizes.push_back({Hs[i][0], Ws[i][0]});
     std::sort(sizes.begin(), sizes.end());
     std::string key = "kr" + std::to_string(KR) + "l" + std::to_string(L) + "it" + std::to_string(IT) + "s" +
-                      std::to_string(p.storage) + "v" + std::to_string(p.window) + std::to_string(p.increment_form);
+                      std::to_string(p.storage) + "v" + std::to_string(p.window) + std::to_string(p.increment_form) + "t" +
+                      std::to_string(p.tile_edge);
     for (auto &sz : sizes) key += ":" + std::to_string(sz.first) + "x" + std::to_string(sz.second);
 
     std::vector<BatchTune> cands;
@@ -332,10 +361,12 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
     const bool tuning = it == h->tune.end();
     if (tuning && record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs a tuned batch");
     if (tuning) {
-        const int occ = std::max(1, queue_occupancy(p.storage, KR, p.window == OFV_WINDOW_GAUSS || p.increment_form));
-        for (int sch : {0, 8})
-            for (int c : {occ, occ - 1})
-                if (c >= 1 && (sch == 0 || sch < n)) cands.push_back(BatchTune{sch, c, 0.0});
+        for (int t : shapes) {
+            const int occ = std::max(1, queue_occupancy(p.storage, KR, var, t));
+            for (int sch : {0, 8})
+                for (int c : {occ, occ - 1})
+                    if (c >= 1 && (sch == 0 || sch < n)) cands.push_back(BatchTune{sch, c, t, 0.0});
+        }
     } else {
         cands.push_back(it->second);
     }
@@ -363,23 +394,33 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
     q.error = q.head + 1;
     q.timeout_ns = kWaitTimeoutNs;
     q.spin_limit = kWaitSpinLimit;
-    q.tmaps = use_tma ? reinterpret_cast<const CUtensorMap *>(base + tmaps_off) : nullptr;
     q.tma_err = h->tma_err_d;
     q.host_err = h->qerr_d;
 
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    struct Events {  // timing events of the tuning pass, destroyed on every return
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events()
+        {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
     if (tuning) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
+        cudaEventCreate(&ev.a);
+        cudaEventCreate(&ev.b);
     }
     std::vector<int2> group;
     std::vector<int> goff;
-    int best = 0;
-    for (size_t c = 0; c < cands.size(); ++c) {
-        build_schedule(cands[c].schedule, S, n, tiles, group, goff);
+    // one persistent launch of candidate c (timed while tuning)
+    auto run = [&](size_t c, bool timed) -> ofv_status {
+        const int shape = cands[c].shape;
+        const bool use_tma = ensure_maps(shape);
+        if (mst != OFV_OK) return mst;
+        q.tmaps = use_tma ? reinterpret_cast<const CUtensorMap *>(base + tmaps_off) : nullptr;
+        build_schedule(cands[c].schedule, S, n, tiles[shape], group, goff);
         q.ngroups = (int)group.size();
         q.total_units = goff.back();
-        const std::string skey = mkey + "#" + std::to_string(cands[c].schedule);
+        const std::string skey = mkey + "#" + std::to_string(cands[c].schedule) + "t" + std::to_string(shape);
         e = cudaSuccess;
         if (h->batch_sched_key != skey) {  // the schedule of this layout is not in the arena yet
             if (record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs the uploaded schedule");
@@ -392,27 +433,37 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
         if (e == cudaSuccess) e = cudaMemsetAsync(q.done, 0, sizeof(int) * (maxgroups + 2), cs);
         if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: uploading the schedule");
         const int ctas = std::min(sms * cands[c].ctas_per_sm, std::max(1, q.total_units));
-        if (tuning) cudaEventRecord(e0, cs);
-        e = launch_queue(p.storage, q, KR, ctas, cs);
+        if (timed) cudaEventRecord(ev.a, cs);
+        e = launch_queue(p.storage, q, KR, ctas, cs, shape);
         if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: persistent launch");
-        if (tuning) {
-            cudaEventRecord(e1, cs);
-            e = cudaEventSynchronize(e1);
+        if (timed) {
+            cudaEventRecord(ev.b, cs);
+            e = cudaEventSynchronize(ev.b);
             if (e != cudaSuccess) return cuda_fail_msg(e, "ofv_compute_batched: timing a candidate");
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventElapsedTime(&ms, ev.a, ev.b);
             cands[c].ms = ms;
-            if (ms < cands[best].ms) best = (int)c;
             if (const int u = *static_cast<volatile int *>(h->qerr_h))
                 return fail_msg(OFV_ERR_TIMEOUT, "ofv_compute_batched: a dependency wait of work unit %d expired",
                                 u - 1);
         }
+        return OFV_OK;
+    };
+    int best = 0;
+    for (size_t c = 0; c < cands.size(); ++c) {
+        const ofv_status st = run(c, tuning);
+        if (st != OFV_OK) return st;
+        if (tuning && cands[c].ms < cands[best].ms) best = (int)c;
     }
     if (tuning) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         h->tune[key] = cands[best];
-        // the last candidate's outputs are already in place (all compute the same fields)
+        // Candidates of one tile shape compute the same fields; another shape
+        // sums the windows in another order.  The fields left in place must be
+        // the chosen configuration's, as in every later call of this signature.
+        if (cands[best].shape != cands.back().shape) {
+            const ofv_status st = run((size_t)best, false);
+            if (st != OFV_OK) return st;
+        }
     }
     if (!record) {
         h->last_tune = tuning ? cands[best] : cands[0];
@@ -487,11 +538,14 @@ ofv_status ofv_graph_create_batched(ofv_handle *h, int n, const ofv_pair *pairs,
     return OFV_OK;
 }
 
-ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm, double *ms, int *tuned)
+ofv_status ofv_batch_tuning(const ofv_handle *h, int *schedule, int *ctas_per_sm, int *tile_edge, double *ms,
+                            int *tuned)
 {
-    if (!h || !schedule || !ctas_per_sm || !ms || !tuned) return fail_msg(OFV_ERR_INVALID_ARG, "NULL argument");
+    if (!h || !schedule || !ctas_per_sm || !tile_edge || !ms || !tuned)
+        return fail_msg(OFV_ERR_INVALID_ARG, "NULL argument");
     *schedule = h->last_tune.schedule;
     *ctas_per_sm = h->last_tune.ctas_per_sm;
+    *tile_edge = block_tile_size(h->p.kernel_radius, h->last_tune.shape);
     *ms = h->last_tune.ms;
     *tuned = h->last_tuned;
     return OFV_OK;
@@ -542,7 +596,7 @@ ofv_status ofv_queue_selftest(int timeout_us, int *error_word)
     if (e == cudaSuccess) {
         *hw = 0;
         q.host_err = hw_d;
-        e = launch_queue(OFV_STORE_F32, q, 4, 1, nullptr);
+        e = launch_queue(OFV_STORE_F32, q, 4, 1, nullptr, 0);
     }
     int err = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&err, q.error, sizeof(int), cudaMemcpyDeviceToHost);

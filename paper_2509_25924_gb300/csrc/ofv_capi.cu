@@ -99,6 +99,9 @@ ofv_status check_params(const ofv_params *p)
         return fail(OFV_ERR_INVALID_ARG, "increment_form=%d is not 0 or 1", p->increment_form);
     if (p->warm_start < 0 || p->warm_start > 7 * kMaxBatch)
         return fail(OFV_ERR_INVALID_ARG, "warm_start=%d outside 0..%d", p->warm_start, 7 * kMaxBatch);
+    if (tile_shape_of(*p) < 0)
+        return fail(OFV_ERR_INVALID_ARG, "tile_edge=%d: 0, %d or %d for KR %d on the fused path", p->tile_edge,
+                    block_tile_edge(p->kernel_radius, 0), block_tile_edge(p->kernel_radius, 1), p->kernel_radius);
     return OFV_OK;
 }
 
@@ -170,14 +173,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder_impl()
 void encode_tensor_maps(ofv_handle *h)
 {
     int cols = 0, rows = 0;
-    block_stage_box(h->p.storage, h->p.kernel_radius, &cols, &rows);
+    block_stage_box(h->p.storage, h->p.kernel_radius, &cols, &rows, tile_shape_of(h->p));
     for (int l = 0; l < h->L; ++l) {
         h->tma_ok[l] = 0;
         if (cols < 1 || h->Ws[l] < cols || h->Hs[l] < rows) continue;
         bool ok = true;
         for (int f = 0; f < h->nslots && ok; ++f)
             ok = encode_block_map(&h->tmap[f][l], h->lvl[f][l], h->Ws[l], h->Hs[l], h->pitch[l], h->p.storage,
-                                  h->p.kernel_radius);
+                                  h->p.kernel_radius, tile_shape_of(h->p));
         h->tma_ok[l] = ok ? 1 : 0;
     }
 }
@@ -325,7 +328,8 @@ ofv_status run_levels(ofv_handle *h, int np, const int *s1, const int *s2, float
                     tm[2 * k + 1] = &h->tmap[s2[k]][l];
                 }
                 const bool use = h->tma_ok[l] && h->tma_err_d;
-                e = launch_iter_block(a, np, p.storage, mode, s, use ? tm : nullptr, h->tma_err_d);
+                e = launch_iter_block(a, np, p.storage, mode, s, use ? tm : nullptr, h->tma_err_d, 0, 0,
+                                      tile_shape_of(p));
             } else {
                 for (int k = 0; k < np && e == cudaSuccess; ++k)
                     e = p.path == OFV_PATH_PLAIN ? launch_iter_plain(a[k], h->plain, p.storage, mode, s)
@@ -507,11 +511,11 @@ ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *
 // stride pitch elements) with the block kernel's TMA box for radius kr; no
 // swizzle, out-of-bounds fill unused (only boxes inside the image are
 // copied).  False when the encoder is unavailable or refuses.
-bool encode_block_map(CUtensorMap *m, const void *base, int W, int H, int pitch, int store, int kr)
+bool encode_block_map(CUtensorMap *m, const void *base, int W, int H, int pitch, int store, int kr, int shape)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder_impl();
     int cols = 0, rows = 0;
-    block_stage_box(store, kr, &cols, &rows);
+    block_stage_box(store, kr, &cols, &rows, shape);
     if (!enc || cols < 1) return false;
     const CUtensorMapDataType dt = store == OFV_STORE_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : store == OFV_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -548,6 +552,7 @@ void ofv_default_params(ofv_params *p)
     p->window_sigma = 0.f;
     p->increment_form = 0;
     p->warm_start = 0;
+    p->tile_edge = 0;
 }
 
 ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out)

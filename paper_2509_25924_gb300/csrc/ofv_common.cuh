@@ -86,11 +86,14 @@ cudaError_t launch_iter_fused(const IterArgs &a, int store, int mode, cudaStream
 // device-visible word set to 1 if a TMA wait expires.
 bool block_supports(int kr);
 // by0, nby: tile rows by0 .. by0+nby-1 only (nby 0: to the bottom of the level).
+// shape: the tile shape (0 default, 1 the alternative; the estimator
+// variants run the default shape).
 cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s,
-                              const CUtensorMap *const *tm = nullptr, int *err = nullptr, int by0 = 0, int nby = 0);
+                              const CUtensorMap *const *tm = nullptr, int *err = nullptr, int by0 = 0, int nby = 0,
+                              int shape = 0);
 // TMA box of the block kernel's staging (columns, rows of one band) for this
-// storage and radius.
-void block_stage_box(int store, int kr, int *cols, int *rows);
+// storage, radius and tile shape.
+void block_stage_box(int store, int kr, int *cols, int *rows, int shape = 0);
 
 struct PlainBufs {
     float *prod;  // 5 planes, each H x pitch floats

@@ -7,7 +7,7 @@
 #include <vector>
 
 #include "../../include/ofv.h"
-#include "ofv_common.cuh"
+#include "k_block.cuh"
 
 namespace ofv {
 
@@ -29,6 +29,7 @@ struct ProfRec {
 struct BatchTune {
     int schedule;     // 0: stage-major over all pairs, else pairs in groups of this many
     int ctas_per_sm;  // persistent CTAs per SM
+    int shape;        // block kernel tile shape (0 default, 1 alternative)
     double ms;        // measured duration of the persistent launch
 };
 
@@ -130,7 +131,20 @@ cudaError_t dev_alloc(void **p, size_t bytes);
 // Steps 1-2 into the handle's pyramid slots (defined with the C ABI).
 ofv_status handle_pyramids(ofv_handle *h, const void *const *frames, const int *slots, int nf, cudaStream_t s);
 // Tensor map of a level image with the block kernel's TMA box.
-bool encode_block_map(CUtensorMap *m, const void *base, int W, int H, int pitch, int store, int kr);
+bool encode_block_map(CUtensorMap *m, const void *base, int W, int H, int pitch, int store, int kr, int shape = 0);
+// Tile shape of the block kernel that params select: 0 (default) or 1 (the
+// alternative edge), -1 when tile_edge is not one of the radius's edges on
+// the fused block path.  The Gaussian window and the increment form run the
+// default shape whatever the edge asked for.
+inline int tile_shape_of(const ofv_params &p)
+{
+    if (p.tile_edge == 0) return 0;
+    if (p.path != OFV_PATH_FUSED || !block_supports(p.kernel_radius)) return -1;
+    if (p.tile_edge == block_tile_edge(p.kernel_radius, 0)) return 0;
+    if (p.tile_edge != block_tile_edge(p.kernel_radius, 1)) return -1;
+    // the estimator variants are built with the default shape only
+    return p.window == OFV_WINDOW_GAUSS || p.increment_form ? 0 : 1;
+}
 // True once a kernel of this handle recorded an expired TMA wait.
 inline bool tma_expired(const ofv_handle *h)
 {

@@ -18,7 +18,8 @@
 #include <mutex>
 
 #include "../../include/ofv.h"
-#include "ofv_common.cuh"
+#include "k_block.cuh"
+#include "ofv_handle.h"
 
 namespace ofv {
 void set_error_message(const char *msg);
@@ -85,7 +86,8 @@ extern "C" ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *p, con
         !std::isfinite(p->norm_eps) || (p->window != OFV_WINDOW_BOX && p->window != OFV_WINDOW_GAUSS) ||
         (p->window == OFV_WINDOW_GAUSS && (!(p->window_sigma > 0.f) || !std::isfinite(p->window_sigma))) ||
         (p->increment_form != 0 && p->increment_form != 1) || p->max_batch < 0 ||
-        p->max_batch > kMaxPairsPerLaunch || p->warm_start < 0 || p->warm_start > 7 * kMaxPairsPerLaunch)
+        p->max_batch > kMaxPairsPerLaunch || p->warm_start < 0 || p->warm_start > 7 * kMaxPairsPerLaunch ||
+        tile_shape_of(*p) < 0)
         return na_fail(OFV_ERR_INVALID_ARG, "ofv_compute_noalloc: parameter out of range (see ofv_params)");
     if (p->path != OFV_PATH_FUSED)
         return na_fail(OFV_ERR_UNSUPPORTED, "ofv_compute_noalloc: only the fused path is available without allocation");
@@ -214,8 +216,9 @@ extern "C" ofv_status ofv_compute_noalloc(int H, int W, const ofv_params *p, con
             } else {
                 a.Vout = vbuf[nxt];
             }
-            e = block_supports(p->kernel_radius) ? launch_iter_block(&a, 1, p->storage, mode, cs)
-                                                 : launch_iter_fused(a, p->storage, mode, cs);
+            e = block_supports(p->kernel_radius)
+                    ? launch_iter_block(&a, 1, p->storage, mode, cs, nullptr, nullptr, 0, 0, tile_shape_of(*p))
+                    : launch_iter_fused(a, p->storage, mode, cs);
             cur = nxt;
             have = true;
         }

@@ -68,7 +68,7 @@ ofv_status plan_strip(int H, int W, const ofv_params &p, int nstrips, int max_di
         o->Hs[l] = (o->Hs[l - 1] + 1) / 2;
         o->Ws[l] = (o->Ws[l - 1] + 1) / 2;
     }
-    const int ts = block_tile_size(KR);
+    const int ts = block_tile_size(KR, std::max(tile_shape_of(p), 0));
     Range need[kMaxLevels];
     for (int l = 0; l < L; ++l) {
         const int Hl = o->Hs[l];
@@ -123,6 +123,7 @@ ofv_status check_strip_args(int H, int W, const ofv_params *p, int nstrips, int 
         return fail_msg(OFV_ERR_INVALID_ARG, "strips: levels_psl=%d outside 0..%d", p->levels_psl, kMaxLevels - 1);
     if (p->path != OFV_PATH_FUSED || !block_supports(p->kernel_radius))
         return fail_msg(OFV_ERR_UNSUPPORTED, "strips: the fused path with KR 1..10 only");
+    if (tile_shape_of(*p) < 0) return fail_msg(OFV_ERR_INVALID_ARG, "strips: tile_edge=%d", p->tile_edge);
     return OFV_OK;
 }
 
@@ -279,7 +280,8 @@ extern "C" ofv_status ofv_compute_strips(ofv_handle *h, int nstrips, int max_dis
     }
 
     // steps 3-6: coarse to fine, every strip's tiles, then the halo copies
-    const int ts = block_tile_size(p.kernel_radius);
+    const int shape = tile_shape_of(p);
+    const int ts = block_tile_size(p.kernel_radius, shape);
     int cur = 0;
     for (int l = L - 1; l >= 0; --l) {
         for (int t = 0; t < IT; ++t) {
@@ -316,7 +318,7 @@ extern "C" ofv_status ofv_compute_strips(ofv_handle *h, int nstrips, int max_dis
                     a.Vout = sb[d].fld[nxt];
                 }
                 if ((e = launch_iter_block(&a, 1, p.storage, mode, s, nullptr, nullptr, own.a / ts,
-                                           (own.b - own.a + ts - 1) / ts)) != cudaSuccess)
+                                           (own.b - own.a + ts - 1) / ts, shape)) != cudaSuccess)
                     return launch_fail("strips: iteration");
             }
             if (last) break;

@@ -1,6 +1,6 @@
 // Host-side check of the block kernel's phase-1 schedule (built and run by
-// test_block_schedule.py; no GPU needed).  For every storage type and
-// window radius it walks the phase-1 loop pixel by pixel, in the row order
+// test_block_schedule.py; no GPU needed).  For every storage type, window
+// radius and tile shape (KS = radius + 16 shape) it walks the phase-1 loop pixel by pixel, in the row order
 // the kernel uses, and checks that
 //   * each pixel reads staged rows inside the staged box, and only rows of
 //     TMA bands the loop has waited for by then (the waits happen before the
@@ -18,11 +18,11 @@ using namespace ofv;
 
 // Extra shared-memory wavefronts of one warp-wide load of the staged tap at
 // product pixel (ry, rx), summed over the warps of the loop.
-template <typename T, int KR>
+template <typename T, int KS>
 static long tap_conflicts(bool up)
 {
-    using BS = BlockShape<KR>;
-    constexpr int NT = BS::NT, RW = BS::RW, SP = StageShape<T, KR>::SP;
+    using BS = BlockShape<KS>;
+    constexpr int NT = BS::NT, RW = BS::RW, SP = StageShape<T, KS>::SP;
     long extra = 0;
     for (int base = 0; base < RW * RW; base += 32) {
         long word[32];
@@ -50,16 +50,16 @@ static long tap_conflicts(bool up)
     return extra;
 }
 
-template <typename T, int KR>
+template <typename T, int KS>
 static int check(const char *tname)
 {
-    using BS = BlockShape<KR>;
-    using SS = StageShape<T, KR>;
-    using RO = RowOrder<T, KR>;
+    using BS = BlockShape<KS>;
+    using SS = StageShape<T, KS>;
+    using RO = RowOrder<T, KS>;
     constexpr int NT = BS::NT, RW = BS::RW, SHB = SS::SHB, SLACK = RO::slack;
     constexpr bool UP = RO::bottom_up;
-    constexpr int I1 = first_iter_of_band<KR, SHB>(1), I2 = first_iter_of_band<KR, SHB>(2);
-    constexpr int J1 = first_iter_of_band_up<KR, SHB, SLACK>(1), J0 = first_iter_of_band_up<KR, SHB, SLACK>(0);
+    constexpr int I1 = first_iter_of_band<KS, SHB>(1), I2 = first_iter_of_band<KS, SHB>(2);
+    constexpr int J1 = first_iter_of_band_up<KS, SHB, SLACK>(1), J0 = first_iter_of_band_up<KS, SHB, SLACK>(0);
     int bad = 0;
     for (int idx = 0; idx < RW * RW; ++idx) {
         const int i = idx / NT;  // loop iteration of the pixel
@@ -80,10 +80,11 @@ static int check(const char *tname)
         for (int r = lo; r <= hi && r >= 0 && r < SS::SHT; ++r)
             if (!landed[r / SHB]) ++bad;
     }
-    const long mine = tap_conflicts<T, KR>(UP), other = tap_conflicts<T, KR>(!UP);
+    const long mine = tap_conflicts<T, KS>(UP), other = tap_conflicts<T, KS>(!UP);
     const bool order_ok = mine <= other;
-    printf("%s KR %2d SP %3d order %s slack %d unlanded/out-of-box reads %d conflicts %ld (other order %ld)%s\n",
-           tname, KR, SS::SP, UP ? "up  " : "down", SLACK, bad, mine, other, bad || !order_ok ? " FAIL" : "");
+    printf("%s KR %2d edge %2d SP %3d order %s slack %d unlanded/out-of-box reads %d conflicts %ld (other order "
+           "%ld)%s\n",
+           tname, BS::R, BS::TS, SS::SP, UP ? "up  " : "down", SLACK, bad, mine, other, bad || !order_ok ? " FAIL" : "");
     return bad || !order_ok;
 }
 
@@ -91,7 +92,9 @@ template <typename T>
 static int all(const char *n)
 {
     return check<T, 1>(n) + check<T, 2>(n) + check<T, 3>(n) + check<T, 4>(n) + check<T, 5>(n) + check<T, 6>(n) +
-           check<T, 7>(n) + check<T, 8>(n) + check<T, 9>(n) + check<T, 10>(n);
+           check<T, 7>(n) + check<T, 8>(n) + check<T, 9>(n) + check<T, 10>(n) + check<T, 17>(n) +
+           check<T, 18>(n) + check<T, 19>(n) + check<T, 20>(n) + check<T, 21>(n) + check<T, 22>(n) +
+           check<T, 23>(n) + check<T, 24>(n) + check<T, 25>(n) + check<T, 26>(n);
 }
 
 int main()

@@ -51,6 +51,7 @@ def test_defaults_follow_the_documented_values():
                                                                       ofv.OFV_PATH_FUSED, 0)
     assert abs(p.det_rel_eps - 1e-6) < 1e-12 and abs(p.norm_eps - 1e-2) < 1e-9
     assert (p.window, p.window_sigma, p.increment_form, p.warm_start) == (ofv.OFV_WINDOW_BOX, 0.0, 0, 0)
+    assert p.tile_edge == 0
 
 
 @pytest.mark.parametrize("cname,mirror", [("ofv_params", "Params"), ("ofv_pair", "Pair")])
@@ -76,10 +77,22 @@ def test_struct_layout_matches_the_header(tmp_path, cname, mirror):
     ("iterations", 0), ("iterations", 65), ("norm_radius", -1), ("input", 7), ("storage", 3),
     ("path", 3), ("prefilter", 2), ("bit_depth", 0), ("bit_depth", 17), ("det_rel_eps", float("nan")),
     ("norm_eps", 0.0), ("max_batch", -1), ("max_batch", 9), ("window", 2), ("window", -1),
-    ("increment_form", 2), ("warm_start", -1), ("warm_start", 57),
+    ("increment_form", 2), ("warm_start", -1), ("warm_start", 57), ("tile_edge", -1), ("tile_edge", 40),
+    ("tile_edge", 16), ("tile_edge", 64),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(field, value):
     p = ofv.ofv_default_params(**{field: value})
+    with pytest.raises(ofv.OfvError) as ei:
+        ofv.ofv_create(1024, 1024, p)
+    assert ei.value.status == ofv.OFV_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(kernel_radius=12, tile_edge=48), dict(path=ofv.OFV_PATH_PLAIN, tile_edge=32),
+                                dict(kernel_radius=6, tile_edge=48), dict(kernel_radius=8, tile_edge=48)])
+def test_tile_edge_must_be_one_of_the_radius_edges_on_the_block_path(kw):
+    """The block kernel (fused path, KR 1..10) has two tile edges per radius:
+    48 or 32 for KR <= 5, 32 or 64 for KR 6, 64 or 32 for KR 7..10."""
+    p = ofv.ofv_default_params(levels_psl=1, **kw)
     with pytest.raises(ofv.OfvError) as ei:
         ofv.ofv_create(1024, 1024, p)
     assert ei.value.status == ofv.OFV_ERR_INVALID_ARG

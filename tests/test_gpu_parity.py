@@ -288,6 +288,38 @@ def test_every_window_radius(kr):
     compare(u, v, ou, ov, nd, label=f"kr={kr}", max_masked=mask_max(kr), sens=sens)
 
 
+def alt_tile_edge(kr):
+    """The block kernel's alternative output tile edge for radius kr."""
+    return 64 if kr == 6 else 32
+
+
+@pytest.mark.parametrize("kr", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+def test_alternative_tile_edge_every_radius(kr):
+    """The alternative tile shape (tile_edge) of every block-kernel radius
+    against the oracle on a ragged 200x330 field (several tiles and a partial
+    tile in both directions), and against the default shape: the window sums
+    are taken in another order, so the two agree to FP32 rounding."""
+    I1, I2 = synth.translation_pair(200, 330, (1.7, 0.8), seed=70 + kr, kind=synth.OUT_F32)
+    kw = dict(levels_psl=1, kernel_radius=kr, iterations=2)
+    u, v = gpu_flow(I1, I2, tile_edge=alt_tile_edge(kr), **kw)
+    ou, ov, nd, _ = oracle_flow(I1, I2, psl=1, kr=kr, it=2)
+    sens = fp32_sensitivity(I1, I2, psl=1, kr=kr, it=2) if kr <= 2 else None
+    compare(u, v, ou, ov, nd, label=f"kr={kr} edge {alt_tile_edge(kr)}", max_masked=mask_max(kr), sens=sens)
+    u0, v0 = gpu_flow(I1, I2, **kw)
+    m = nd >= NDET_MIN
+    if sens is not None:
+        m &= sens <= 0.1 * FP32_TOL
+    assert max(np.abs(u - u0)[m].max(), np.abs(v - v0)[m].max()) <= FP32_TOL
+
+
+@pytest.mark.parametrize("storage", [ofv.OFV_STORE_F16, ofv.OFV_STORE_BF16])
+def test_alternative_tile_edge_reduced_storage(storage):
+    I1, I2, _, _ = synth.turbulence_pair(384, 512, seed=21)
+    u, v = gpu_flow(I1, I2, storage=storage, tile_edge=32, **PARAMS)
+    ou, ov, nd, _ = oracle_flow(I1, I2)
+    compare(u, v, ou, ov, nd, rms_tol=REDUCED_RMS_TOL, label=f"edge 32 store={storage}")
+
+
 def test_u8_input_with_paper_benchmark_parameters():
     """NR 2, KR 10, IT 3 on 8-bit frames (the parameter set of the paper's
     throughput benchmark, Sec. 6), PSL 1."""
@@ -540,9 +572,11 @@ def test_batched_uneven_sizes_match_per_pair_compute_and_oracle(storage):
             dev_pairs.append((t1, t2, u, v))
         ofv.ofv_compute_batched(h, dev_pairs)
         tun = ofv.ofv_batch_tuning(h)
-        assert tun["tuned"] and tun["ms"] > 0
+        assert tun["tuned"] and tun["ms"] > 0 and tun["tile_edge"] in (32, 48)
+        # each pair against ofv_compute with the tile edge the tuner chose
+        pp = ofv.ofv_default_params(storage=storage, tile_edge=tun["tile_edge"], **PARAMS)
         for (t1, t2, u, v), (H, W) in zip(dev_pairs, sizes):
-            hh = ofv.ofv_create(H, W, p)
+            hh = ofv.ofv_create(H, W, pp)
             ru = torch.empty((H, W), device=DEV); rv = torch.empty_like(ru)
             ofv.ofv_compute(hh, t1, t2, ru, rv)
             torch.cuda.synchronize()
@@ -557,6 +591,36 @@ def test_batched_uneven_sizes_match_per_pair_compute_and_oracle(storage):
             ou, ov, nd, _ = oracle_flow(I1, I2)
             kw = dict(rms_tol=REDUCED_RMS_TOL) if storage != ofv.OFV_STORE_F32 else {}
             compare(u.cpu().numpy(), v.cpu().numpy(), ou, ov, nd, label=f"batched {I1.shape}", **kw)
+    finally:
+        ofv.ofv_destroy(h)
+
+
+@pytest.mark.parametrize("edge", [48, 32])
+def test_batched_with_a_fixed_tile_edge(edge):
+    """tile_edge on the batched handle fixes the tile shape of the persistent
+    launch (the tuner then picks the schedule only): every pair bitwise equal
+    to ofv_compute with the same edge, and the first pair against the oracle."""
+    sizes = [(256, 256), (300, 420), (96, 640), (513, 257)]
+    data = _uneven_pairs(sizes, seed0=300)
+    p = ofv.ofv_default_params(tile_edge=edge, **PARAMS)
+    h = ofv.ofv_create(64, 64, p)
+    try:
+        bufs = []
+        for (I1, I2), (H, W) in zip(data, sizes):
+            bufs.append((torch.from_numpy(I1).to(DEV), torch.from_numpy(I2).to(DEV),
+                         torch.full((H, W), float("nan"), device=DEV), torch.full((H, W), float("nan"), device=DEV)))
+        ofv.ofv_compute_batched(h, bufs)
+        assert ofv.ofv_batch_tuning(h)["tile_edge"] == edge
+        for (t1, t2, u, v), (H, W) in zip(bufs, sizes):
+            hh = ofv.ofv_create(H, W, p)
+            ru = torch.empty((H, W), device=DEV); rv = torch.empty_like(ru)
+            ofv.ofv_compute(hh, t1, t2, ru, rv)
+            torch.cuda.synchronize()
+            ofv.ofv_destroy(hh)
+            assert torch.equal(u, ru) and torch.equal(v, rv), f"{H}x{W} edge {edge}"
+        I1, I2 = data[0]
+        ou, ov, nd, _ = oracle_flow(I1, I2)
+        compare(bufs[0][2].cpu().numpy(), bufs[0][3].cpu().numpy(), ou, ov, nd, label=f"batched edge {edge}")
     finally:
         ofv.ofv_destroy(h)
 

@@ -84,6 +84,15 @@ def test_paper_parameters_two_strips():
     assert torch.equal(us, u) and torch.equal(vs, v)
 
 
+@pytest.mark.parametrize("kr,edge", [(4, 32), (10, 32), (6, 64)])
+def test_alternative_tile_edge_strips(kr, edge):
+    """The strips own whole rows of the tile grid of the shape tile_edge
+    selects."""
+    F = synth.stream_frames(700, 900, 2, seed=11)
+    (u, v), (us, vs) = _both(F[0], F[1], 3, 8, kernel_radius=kr, tile_edge=edge)
+    assert torch.equal(us, u) and torch.equal(vs, v)
+
+
 def test_strips_refuse_a_mask_and_bad_counts():
     h = ofv.ofv_create(128, 128, ofv.ofv_default_params(input=ofv.OFV_IN_F32))
     try:

@@ -36,7 +36,8 @@ def test_oversize_and_invalid_requests_are_rejected_before_any_device_work():
         ofv.ofv_compute_noalloc(256, 256, ofv.ofv_default_params(path=ofv.OFV_PATH_PLAIN), None, 16, 32, 48, 64, 0)
     assert ei.value.status == ofv.OFV_ERR_UNSUPPORTED
     # the fields ofv_create range-checks are range-checked here too
-    for field, bad in (("max_batch", -1), ("max_batch", 9), ("warm_start", -1), ("warm_start", 57)):
+    for field, bad in (("max_batch", -1), ("max_batch", 9), ("warm_start", -1), ("warm_start", 57),
+                       ("tile_edge", 40)):
         q = ofv.ofv_default_params(**{field: bad})
         with pytest.raises(ofv.OfvError) as ei:
             ofv.ofv_compute_noalloc(256, 256, q, None, 16, 32, 48, 64, 0)
@@ -117,16 +118,17 @@ def test_noalloc_matches_the_oracle():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("storage,kr", [(ofv.OFV_STORE_F16, 4), (ofv.OFV_STORE_BF16, 4), (ofv.OFV_STORE_F32, 12)])
-def test_noalloc_reduced_storage_and_large_radius(storage, kr):
-    """16-bit level storage (2 bytes per sample in the scratch layout) and a
-    radius above 10 (the tile kernel instead of the block kernel), bitwise
-    against ofv_compute on two calls in a row."""
+@pytest.mark.parametrize("storage,kr,edge", [(ofv.OFV_STORE_F16, 4, 0), (ofv.OFV_STORE_BF16, 4, 0),
+                                             (ofv.OFV_STORE_F32, 12, 0), (ofv.OFV_STORE_F32, 4, 32)])
+def test_noalloc_reduced_storage_and_large_radius(storage, kr, edge):
+    """16-bit level storage (2 bytes per sample in the scratch layout), a
+    radius above 10 (the tile kernel instead of the block kernel) and the
+    alternative tile edge, bitwise against ofv_compute on two calls in a row."""
     torch = _torch()
     lib = _lib()
     H, W = 300, 420
     frames = torch.from_numpy(synth.stream_frames(H, W, 3, seed=9)).to("cuda")
-    p = ofv.ofv_default_params(storage=storage, kernel_radius=kr, levels_psl=1 if kr > 10 else 2)
+    p = ofv.ofv_default_params(storage=storage, kernel_radius=kr, levels_psl=1 if kr > 10 else 2, tile_edge=edge)
     for k in range(2):
         u_ref, v_ref = _compute(torch, H, W, p, frames[k], frames[k + 1])
         u, v = _noalloc(torch, lib, H, W, p, frames[k], frames[k + 1])
