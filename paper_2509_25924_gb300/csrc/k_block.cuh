@@ -348,6 +348,30 @@ __device__ __forceinline__ Sample2 bilin_weighted2(const T *__restrict__ rm1, co
     return s;
 }
 
+// The five products of one pixel from the staged tile: frame 2 sampled at
+// integer offset (ix, iy) with fractions (fx2, fy2), frame 1 at -(ix, iy) - 1
+// with fractions 1 - (fx2, fy2); base indexes the staged element left of and
+// above the pixel.
+template <typename T, int SP, bool VAR>
+__device__ __forceinline__ void products_staged(const T *__restrict__ st1, const T *__restrict__ st2, int base, int ix,
+                                                int iy, float fx2, float fy2, const IterArgs &a, float2 V0, float p[5])
+{
+    const int off = iy * SP + ix;
+    const Sample2 s12 = bilin_weighted2<T, SP>(st1 + (base - off - SP - 1), st2 + (base + off),
+                                               make_float2(fx2, 1.f - fx2), make_float2(1.f - fx2, fx2),
+                                               make_float2(fy2, 1.f - fy2), make_float2(1.f - fy2, fy2));
+    // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4
+    const float Gx = 0.25f * (s12.gx.x + s12.gx.y);
+    const float Gy = 0.25f * (s12.gy.x + s12.gy.y);
+    const float It = s12.val.y - s12.val.x;
+    const float r = (VAR && a.inc) ? -It : Gx * V0.x + Gy * V0.y - It;
+    p[0] = Gx * Gx;
+    p[1] = Gx * Gy;
+    p[2] = Gy * Gy;
+    p[3] = Gx * r;
+    p[4] = Gy * r;
+}
+
 // Products of one pixel (x, y) of a tile whose staged region lies inside
 // the image: no clamping or border remap is needed while the warp stays
 // within REACH px.  Frame 2 samples at k + h with integer part (ix, iy) =
@@ -363,31 +387,39 @@ __device__ __forceinline__ void products_interior(const T *__restrict__ st1, con
     const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
     const float flx = floorf(hx), fly = floorf(hy);
     const int ix = (int)flx, iy = (int)fly;
-    float Gx, Gy, It;
     if (((unsigned)(ix + kBlockReach) | (unsigned)(iy + kBlockReach)) < (unsigned)(2 * kBlockReach)) {
-        const float fx2 = hx - flx, fy2 = hy - fly;
-        const int base = (y - 1 - sy0) * SP + (x - 1 - sx0), off = iy * SP + ix;
-        const Sample2 s12 = bilin_weighted2<T, SP>(st1 + (base - off - SP - 1), st2 + (base + off),
-                                                   make_float2(fx2, 1.f - fx2), make_float2(1.f - fx2, fx2),
-                                                   make_float2(fy2, 1.f - fy2), make_float2(1.f - fy2, fy2));
-        // doubled gradients: G = (g1 + g2) / 2 = (2 g1 + 2 g2) / 4
-        Gx = 0.25f * (s12.gx.x + s12.gx.y);
-        Gy = 0.25f * (s12.gy.x + s12.gy.y);
-        It = s12.val.y - s12.val.x;
+        products_staged<T, SP, VAR>(st1, st2, (y - 1 - sy0) * SP + (x - 1 - sx0), ix, iy, hx - flx, hy - fly, a, V0,
+                                    p);
     } else {
         const T *P1 = static_cast<const T *>(a.P1), *P2 = static_cast<const T *>(a.P2);
         const Sample s1 = sample_global(P1, a.H, a.W, a.pitch, x, y, -hx, -hy);
         const Sample s2 = sample_global(P2, a.H, a.W, a.pitch, x, y, hx, hy);
-        Gx = 0.5f * (s1.gx + s2.gx);
-        Gy = 0.5f * (s1.gy + s2.gy);
-        It = s2.val - s1.val;
+        const float Gx = 0.5f * (s1.gx + s2.gx), Gy = 0.5f * (s1.gy + s2.gy);
+        const float It = s2.val - s1.val;
+        const float r = (VAR && a.inc) ? -It : Gx * V0.x + Gy * V0.y - It;
+        p[0] = Gx * Gx;
+        p[1] = Gx * Gy;
+        p[2] = Gy * Gy;
+        p[3] = Gx * r;
+        p[4] = Gy * r;
     }
-    const float r = (VAR && a.inc) ? -It : Gx * V0.x + Gy * V0.y - It;
-    p[0] = Gx * Gx;
-    p[1] = Gx * Gy;
-    p[2] = Gy * Gy;
-    p[3] = Gx * r;
-    p[4] = Gy * r;
+}
+
+// The same without the branch to the general sampler: returns false, with
+// products of an in-reach stand-in offset, when the warp leaves the staged
+// margin; the caller then recomputes the pixel with products_interior.
+// Keeps the hot loop free of a divergent branch and a call.
+template <typename T, int SP, bool VAR = false>
+__device__ __forceinline__ bool products_staged_only(const T *__restrict__ st1, const T *__restrict__ st2, int sx0,
+                                                     int sy0, const IterArgs &a, int x, int y, float2 V0, float p[5])
+{
+    const float hx = 0.5f * V0.x, hy = 0.5f * V0.y;
+    const float flx = floorf(hx), fly = floorf(hy);
+    const int ix = (int)flx, iy = (int)fly;
+    const bool near = ((unsigned)(ix + kBlockReach) | (unsigned)(iy + kBlockReach)) < (unsigned)(2 * kBlockReach);
+    products_staged<T, SP, VAR>(st1, st2, (y - 1 - sy0) * SP + (x - 1 - sx0), near ? ix : 0, near ? iy : 0, hx - flx,
+                                hy - fly, a, V0, p);
+    return near;
 }
 
 // Phase 1 of a tile whose staged box lies inside the image: every pixel of
@@ -430,6 +462,7 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
     static_assert(SS::NBAND == 3, "three staging bands");
+    static_assert((BS::RW * BS::RW + BS::NT - 1) / BS::NT <= 32, "one bit per pixel of a thread");
     constexpr int NT = BS::NT, RW = BS::RW, RWP = BS::RWP, PLANE = RW * RWP;
     constexpr bool UP = RowOrder<T, KR>::bottom_up;
     constexpr int DX = NT % RW, DY = UP ? -(NT / RW) : NT / RW, DW = UP ? -1 : 1;
@@ -448,6 +481,7 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
             mbar_wait_bounded(bars + b, parity, 1000000000LL);
         }
     };
+    unsigned far = 0, bit = 1;  // bit k: the thread's k-th pixel left the staged margin
     auto pixel = [&](int idx) {
         const float2 V0c = V0n;
         const int gx = px0 + rx, gy = py0 + ry;
@@ -460,7 +494,8 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
         }
         if (idx + NT < RW * RW) V0n = fetch_v0_ct<COH, MODE>(a, px0 + rx, py0 + ry);
         float p[5];
-        products_interior<T, SP, VAR>(st1, st2, sx0, sy0, a, gx, gy, V0c, p);
+        if (!products_staged_only<T, SP, VAR>(st1, st2, sx0, sy0, a, gx, gy, V0c, p)) far |= bit;
+        bit <<= 1;
         if (VAR && a.mask && !__ldg(a.mask + (int64_t)gy * a.W + gx)) p[0] = p[1] = p[2] = p[3] = p[4] = 0.f;
         q[0] = p[0];
         q[PLANE] = p[1];
@@ -483,6 +518,23 @@ __device__ __forceinline__ void products_tile_interior(const IterArgs &a, const 
         wait_band(2);
     }
     for (; idx < RW * RW; idx += NT) pixel(idx);
+    // the pixels whose warp left the staged margin (rare), again with the
+    // general sampler; the thread's k-th pixel is tid + k NT
+    for (int k = 0; far != 0; ++k, far >>= 1) {
+        if (!(far & 1u)) continue;
+        const int i = tid + k * NT;
+        const int py = UP ? RW - 1 - i / RW : i / RW, px = i - (i / RW) * RW;
+        const int gx = px0 + px, gy = py0 + py;
+        float p[5];
+        products_interior<T, SP, VAR>(st1, st2, sx0, sy0, a, gx, gy, fetch_v0_ct<COH, MODE>(a, gx, gy), p);
+        if (VAR && a.mask && !__ldg(a.mask + (int64_t)gy * a.W + gx)) p[0] = p[1] = p[2] = p[3] = p[4] = 0.f;
+        float *q = prod + py * RWP + px;
+        q[0] = p[0];
+        q[PLANE] = p[1];
+        q[2 * PLANE] = p[2];
+        q[3 * PLANE] = p[3];
+        q[4 * PLANE] = p[4];
+    }
 }
 
 // Window sums of one line of the product planes, in place: for outputs
