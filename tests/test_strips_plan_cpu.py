@@ -25,9 +25,10 @@ import torch.multiprocessing as mp  # noqa: E402
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
-CASES = [  # H, W, PSL, KR, NR, prefilter, max_disp
-    (4096, 5120, 2, 4, 0, 0, 8), (1024, 1024, 2, 4, 0, 0, 6), (300, 200, 2, 4, 2, 1, 6), (2048, 2048, 2, 10, 2, 0, 16),
-    (97, 131, 1, 3, 0, 0, 4), (600, 80, 3, 2, 1, 0, 20),
+CASES = [  # H, W, PSL, KR, NR, prefilter, max_disp, tile_edge (0: the radius's default)
+    (4096, 5120, 2, 4, 0, 0, 8, 0), (1024, 1024, 2, 4, 0, 0, 6, 0), (300, 200, 2, 4, 2, 1, 6, 0),
+    (2048, 2048, 2, 10, 2, 0, 16, 0), (97, 131, 1, 3, 0, 0, 4, 0), (600, 80, 3, 2, 1, 0, 20, 0),
+    (1024, 1024, 2, 4, 0, 0, 6, 32), (700, 900, 2, 6, 0, 0, 8, 64), (2048, 2048, 2, 10, 2, 0, 16, 32),
 ]
 
 
@@ -42,12 +43,12 @@ def _worker(rank, ws, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     import paper_2509_25924_gb300 as ofv
     results = []
-    for (H, W, psl, kr, nr, pf, md) in CASES:
-        p = ofv.ofv_default_params(levels_psl=psl, kernel_radius=kr, norm_radius=nr, prefilter=pf)
+    for (H, W, psl, kr, nr, pf, md, te) in CASES:
+        p = ofv.ofv_default_params(levels_psl=psl, kernel_radius=kr, norm_radius=nr, prefilter=pf, tile_edge=te)
         mine = [ofv.ofv_strip_plan(H, W, p, ws, md, l, rank) for l in range(psl + 1)]
         plans = [None] * ws
         dist.all_gather_object(plans, mine)  # rank k's plan, as rank k computed it
-        results.append(_check(ofv, H, W, psl, kr, nr, pf, md, rank, ws, plans))
+        results.append(_check(ofv, H, W, psl, kr, nr, pf, md, te, rank, ws, plans))
     dist.barrier()
     q.put((rank, results))
     dist.destroy_process_group()
@@ -57,8 +58,8 @@ def _inside(r, outer):
     return r[0] >= r[1] or (outer[0] <= r[0] and r[1] <= outer[1])
 
 
-def _check(ofv, H, W, psl, kr, nr, pf, md, rank, ws, plans):
-    ts = 48 if kr <= 5 else (32 if kr == 6 else 64)  # the block kernel's tile edge
+def _check(ofv, H, W, psl, kr, nr, pf, md, te, rank, ws, plans):
+    ts = te or (48 if kr <= 5 else (32 if kr == 6 else 64))  # the block kernel's tile edge
     Hs = [H]
     for _ in range(psl):
         Hs.append((Hs[-1] + 1) // 2)
