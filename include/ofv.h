@@ -111,8 +111,8 @@ typedef struct {
                            multiple d = m B (m <= 7, device sequences only): groups of B pairs, each
                            waiting for the group m back, so the m - 1 groups between still overlap. */
     int tile_edge;      /* fused block kernel (KR 1..10) output tile edge in px: 0 = the radius's default
-                           (48 for KR <= 5, 32 for KR 6, 64 for KR 7..10); or its alternative (32 for
-                           KR != 6, 64 for KR 6).  With 0, ofv_compute_batched's autotuner picks one of
+                           (48 for KR <= 5, 64 for KR 6..10); or the alternative, 32.  With 0,
+                           ofv_compute_batched's autotuner picks one of
                            the two per batch signature (ofv_batch_tuning reports it); nonzero fixes it.
                            The window sums' rounding follows the tile grid, so fields of different tile
                            edges agree to FP32 rounding, not bitwise.  The estimator variants (Gaussian

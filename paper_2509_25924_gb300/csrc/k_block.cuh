@@ -2,7 +2,7 @@
 // kernel behind OFV_PATH_FUSED for window radii 1..10.
 //
 // One CTA owns a TS x TS tile of output pixels (by default 48 px for
-// KR <= 5, 32 for KR 6 and 64 for KR 7..10; see block_tile_edge) and works
+// KR <= 5 and 64 for KR 6..10; see block_tile_edge) and works
 // entirely on chip in five phases:
 //   0. stage the two level images over the tile, its KR window halo, a
 //      REACH px warp margin and the gradient stencil into shared memory:
@@ -52,23 +52,22 @@ __host__ __device__ constexpr int ks_radius(int ks) { return ks & 15; }
 __host__ __device__ constexpr int ks_shape(int ks) { return ks >> 4; }
 
 // Output tile edge of shape v for radius kr.  Default shapes, measured per
-// radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles, two CTAs per SM
-// (64-px tiles at one CTA per SM: -15..-18 %); KR 6: 32-px tiles, two CTAs
-// per SM (64 px: -2.5 %); KR 7..10: 64-px tiles, one CTA of 1024 threads
-// per SM (less halo work: +21..26 % against 32 or 48 px; 1024 threads
-// instead of 512: +13 % at KR 10).  Alternatives: 32-px tiles of 256
-// threads (KR 6: 64-px tiles of 512 threads).
+// radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles of 512 threads, two
+// CTAs per SM (64-px tiles at one CTA per SM: -15..-18 %); KR 6..10: 64-px
+// tiles, one CTA of 1024 threads per SM (less halo work: +21..26 % against
+// 32 or 48 px at KR 7..10, +13.5 % against 32 px at KR 6; 1024 threads
+// instead of 512: +13 % at KR 10).  Alternative: 32-px tiles of 256 threads.
 __host__ __device__ constexpr int block_tile_edge(int kr, int v)
 {
-    return v == 0 ? (kr <= 5 ? 48 : kr == 6 ? 32 : 64) : (kr == 6 ? 64 : 32);
+    return v == 0 ? (kr <= 5 ? 48 : 64) : 32;
 }
 
 template <int KS> struct BlockShape {
     static constexpr int R = ks_radius(KS);                // window radius
     static constexpr int TS = block_tile_edge(R, ks_shape(KS));  // output tile edge
-    static constexpr int NT = TS == 32 ? 256 : (TS == 64 && R >= 7) ? 1024 : 512;  // threads
+    static constexpr int NT = TS == 32 ? 256 : TS == 48 ? 512 : 1024;  // threads
     // resident CTAs per SM (shared memory)
-    static constexpr int MINB = TS == 32 ? (R <= 5 ? 3 : 2) : TS == 48 ? 2 : (R <= 6 && ks_shape(KS) == 0 ? 2 : 1);
+    static constexpr int MINB = TS == 32 ? (R <= 5 ? 3 : 2) : TS == 48 ? 2 : 1;
     static constexpr int RW = TS + 2 * R;                 // product region edge
     static constexpr int RWP = RW | 1;                    // odd row pitch of the product planes
     static constexpr int SH = RW + 2 * kBlockReach + 3;   // staged rows

@@ -91,7 +91,7 @@ def test_invalid_parameters_are_rejected_on_the_host(field, value):
                                 dict(kernel_radius=6, tile_edge=48), dict(kernel_radius=8, tile_edge=48)])
 def test_tile_edge_must_be_one_of_the_radius_edges_on_the_block_path(kw):
     """The block kernel (fused path, KR 1..10) has two tile edges per radius:
-    48 or 32 for KR <= 5, 32 or 64 for KR 6, 64 or 32 for KR 7..10."""
+    48 or 32 for KR <= 5, 64 or 32 for KR 6..10."""
     p = ofv.ofv_default_params(levels_psl=1, **kw)
     with pytest.raises(ofv.OfvError) as ei:
         ofv.ofv_create(1024, 1024, p)

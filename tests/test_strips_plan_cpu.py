@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 CASES = [  # H, W, PSL, KR, NR, prefilter, max_disp, tile_edge (0: the radius's default)
     (4096, 5120, 2, 4, 0, 0, 8, 0), (1024, 1024, 2, 4, 0, 0, 6, 0), (300, 200, 2, 4, 2, 1, 6, 0),
     (2048, 2048, 2, 10, 2, 0, 16, 0), (97, 131, 1, 3, 0, 0, 4, 0), (600, 80, 3, 2, 1, 0, 20, 0),
-    (1024, 1024, 2, 4, 0, 0, 6, 32), (700, 900, 2, 6, 0, 0, 8, 64), (2048, 2048, 2, 10, 2, 0, 16, 32),
+    (1024, 1024, 2, 4, 0, 0, 6, 32), (700, 900, 2, 6, 0, 0, 8, 32), (2048, 2048, 2, 10, 2, 0, 16, 32),
 ]
 
 
@@ -59,7 +59,7 @@ def _inside(r, outer):
 
 
 def _check(ofv, H, W, psl, kr, nr, pf, md, te, rank, ws, plans):
-    ts = te or (48 if kr <= 5 else (32 if kr == 6 else 64))  # the block kernel's tile edge
+    ts = te or (48 if kr <= 5 else 64)  # the block kernel's tile edge
     Hs = [H]
     for _ in range(psl):
         Hs.append((Hs[-1] + 1) // 2)
