@@ -52,8 +52,9 @@ __host__ __device__ constexpr int ks_radius(int ks) { return ks & 15; }
 __host__ __device__ constexpr int ks_shape(int ks) { return ks >> 4; }
 
 // Output tile edge of shape v for radius kr.  Default shapes, measured per
-// radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles of 512 threads, two
-// CTAs per SM (64-px tiles at one CTA per SM: -15..-18 %); KR 6..10: 64-px
+// radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles of 576 threads, two
+// CTAs per SM, 56 registers (512 threads: -2 %; 640: no gain, 48 registers
+// and spills; 64-px tiles at one CTA per SM: -15..-18 %); KR 6..10: 64-px
 // tiles, one CTA of 1024 threads per SM (less halo work: +21..26 % against
 // 32 or 48 px at KR 7..10, +13.5 % against 32 px at KR 6; 1024 threads
 // instead of 512: +13 % at KR 10).  Alternative: 32-px tiles of 256 threads.
@@ -65,7 +66,7 @@ __host__ __device__ constexpr int block_tile_edge(int kr, int v)
 template <int KS> struct BlockShape {
     static constexpr int R = ks_radius(KS);                // window radius
     static constexpr int TS = block_tile_edge(R, ks_shape(KS));  // output tile edge
-    static constexpr int NT = TS == 32 ? 256 : TS == 48 ? 512 : 1024;  // threads
+    static constexpr int NT = TS == 32 ? 256 : TS == 48 ? 576 : 1024;  // threads
     // resident CTAs per SM (shared memory)
     static constexpr int MINB = TS == 32 ? (R <= 5 ? 3 : 2) : TS == 48 ? 2 : 1;
     static constexpr int RW = TS + 2 * R;                 // product region edge
