@@ -126,8 +126,11 @@ typedef struct ofv_handle ofv_handle;
    box window, direct form, no warm start. */
 void ofv_default_params(ofv_params *p);
 
-/* Create a handle for H x W frames with parameters *p (copied).  Allocates
-   the whole workspace on the current device.  Every level must be at least
+/* Create a handle for H x W frames with parameters *p (copied): the
+   parameters of Sec. 2 and Sec. 6 (pyramid levels PSL, window radius KR,
+   iterations IT, normalization radius NR).  Allocates the whole workspace
+   on the current device: the level images of the pyramid (Sec. 2, step 2)
+   and the displacement fields of the iterations (Eq. 2).  Every level must be at least
    max(8, 2KR+1) pixels in both dimensions (else OFV_ERR_SHAPE); H * W must
    not exceed 2^31 - 1.  On failure *out is set to NULL and nothing leaks. */
 ofv_status ofv_create(int H, int W, const ofv_params *p, ofv_handle **out);
@@ -153,8 +156,11 @@ ofv_status ofv_set_prefilter(ofv_handle *h, const float *w25, ofv_stream_t s);
 ofv_status ofv_set_mask(ofv_handle *h, const uint8_t *mask, ofv_stream_t s);
 
 /* Estimate the displacement field between frames I1 (time t) and I2 (time
-   t + dt), both H x W of the handle's input type.  Writes u and v (H x W
-   float each).  I1, I2, u and v are device pointers; u and v must not alias
+   t + dt), both H x W of the handle's input type: Sec. 2 steps 1-6 (local
+   normalization, the pyramid, and per level IT Gauss-Newton iterations of
+   the symmetric SSD of Eq. 2 with the window sums of its normal equations),
+   giving V = (u, v) in px per frame, the velocity of Eq. 1 times dt.
+   Writes u and v (H x W float each).  I1, I2, u and v are device pointers; u and v must not alias
    the inputs. */
 ofv_status ofv_compute(ofv_handle *h, const void *I1, const void *I2, float *u, float *v,
                        ofv_stream_t s);
@@ -329,15 +335,18 @@ typedef struct {
 
 /* Estimate n pairs of any sizes (each within the shape limits of
  * ofv_create for the handle's parameters; the handle's own H, W do not
- * matter) with the handle's parameters, 1 <= n <= 32767.  pairs is a HOST array.  The frames
- * are ingested and reduced size class by size class, then every (level,
+ * matter) with the handle's parameters, 1 <= n <= 32767: the estimator of
+ * Sec. 2 (steps 1-6, Eq. 2) for every pair, as ofv_compute computes it.
+ * pairs is a HOST array.  All 2n frames are ingested by one launch and each
+ * pyramid level of all of them is reduced by one launch; then every (level,
  * iteration, tile) of every pair runs in ONE persistent launch of the fused
  * kernel: CTAs take work units from a queue in the order of a schedule, and
  * a unit of one Gauss-Newton iteration waits (bounded) until the previous
  * iteration of its pair is complete.  The first batch of a given signature
- * (sorted sizes and parameters) runs the autotuner: each candidate schedule
- * (all pairs stage by stage, or groups of 8 pairs) and persistent grid (one
- * or two CTAs per SM) is timed on the batch itself and the fastest is kept
+ * (sorted sizes and parameters) runs the autotuner: each candidate -- tile
+ * shape (see ofv_params.tile_edge), schedule (all pairs stage by stage, or
+ * groups of 8 pairs) and persistent grid (the resident CTAs per SM, or one
+ * fewer) -- is timed on the batch itself and the fastest is kept
  * for later batches of that signature (that first call waits for its
  * timings).  Otherwise the call enqueues the batch on s and returns; the
  * fields are valid once s reaches them, and the next call's host work
@@ -452,7 +461,9 @@ ofv_status ofv_profile_enable(ofv_handle *h, int enable);
 ofv_status ofv_profile_read(ofv_handle *h, int k, double *total_ms, int64_t *launches,
                             double *alg_bytes);
 
-/* Message describing the most recent failure in the calling thread. */
+/* Message describing the most recent failure in the calling thread.  It
+   takes no handle: errors are recorded per thread, so a failed ofv_create
+   (which has no handle to return) reports through the same call. */
 const char *ofv_last_error(void);
 
 /* Name of a status code. */

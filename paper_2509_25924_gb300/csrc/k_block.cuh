@@ -661,11 +661,19 @@ using SolveStore = SolveStoreT<false>;
 // CTA; parity is the phase this tile's copies complete (the number of
 // earlier TMA tiles of the CTA, mod 2).  Returns true when the tile was
 // staged by TMA.
-template <typename T, int KR, bool COH, typename Epi = SolveStore, bool VAR = false>
+// Side work a caller may slot into the tile's phases: after_products(tid)
+// runs after phase 1's loop and after_rows(tid) after phase 2's, each before
+// the phase's closing barrier.
+struct NoSide {
+    __device__ __forceinline__ void after_products(int) const {}
+    __device__ __forceinline__ void after_rows(int) const {}
+};
+
+template <typename T, int KR, bool COH, typename Epi = SolveStore, bool VAR = false, typename Side = NoSide>
 __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, int by, float4 *smem_f4,
                                            const CUtensorMap *tm1 = nullptr, const CUtensorMap *tm2 = nullptr,
                                            int *err = nullptr, const Epi &epi = Epi(), uint64_t *tma_bars = nullptr,
-                                           unsigned parity = 0, bool init_bars = false)
+                                           unsigned parity = 0, bool init_bars = false, const Side &side = Side())
 {
     using BS = BlockShape<KR>;
     using SS = StageShape<T, KR>;
@@ -797,6 +805,7 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
             rx = nrx;
         }
     }
+    side.after_products(tid);
     __syncthreads();
 
     // phase 2: horizontal window sums, one (row, channel) per thread
@@ -812,6 +821,7 @@ __device__ __forceinline__ bool block_tile(const IterArgs &a, int mode, int bx, 
             window_sums_inplace<R, TS>(prod + c * PLANE + row * RWP, 1);
         }
     }
+    side.after_rows(tid);
     __syncthreads();
 
     // phase 3: vertical window sums, one (column, channel) per thread
@@ -877,9 +887,8 @@ struct BatchPair {
 
 struct QueueParams {
     const BatchPair *pairs;  // [npairs]
-    const int *group_off;    // [ngroups + 1] first unit of each (stage, pair) group
-    const int2 *group;       // [ngroups] (stage, pair)
-    int ngroups, total_units, npairs;
+    const int4 *unit_desc;   // [total_units] (stage, pair, tile, tiles of the pair's previous stage)
+    int total_units, npairs;
     int L, IT, kr;
     float eps_rel, eps_abs;
     int inc, gauss;          // estimator variants (as IterArgs)
@@ -901,42 +910,72 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
-template <int TS>
-__device__ __forceinline__ int tiles_of(int H, int W) { return ((W + TS - 1) / TS) * ((H + TS - 1) / TS); }
+// The persistent kernel's side work (see NoSide): thread 0 publishes the
+// unit it claimed for after this tile, and a thread with no line in the
+// row pass reads that unit's descriptor and looks once whether its
+// dependency is already complete, so the next unit starts without those
+// round trips.
+struct QueueSide {
+    const QueueParams *q;
+    int next;          // thread 0: the claimed next unit
+    int side_tid;      // the thread that prefetches
+    int *s_next;
+    int4 *s_dec;       // prefetched descriptor
+    int *s_dec_unit;   // its unit (-1: none)
+    int *s_dec_ok;     // 1: its dependency was seen complete
+    __device__ __forceinline__ void after_products(int tid) const
+    {
+        if (tid == 0) *s_next = next;
+    }
+    __device__ __forceinline__ void after_rows(int tid) const
+    {
+        if (tid != side_tid) return;
+        const int n = *s_next;
+        if (n >= q->total_units) return;
+        const int4 d = __ldg(q->unit_desc + n);
+        *s_dec_ok = d.x == 0 || ld_acquire(q->done + (d.x - 1) * q->npairs + d.y) >= d.w;
+        *s_dec = d;
+        *s_dec_unit = n;
+    }
+};
 
 template <typename T, int KR, bool VAR>
 __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_iter_queue(const __grid_constant__ QueueParams q)
 {
     constexpr int TS = BlockShape<KR>::TS;
     extern __shared__ __align__(128) float4 smem_f4[];
-    __shared__ int s_unit, s_fail;
+    __shared__ int s_unit, s_fail, s_next, s_dec_unit, s_dec_ok;
+    __shared__ int4 s_dec;
     __shared__ __align__(8) uint64_t s_bar[StageShape<T, KR>::NBAND];
     const int S = q.L * q.IT;
     unsigned tma_uses = 0;  // TMA-staged tiles of this CTA so far
     if (q.tmaps && threadIdx.x == 0)
         for (int b = 0; b < StageShape<T, KR>::NBAND; ++b) mbar_init(&s_bar[b], 1);  // visible after the loop's first barrier
+    if (threadIdx.x == 0) {
+        s_unit = atomicAdd(q.head, 1);
+        s_fail = 0;
+        s_dec_unit = -1;
+    }
+    __syncthreads();
+    // thread 0: the (stage, pair) whose previous stage it last saw complete
+    int checked = -1;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_unit = atomicAdd(q.head, 1);
-            s_fail = 0;
-        }
-        __syncthreads();
         const int unit = s_unit;
         if (unit >= q.total_units) break;
-        // (stage, pair) group of the unit: binary search in the offsets
-        int lo = 0, hi = q.ngroups - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(q.group_off + mid) <= unit) lo = mid; else hi = mid - 1;
-        }
-        const int2 sp = __ldg(q.group + lo);
-        const int s = sp.x, p = sp.y;
-        const int tile = unit - __ldg(q.group_off + lo);
+        // the unit's descriptor, prefetched during the previous tile when
+        // this CTA ran one
+        const bool pre = s_dec_unit == unit;
+        const int4 d = pre ? s_dec : __ldg(q.unit_desc + unit);
+        const bool pre_ok = pre && s_dec_ok;
+        const int s = d.x, p = d.y, tile = d.z, need = d.w;
+        const int key = s * q.npairs + p;
         const BatchPair &bp = q.pairs[p];
         const int l = q.L - 1 - s / q.IT, t = s % q.IT;
-        if (s > 0 && threadIdx.x == 0) {
-            const int lp = q.L - 1 - (s - 1) / q.IT;
-            const int need = tiles_of<TS>(bp.H[lp], bp.W[lp]);
+        // the next unit is claimed now and read after this tile, so the
+        // claim's round trip overlaps the tile's work
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(q.head, 1);
+        if (s > 0 && threadIdx.x == 0 && !pre_ok && checked != key) {
             const int *cnt = q.done + (s - 1) * q.npairs + p;
             const long long t0 = global_ns();
             int spins = 0;
@@ -949,6 +988,7 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_it
                 }
                 __nanosleep(128);
             }
+            checked = key;
         }
         __syncthreads();
         if (s_fail) break;
@@ -987,13 +1027,19 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_it
         }
         const int ntx = (a.W + TS - 1) / TS;
         const CUtensorMap *tm = q.tmaps ? q.tmaps + ((size_t)p * 16 + l) * 2 : nullptr;
-        if (block_tile<T, KR, true, SolveStoreT<VAR>, VAR>(a, mode, tile % ntx, tile / ntx, smem_f4, tm,
-                                                           tm ? tm + 1 : nullptr, q.tma_err, SolveStoreT<VAR>(),
-                                                           q.tmaps ? s_bar : nullptr, tma_uses & 1u))
+        const QueueSide side{&q, next, BlockShape<KR>::NT - 1, &s_next, &s_dec, &s_dec_unit, &s_dec_ok};
+        if (block_tile<T, KR, true, SolveStoreT<VAR>, VAR, QueueSide>(a, mode, tile % ntx, tile / ntx, smem_f4, tm,
+                                                                      tm ? tm + 1 : nullptr, q.tma_err,
+                                                                      SolveStoreT<VAR>(), q.tmaps ? s_bar : nullptr,
+                                                                      tma_uses & 1u, false, side))
             ++tma_uses;
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(q.done + s * q.npairs + p, 1);
+        if (threadIdx.x == 0) {
+            atomicAdd(q.done + key, 1);
+            s_unit = next;
+        }
+        __syncthreads();
     }
 }
 

@@ -77,20 +77,17 @@ struct DevGuard {
     }
 };
 
-// Unit list of one schedule: groups (stage, pair) with their first unit.
-void build_schedule(int schedule, int S, int n, const std::vector<std::vector<int>> &tiles, std::vector<int2> &group,
-                    std::vector<int> &off)
+// Unit list of one schedule, in claim order: per unit (stage, pair, tile,
+// tiles of the pair's previous stage -- the count its dependency waits for).
+void build_schedule(int schedule, int S, int n, const std::vector<std::vector<int>> &tiles, std::vector<int4> &desc)
 {
-    group.clear();
-    off.assign(1, 0);
+    desc.clear();
     const int chunk = schedule > 0 ? schedule : n;
     for (int c0 = 0; c0 < n; c0 += chunk) {
         const int c1 = std::min(n, c0 + chunk);
         for (int s = 0; s < S; ++s)
-            for (int p = c0; p < c1; ++p) {
-                group.push_back(make_int2(s, p));
-                off.push_back(off.back() + tiles[p][s]);
-            }
+            for (int p = c0; p < c1; ++p)
+                for (int t = 0; t < tiles[p][s]; ++t) desc.push_back(make_int4(s, p, t, s > 0 ? tiles[p][s - 1] : 0));
     }
 }
 
@@ -195,10 +192,17 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
     const size_t tmaps_off = off;  // [pair][16 levels][2 frames] tensor maps
     off = align_up(off + sizeof(CUtensorMap) * 32 * (size_t)n, 256);
     const size_t maxgroups = (size_t)S * n;
-    const size_t goff_off = off;
-    off = align_up(off + sizeof(int) * (maxgroups + 1), 256);
-    const size_t grp_off = off;
-    off = align_up(off + sizeof(int2) * maxgroups, 256);
+    size_t maxunits = 1;  // units of the tile shape with the most tiles
+    for (int t : shapes) {
+        size_t u = 0;
+        for (int i = 0; i < n; ++i)
+            for (int st = 0; st < S; ++st) u += (size_t)tiles[t][i][st];
+        maxunits = std::max(maxunits, u);
+    }
+    if (maxunits > 2147483647u)
+        return fail_msg(OFV_ERR_SHAPE, "ofv_compute_batched: %zu work units exceed 2^31 - 1", maxunits);
+    const size_t desc_off = off;
+    off = align_up(off + sizeof(int4) * maxunits, 256);
     const size_t done_off = off;
     off = align_up(off + sizeof(int) * (maxgroups + 2), 256);  // done counters, head, error
     const size_t ing_off = off;  // ingest descriptors of the 2n frames, then the reduce ones per level
@@ -374,8 +378,7 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
     QueueParams q;
     memset(&q, 0, sizeof q);
     q.pairs = reinterpret_cast<const BatchPair *>(base + pairs_off);
-    q.group_off = reinterpret_cast<const int *>(base + goff_off);
-    q.group = reinterpret_cast<const int2 *>(base + grp_off);
+    q.unit_desc = reinterpret_cast<const int4 *>(base + desc_off);
     q.npairs = n;
     q.L = L;
     q.IT = IT;
@@ -409,25 +412,20 @@ ofv_status batched_impl(ofv_handle *h, int n, const ofv_pair *pairs, ofv_stream_
         cudaEventCreate(&ev.a);
         cudaEventCreate(&ev.b);
     }
-    std::vector<int2> group;
-    std::vector<int> goff;
+    std::vector<int4> desc;
     // one persistent launch of candidate c (timed while tuning)
     auto run = [&](size_t c, bool timed) -> ofv_status {
         const int shape = cands[c].shape;
         const bool use_tma = ensure_maps(shape);
         if (mst != OFV_OK) return mst;
         q.tmaps = use_tma ? reinterpret_cast<const CUtensorMap *>(base + tmaps_off) : nullptr;
-        build_schedule(cands[c].schedule, S, n, tiles[shape], group, goff);
-        q.ngroups = (int)group.size();
-        q.total_units = goff.back();
+        build_schedule(cands[c].schedule, S, n, tiles[shape], desc);
+        q.total_units = (int)desc.size();
         const std::string skey = mkey + "#" + std::to_string(cands[c].schedule) + "t" + std::to_string(shape);
         e = cudaSuccess;
         if (h->batch_sched_key != skey) {  // the schedule of this layout is not in the arena yet
             if (record) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_compute_batched: recording needs the uploaded schedule");
-            e = cudaMemcpyAsync(base + goff_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice, cs);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(base + grp_off, group.data(), sizeof(int2) * group.size(), cudaMemcpyHostToDevice,
-                                    cs);
+            e = cudaMemcpyAsync(base + desc_off, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice, cs);
             h->batch_sched_key = e == cudaSuccess ? skey : std::string();
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(q.done, 0, sizeof(int) * (maxgroups + 2), cs);
@@ -567,18 +565,15 @@ ofv_status ofv_queue_selftest(int timeout_us, int *error_word)
     BatchPair bp;
     memset(&bp, 0, sizeof bp);
     bp.H[0] = bp.W[0] = bp.H[1] = bp.W[1] = 8;
-    const int goff[2] = {0, 1};
-    const int2 grp = make_int2(1, 0);  // stage 1 of pair 0: waits for stage 0, which has no units
+    // stage 1 of pair 0: waits for the one tile of stage 0, which no unit runs
+    const int4 unit = make_int4(1, 0, 0, 1);
     e = cudaMemcpy(b, &bp, sizeof bp, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + 2048, goff, sizeof goff, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + 2112, &grp, sizeof grp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + 2048, &unit, sizeof unit, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b + 3072, 0, 64);
     QueueParams q;
     memset(&q, 0, sizeof q);
     q.pairs = reinterpret_cast<const BatchPair *>(b);
-    q.group_off = reinterpret_cast<const int *>(b + 2048);
-    q.group = reinterpret_cast<const int2 *>(b + 2112);
-    q.ngroups = 1;
+    q.unit_desc = reinterpret_cast<const int4 *>(b + 2048);
     q.total_units = 1;
     q.npairs = 1;
     q.L = 2;
