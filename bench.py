@@ -345,6 +345,7 @@ def run_ours(args, ws, rank, local):
         line["paper_perf_set"] = paper_perf_set(ofv, torch, synth, dev, stream)
         line["batched_64_uneven"] = batched_uneven(ofv, torch, synth, dev, stream)
         line["backward_1Mp"] = backward_1mp(ofv, torch, frames, dev, stream)
+        line["single_pair_1Mp"] = single_pair(ofv, torch, frames, dev, stream)
 
     ofv.ofv_destroy(h)
     del u, v, frames
@@ -515,6 +516,42 @@ def sizes(ofv, torch, synth, dev, stream, frames1, u1, v1):
         if kind is not None:
             del frames, u, v
             torch.cuda.empty_cache()
+    return out
+
+
+def single_pair(ofv, torch, frames, dev, stream, reps=50):
+    """One 1 Mp pair at a time (no batching of pairs into a launch), three
+    ways: ofv_compute on a handle, ofv_compute_noalloc (the library's fixed
+    scratch array, image tiles staged by cp.async instead of TMA), and
+    ofv_compute_strips with 2 strips run one after the other on this device
+    (the layout a two-GPU split of one field uses, here without a second
+    GPU).  Times with CUDA events over reps calls each."""
+    H, W = H1, W1
+    I1, I2 = frames[0], frames[1]
+    u = torch.empty((H, W), device=dev)
+    v = torch.empty_like(u)
+    p = ofv.ofv_default_params()
+    h = ofv.ofv_create(H, W, p)
+    out = {}
+    try:
+        calls = {"ofv_compute": lambda: ofv.ofv_compute(h, I1, I2, u, v, stream),
+                 "ofv_compute_noalloc": lambda: ofv.ofv_compute_noalloc(H, W, p, None, I1, I2, u, v, stream),
+                 "ofv_compute_strips_2": lambda: ofv.ofv_compute_strips(h, 2, 8, I1, I2, u, v, stream)}
+        for name, fn in calls.items():
+            fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out[name] = {"ms_per_pair": ms, "fields_per_s": 1e3 / ms}
+    finally:
+        ofv.ofv_destroy(h)
+    out["workload"] = "the first pair of the 1 Mp stream (u16, PSL 2, KR 4, IT 3, FP32), one pair per call"
     return out
 
 
