@@ -180,10 +180,15 @@ def run_reference(args, ws, rank):
 # our arm
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
+    """Hash of the iteration kernel's sources with comments and blank lines
+    removed: it changes when the code changes, not when a comment does."""
+    import re
     h = hashlib.sha256()
     for f in ("k_block.cuh", "k_block_inst.cuh", "iter_math.cuh", "ofv_common.cuh"):
-        with open(os.path.join(ROOT, "paper_2509_25924_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2509_25924_gb300", "csrc", f)) as fh:
+            src = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines())
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
 
 

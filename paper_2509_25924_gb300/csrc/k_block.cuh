@@ -872,8 +872,11 @@ __global__ void __launch_bounds__(BlockShape<KR>::NT, BlockShape<KR>::MINB) k_it
 // iteration) stages, in one launch.  Work units (stage, pair, tile) are
 // handed out in the order of a schedule built on the host; a unit of stage
 // s waits until every tile of stage s-1 of its pair is done (a per-(stage,
-// pair) counter).  Units are claimed in schedule order by resident CTAs, so
-// every unit a CTA waits for is held by a running CTA.  The wait is bounded
+// pair) counter).  Units are claimed in schedule order by resident CTAs,
+// each CTA one unit ahead of the one it runs; a unit depends only on
+// earlier units, so the earliest unfinished unit is always being run by its
+// CTA (any unit before it in that CTA is finished) and the launch cannot
+// stall on itself.  The wait is bounded
 // by an iteration count and a %globaltimer deadline; on expiry the CTA
 // records an error word and leaves, and the host reports OFV_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
