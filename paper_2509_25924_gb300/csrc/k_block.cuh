@@ -14,7 +14,9 @@
 //      at the image border;
 //   1. the five products of every pixel of tile + halo (bilinear value and
 //      central-difference gradient of both frames at k -/+ V0/2) into
-//      shared memory; taps farther than REACH px come from global memory;
+//      shared memory; pixels whose warp reaches farther than REACH px are
+//      recomputed from global memory after the loop, which keeps the loop
+//      free of branches;
 //   2. horizontal window sums, in place, one (row, channel) per thread;
 //   3. vertical window sums, in place, one (column, channel) per thread;
 //   4. the guarded 2x2 solve per output pixel and the store of V.
