@@ -46,12 +46,17 @@ struct BlockParams {
     CUtensorMap tm[kBlockMaxBatch][2];
 };
 
-// The block kernels' templates take KS = KR + 16 V: the window radius KR
-// (1 .. 10) and the tile shape V (0: the default shape of the radius, 1: its
+// The block kernels' templates take KS = KR + 16 V + 32 Q: the window radius
+// KR (1 .. 10), the tile shape V (0: the default shape of the radius, 1: its
 // alternative, which the batched autotuner tries and ofv_params.tile_edge
-// selects).
+// selects) and Q = 1 for the persistent batched kernel, which runs 48-px
+// tiles with 512 threads instead of 576 (its queue state leaves fewer
+// registers: 576 threads spill there, +3.2 % with 512).  Each output pixel
+// is computed by the same tile with the same arithmetic whatever the thread
+// count, so the two kernels give the same fields.
 __host__ __device__ constexpr int ks_radius(int ks) { return ks & 15; }
-__host__ __device__ constexpr int ks_shape(int ks) { return ks >> 4; }
+__host__ __device__ constexpr int ks_shape(int ks) { return (ks >> 4) & 1; }
+__host__ __device__ constexpr int ks_queue(int ks) { return ks >> 5; }
 
 // Output tile edge of shape v for radius kr.  Default shapes, measured per
 // radius (1 Mp stream, fields/s): KR <= 5: 48-px tiles of 576 threads, two
@@ -68,7 +73,7 @@ __host__ __device__ constexpr int block_tile_edge(int kr, int v)
 template <int KS> struct BlockShape {
     static constexpr int R = ks_radius(KS);                // window radius
     static constexpr int TS = block_tile_edge(R, ks_shape(KS));  // output tile edge
-    static constexpr int NT = TS == 32 ? 256 : TS == 48 ? 576 : 1024;  // threads
+    static constexpr int NT = TS == 32 ? 256 : TS == 48 ? (ks_queue(KS) ? 512 : 576) : 1024;  // threads
     // resident CTAs per SM (shared memory)
     static constexpr int MINB = TS == 32 ? (R <= 5 ? 3 : 2) : TS == 48 ? 2 : 1;
     static constexpr int RW = TS + 2 * R;                 // product region edge

@@ -103,7 +103,8 @@ cudaError_t launch_queue_t(const QueueParams &q, int kr, int ctas, cudaStream_t 
     case K:              \
         if constexpr (!VAR) { X##_BODY(K) } else { break; }
 #define OFV_QUEUE_CASE(K) case K: OFV_QUEUE_CASE_BODY(K)
-#define OFV_QUEUE_CASE_BODY(K) return run_queue<T, K, VAR>(q, ctas, dev, s);
+// the persistent kernel's own thread count: KS | 32 (see BlockShape)
+#define OFV_QUEUE_CASE_BODY(K) return run_queue<T, (K) | 32, VAR>(q, ctas, dev, s);
     OFV_KS_CASES(OFV_QUEUE_CASE)
 #undef OFV_QUEUE_CASE
 #undef OFV_QUEUE_CASE_BODY
@@ -122,7 +123,7 @@ int queue_occupancy_t(int kr, int shape)
     case K:              \
         if constexpr (!VAR) { X##_BODY(K) } else { break; }
 #define OFV_OCC_CASE(K) case K: OFV_OCC_CASE_BODY(K)
-#define OFV_OCC_CASE_BODY(K) return queue_occupancy_kr<T, K, VAR>();
+#define OFV_OCC_CASE_BODY(K) return queue_occupancy_kr<T, (K) | 32, VAR>();
     OFV_KS_CASES(OFV_OCC_CASE)
 #undef OFV_OCC_CASE
 #undef OFV_OCC_CASE_BODY

@@ -1,6 +1,7 @@
 // Host-side check of the block kernel's phase-1 schedule (built and run by
 // test_block_schedule.py; no GPU needed).  For every storage type, window
-// radius and tile shape (KS = radius + 16 shape) it walks the phase-1 loop pixel by pixel, in the row order
+// radius and tile shape (KS = radius + 16 shape, + 32 for the persistent
+// kernel's thread count) it walks the phase-1 loop pixel by pixel, in the row order
 // the kernel uses, and checks that
 //   * each pixel reads staged rows inside the staged box, and only rows of
 //     TMA bands the loop has waited for by then (the waits happen before the
@@ -82,9 +83,10 @@ static int check(const char *tname)
     }
     const long mine = tap_conflicts<T, KS>(UP), other = tap_conflicts<T, KS>(!UP);
     const bool order_ok = mine <= other;
-    printf("%s KR %2d edge %2d SP %3d order %s slack %d unlanded/out-of-box reads %d conflicts %ld (other order "
-           "%ld)%s\n",
-           tname, BS::R, BS::TS, SS::SP, UP ? "up  " : "down", SLACK, bad, mine, other, bad || !order_ok ? " FAIL" : "");
+    printf("%s KR %2d edge %2d NT %4d SP %3d order %s slack %d unlanded/out-of-box reads %d conflicts %ld (other "
+           "order %ld)%s\n",
+           tname, BS::R, BS::TS, NT, SS::SP, UP ? "up  " : "down", SLACK, bad, mine, other,
+           bad || !order_ok ? " FAIL" : "");
     return bad || !order_ok;
 }
 
@@ -94,7 +96,9 @@ static int all(const char *n)
     return check<T, 1>(n) + check<T, 2>(n) + check<T, 3>(n) + check<T, 4>(n) + check<T, 5>(n) + check<T, 6>(n) +
            check<T, 7>(n) + check<T, 8>(n) + check<T, 9>(n) + check<T, 10>(n) + check<T, 17>(n) +
            check<T, 18>(n) + check<T, 19>(n) + check<T, 20>(n) + check<T, 21>(n) + check<T, 22>(n) +
-           check<T, 23>(n) + check<T, 24>(n) + check<T, 25>(n) + check<T, 26>(n);
+           check<T, 23>(n) + check<T, 24>(n) + check<T, 25>(n) + check<T, 26>(n) +
+           // the persistent kernel's forms of the 48-px tiles (512 threads)
+           check<T, 33>(n) + check<T, 34>(n) + check<T, 35>(n) + check<T, 36>(n) + check<T, 37>(n);
 }
 
 int main()

@@ -30,8 +30,9 @@ def test_phase1_band_waits_and_row_order(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
     lines = out.stdout.splitlines()
-    assert len(lines) == 61 and lines[-1] == "0 failing cases"
+    assert len(lines) == 76 and lines[-1] == "0 failing cases"
     assert sum(" edge 32 " in l for l in lines) == 3 * 10 and sum(" edge 64 " in l for l in lines) == 3 * 5
+    assert sum(" edge 48 NT  512 " in l for l in lines) == 3 * 5  # the persistent kernel's form
     # the FP32 KR 4 tile (the default configuration) runs bottom up, conflict-free
-    kr4 = [l for l in lines if l.startswith("f32  KR  4 edge 48 ")]
+    kr4 = [l for l in lines if l.startswith("f32  KR  4 edge 48 NT  576 ")]
     assert len(kr4) == 1 and "order up" in kr4[0] and " conflicts 0 " in kr4[0]
