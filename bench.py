@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=FRAMES1, help="frames in the 1 Mp stream (pairs + 1)")
     ap.add_argument("--backward-only", action="store_true",
                     help="time only the reverse mode on 1 Mp pairs of the stream (one JSON line)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="time only the 64 uneven pairs through ofv_compute_batched (one JSON line)")
     ap.add_argument("--paper-only", action="store_true",
                     help="time only the paper's benchmark parameters (u8, NR 2, KR 10, IT 3) at 1 Mp (one JSON line)")
     return ap.parse_args()
@@ -911,6 +913,15 @@ def main():
         return
     if args.backward_only:
         run_backward_only(args)
+        return
+    if args.batched_only:
+        import torch
+        import paper_2509_25924_gb300 as ofv
+        import synth
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"batched_64_uneven": batched_uneven(ofv, torch, synth, dev, torch.cuda.current_stream())}),
+              flush=True)
         return
     if args.paper_only:
         import torch
