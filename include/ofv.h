@@ -305,7 +305,8 @@ ofv_status ofv_compute_strips(ofv_handle *h, int nstrips, int max_disp, const vo
  * process exits.  It keeps no TMA tensor maps, so the iteration kernel
  * stages its image tiles by cp.async (same arithmetic, so the same field).
  * params->max_batch and params->warm_start are range-checked as ofv_create
- * checks them and otherwise ignored.  The caller passes the frames I1, I2 (H x W, params->input type),
+ * checks them and otherwise ignored; params->tile_edge is checked and used
+ * as by ofv_create.  The caller passes the frames I1, I2 (H x W, params->input type),
  * the outputs u, v (H x W float) and, when params->prefilter = 1, the 25
  * pre-filter weights w25 (device, row-major 5x5; may be NULL otherwise).
  * A request whose workspace would exceed the array (about 27 bytes per pixel
