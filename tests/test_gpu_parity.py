@@ -625,6 +625,34 @@ def test_batched_with_a_fixed_tile_edge(edge):
         ofv.ofv_destroy(h)
 
 
+@pytest.mark.parametrize("kr,storage", [(1, ofv.OFV_STORE_F32), (6, ofv.OFV_STORE_F32), (10, ofv.OFV_STORE_F16)])
+def test_batched_other_radii_and_storage(kr, storage):
+    """The persistent kernel's forms for other radii (48-px tiles at KR 1,
+    64-px tiles of 1024 threads at KR 6 and 10) and 16-bit storage: every
+    pair bitwise equal to ofv_compute with the tile edge the tuner chose."""
+    sizes = [(200, 232), (300, 420), (513, 257), (256, 256), (130, 640)]
+    data = _uneven_pairs(sizes, seed0=400 + kr)
+    p = ofv.ofv_default_params(storage=storage, levels_psl=1, kernel_radius=kr, iterations=2)
+    h = ofv.ofv_create(64, 64, p)
+    try:
+        bufs = []
+        for (I1, I2), (H, W) in zip(data, sizes):
+            bufs.append((torch.from_numpy(I1).to(DEV), torch.from_numpy(I2).to(DEV),
+                         torch.full((H, W), float("nan"), device=DEV), torch.full((H, W), float("nan"), device=DEV)))
+        ofv.ofv_compute_batched(h, bufs)
+        edge = ofv.ofv_batch_tuning(h)["tile_edge"]
+        pp = ofv.ofv_default_params(storage=storage, levels_psl=1, kernel_radius=kr, iterations=2, tile_edge=edge)
+        for (t1, t2, u, v), (H, W) in zip(bufs, sizes):
+            hh = ofv.ofv_create(H, W, pp)
+            ru = torch.empty((H, W), device=DEV); rv = torch.empty_like(ru)
+            ofv.ofv_compute(hh, t1, t2, ru, rv)
+            torch.cuda.synchronize()
+            ofv.ofv_destroy(hh)
+            assert torch.equal(u, ru) and torch.equal(v, rv), f"{H}x{W} kr {kr} edge {edge}"
+    finally:
+        ofv.ofv_destroy(h)
+
+
 def test_batched_graph_replays_the_batch_and_keeps_its_own_workspace():
     """ofv_graph_create_batched records the batch; a replay gives bitwise the
     eager batch's fields, follows new frames written into the same buffers,
