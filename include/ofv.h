@@ -395,9 +395,16 @@ ofv_status ofv_queue_selftest(int timeout_us, int *error_word);
  * every float) on stream s.  A compute call must then give bitwise the same
  * result as before: no output depends on scratch it did not write first.
  * The pre-filter weights and the region mask are state, not scratch, and
- * are kept. */
+ * are kept.
+ *
+ * ofv_debug_reciprocal(x, y, n, s): y[i] = 1 / x[i] as the fused path's
+ * 2x2 solve forms it (Eq. 2's normal equations are solved by Cramer's rule
+ * with one reciprocal of the determinant): the hardware approximation
+ * refined by one Newton-Raphson step.  x and y are device arrays of n
+ * floats; for testing its error against 1/x. */
 void ofv_debug_fail_alloc(int n);
 ofv_status ofv_debug_poison(ofv_handle *h, ofv_stream_t s);
+ofv_status ofv_debug_reciprocal(const float *x, float *y, int n, ofv_stream_t s);
 
 /* ---- CUDA-graph replay (live loop) -------------------------------------
  * A live acquisition hands the estimator a new pair into the same device

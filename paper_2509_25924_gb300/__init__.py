@@ -22,7 +22,7 @@ __all__ = [
     "ofv_compute_noalloc", "ofv_compute_strips", "ofv_strip_plan", "ofv_compute_batched", "ofv_batch_tuning",
     "ofv_graph_create",
     "ofv_graph_create_batched", "ofv_graph_launch", "ofv_graph_destroy", "ofv_backward", "ofv_vorticity", "ofv_recirculation_area", "ofv_probe",
-    "ofv_debug_fail_alloc", "ofv_debug_poison", "ofv_level_shape",
+    "ofv_debug_fail_alloc", "ofv_debug_poison", "ofv_debug_reciprocal", "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
     "Flow", "lib_path", "EXPORTED_SYMBOLS",
@@ -43,7 +43,7 @@ EXPORTED_SYMBOLS = [
     "ofv_graph_destroy", "ofv_compute_batched", "ofv_batch_tuning", "ofv_queue_selftest", "ofv_backward",
     "ofv_compute_strips", "ofv_strip_plan",
     "ofv_vorticity", "ofv_recirculation_area", "ofv_probe", "ofv_debug_fail_alloc", "ofv_debug_poison",
-    "ofv_level_shape",
+    "ofv_debug_reciprocal", "ofv_level_shape",
     "ofv_read_level",
     "ofv_profile_enable", "ofv_profile_read", "ofv_last_error", "ofv_status_string", "ofv_version",
 ]
@@ -105,6 +105,7 @@ def _load_library():
         "ofv_probe": ([I, I, I, P, P, Z, I, P, P, P], I),
         "ofv_debug_fail_alloc": ([I], None),
         "ofv_debug_poison": ([P, P], I),
+        "ofv_debug_reciprocal": ([P, P, I, P], I),
         "ofv_level_shape": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "ofv_read_level": ([P, I, I, P, P], I),
         "ofv_profile_enable": ([P, I], I),
@@ -261,6 +262,11 @@ def ofv_debug_fail_alloc(n: int):
 def ofv_debug_poison(h: int, stream=None):
     """Fill the handle's scratch with NaN bytes (state is kept)."""
     _check(_lib.ofv_debug_poison(h, _stream(stream)), "ofv_debug_poison")
+
+
+def ofv_debug_reciprocal(x, y, n: int, stream=None):
+    """y[i] = 1/x[i] as the forward solve forms it (device float arrays)."""
+    _check(_lib.ofv_debug_reciprocal(_addr(x), _addr(y), n, _stream(stream)), "ofv_debug_reciprocal")
 
 
 def ofv_recirculation_area(H: int, W: int, n: int, u, field_stride: int, mask, counts, stream=None):

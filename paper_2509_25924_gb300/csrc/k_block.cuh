@@ -616,6 +616,17 @@ __device__ __forceinline__ void window_wsums_inplace(float *line, int stride, co
     }
 }
 
+// 1/d for the solve: the MUFU approximation (rcp.approx) refined by one
+// Newton-Raphson step for the root of 1/y - d, y1 = y0 + y0 (1 - d y0), with
+// no slow path.  Normal d and 1/d only (the solve reaches it with det above
+// eps_rel (Sxx + Syy)^2 > 0); subnormals flush to zero.
+__device__ __forceinline__ float recip_newton(float d)
+{
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(d));
+    return fmaf(y0, fmaf(-d, y0, 1.f), y0);
+}
+
 // Phase 4 of the forward iteration: the guarded 2x2 solve of pixel (gx, gy)
 // from its window sums S = (Sxx, Sxy, Syy, Sxr, Syr) and the store of V.
 template <bool VAR>
@@ -630,11 +641,7 @@ struct SolveStoreT {
         if (!(tr > a.eps_abs) || det <= a.eps_rel * tr * tr) {
             V = fetch_v0_rt<COH>(a, mode, gx, gy);
         } else {
-            // reciprocal: the MUFU approximation and one Newton step
-            // y1 = y0 + y0 (1 - det y0), without a slow path
-            float y0;
-            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(det));
-            const float inv = fmaf(y0, fmaf(-det, y0, 1.f), y0);
+            const float inv = recip_newton(det);
             V = make_float2((syy * sxr - sxy * syr) * inv, (sxx * syr - sxy * sxr) * inv);
             if (VAR && a.inc) {  // increment form: V = V0(m) + H^-1 (Sxr, Syr)
                 const float2 V0 = fetch_v0_rt<COH>(a, mode, gx, gy);

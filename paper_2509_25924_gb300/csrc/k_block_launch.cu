@@ -14,6 +14,21 @@ extern template cudaError_t launch_block_t<__nv_bfloat16, true>(const BlockParam
 
 bool block_supports(int kr) { return kr >= 1 && kr <= kBlockMaxKR; }
 
+// The solve's reciprocal on its own, for its error test.
+__global__ void k_recip(const float *x, float *y, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = recip_newton(x[i]);
+}
+
+cudaError_t launch_recip(const float *x, float *y, int n, cudaStream_t s)
+{
+    if (n < 0) return cudaErrorInvalidValue;
+    if (n == 0) return cudaSuccess;
+    k_recip<<<(n + 255) / 256, 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_iter_block(const IterArgs *a, int npairs, int store, int mode, cudaStream_t s,
                               const CUtensorMap *const *tm, int *err, int by0, int nby, int shape)
 {

@@ -734,6 +734,13 @@ ofv_status ofv_destroy(ofv_handle *h)
 
 void ofv_debug_fail_alloc(int n) { g_fail_alloc.store(n > 0 ? n : 0); }
 
+ofv_status ofv_debug_reciprocal(const float *x, float *y, int n, ofv_stream_t s)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return fail_msg(OFV_ERR_INVALID_ARG, "ofv_debug_reciprocal: bad arguments");
+    const cudaError_t e = launch_recip(x, y, n, (cudaStream_t)s);
+    return e == cudaSuccess ? OFV_OK : cuda_fail_msg(e, "ofv_debug_reciprocal");
+}
+
 ofv_status ofv_debug_poison(ofv_handle *h, ofv_stream_t s)
 {
     if (!h) return fail(OFV_ERR_INVALID_ARG, "handle is NULL");

@@ -85,6 +85,8 @@ cudaError_t launch_iter_fused(const IterArgs &a, int store, int mode, cudaStream
 // staged box lies inside the image are then loaded by TMA.  err (optional):
 // device-visible word set to 1 if a TMA wait expires.
 bool block_supports(int kr);
+// The forward solve's reciprocal of x[0..n-1] into y (device arrays), for tests.
+cudaError_t launch_recip(const float *x, float *y, int n, cudaStream_t s);
 // by0, nby: tile rows by0 .. by0+nby-1 only (nby 0: to the bottom of the level).
 // shape: the tile shape (0 default, 1 the alternative; the estimator
 // variants run the default shape).

@@ -320,6 +320,26 @@ def test_alternative_tile_edge_reduced_storage(storage):
     compare(u, v, ou, ov, nd, rms_tol=REDUCED_RMS_TOL, label=f"edge 32 store={storage}")
 
 
+def test_solve_reciprocal_is_faithfully_rounded():
+    """The forward solve's 1/det (the hardware reciprocal approximation
+    refined by one Newton-Raphson step) against the correctly rounded FP32
+    reciprocal: at most one unit in the last place away, over normal
+    magnitudes 1e-37 .. 1e37 of both signs and a few exact cases."""
+    rng = np.random.default_rng(11)
+    mag = 10.0 ** rng.uniform(-37, 37, 200000)
+    x = np.concatenate([mag, -mag, [1.0, 2.0, 3.0, 0.5, 1e-37, 1e37, 1.0000001, 0.99999994]]).astype(np.float32)
+    tx = torch.from_numpy(x).to(DEV)
+    ty = torch.empty_like(tx)
+    ofv.ofv_debug_reciprocal(tx, ty, tx.numel())
+    torch.cuda.synchronize()
+    y = ty.cpu().numpy()
+    rn = (np.float32(1.0) / x).astype(np.float32)  # IEEE division: correctly rounded
+    ulps = np.abs(y.astype(np.float64) - rn.astype(np.float64)) / np.spacing(np.abs(rn)).astype(np.float64)
+    print(f"reciprocal: exact {np.mean(ulps == 0):.4%}, max {ulps.max():.2f} ulp")
+    assert np.isfinite(y).all() and ulps.max() <= 1.0
+    assert y[-8] == 1.0 and y[-7] == 0.5 and y[-5] == 2.0
+
+
 def test_u8_input_with_paper_benchmark_parameters():
     """NR 2, KR 10, IT 3 on 8-bit frames (the parameter set of the paper's
     throughput benchmark, Sec. 6), PSL 1."""
