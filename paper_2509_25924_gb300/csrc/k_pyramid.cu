@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(256) k_ingest(const __grid_constant__ FR p)
 }
 
 // The same with the boxes in shared memory: a CTA of 32 x 8 threads stages
-// its 32 x 8 pixels and the NR halo (scaled values, zero outside the image,
-// so the boxes are truncated there).  The mean comes from separable sums:
+// a 32 x 32 block (four rows per thread) and the NR halo (scaled values,
+// zero outside the image, so the boxes are truncated there).  The mean comes from separable sums:
 // row sums over 2NR+1 columns for every staged row, then 2NR+1 of them down
 // each output column.  The variance is the centred sum of (I - mu)^2 over
 // the in-image box (E[I^2] - mu^2 cancels too many digits where the box is
@@ -79,12 +79,12 @@ __global__ void __launch_bounds__(256) k_ingest(const __grid_constant__ FR p)
 template <int NRC, typename TI, typename TS, typename FR>
 __device__ __forceinline__ void ingest_norm_tile(const FR &p)
 {
-    extern __shared__ float tile[];  // (8 + 2 NR) rows of (32 + 2 NR), then (8 + 2 NR) x 32 row sums
+    extern __shared__ float tile[];  // (32 + 2 NR) rows of (32 + 2 NR), then (32 + 2 NR) x 32 row sums
     const IngestArgs &a = p.get(blockIdx.z);
     const int nr = NRC > 0 ? NRC : a.nr, K = 2 * nr + 1;
-    const int TW = 32 + 2 * nr, TH = 8 + 2 * nr;
+    const int TW = 32 + 2 * nr, TH = 32 + 2 * nr;
     float *rs = tile + TH * TW;
-    const int bx0 = blockIdx.x * 32, by0 = blockIdx.y * 8;
+    const int bx0 = blockIdx.x * 32, by0 = blockIdx.y * 32;
     if (bx0 >= a.W || by0 >= a.H) return;  // the whole CTA lies outside this frame
     const int x0 = bx0 - nr, y0 = by0 - nr;
     const TI *raw = static_cast<const TI *>(a.raw);
@@ -108,44 +108,49 @@ __device__ __forceinline__ void ingest_norm_tile(const FR &p)
         rs[t] = s1;
     }
     __syncthreads();
-    const int j = bx0 + threadIdx.x, i = by0 + threadIdx.y;
-    if (i >= a.H || j >= a.W) return;
-    const int i0 = max(i - nr, 0), i1 = min(i + nr, a.H - 1);
+    const int j = bx0 + threadIdx.x;
+    if (j >= a.W) return;
     const int j0 = max(j - nr, 0), j1 = min(j + nr, a.W - 1);
-    const float inv_n = 1.0f / (float)((i1 - i0 + 1) * (j1 - j0 + 1));
-    float s1 = 0.f;
-    if constexpr (NRC > 0) {
+#pragma unroll 1
+    for (int ly = threadIdx.y; ly < 32; ly += 8) {
+        const int i = by0 + ly;
+        if (i >= a.H) break;
+        const int i0 = max(i - nr, 0), i1 = min(i + nr, a.H - 1);
+        const float inv_n = 1.0f / (float)((i1 - i0 + 1) * (j1 - j0 + 1));
+        float s1 = 0.f;
+        if constexpr (NRC > 0) {
 #pragma unroll
-        for (int k = 0; k < 2 * NRC + 1; ++k) s1 += rs[(threadIdx.y + k) * 32 + threadIdx.x];
-    } else {
-        for (int k = 0; k < K; ++k) s1 += rs[(threadIdx.y + k) * 32 + threadIdx.x];
-    }
-    const float mu = s1 * inv_n;
-    float q = 0.f;
-    const float *box = tile + threadIdx.y * TW + threadIdx.x;  // staged (i - nr, j - nr)
-    if (NRC > 0 && i - nr >= 0 && i + nr < a.H && j - nr >= 0 && j + nr < a.W) {
+            for (int k = 0; k < 2 * NRC + 1; ++k) s1 += rs[(ly + k) * 32 + threadIdx.x];
+        } else {
+            for (int k = 0; k < K; ++k) s1 += rs[(ly + k) * 32 + threadIdx.x];
+        }
+        const float mu = s1 * inv_n;
+        float q = 0.f;
+        const float *box = tile + ly * TW + threadIdx.x;  // staged (i - nr, j - nr)
+        if (NRC > 0 && i - nr >= 0 && i + nr < a.H && j - nr >= 0 && j + nr < a.W) {
 #pragma unroll
-        for (int r = 0; r < 2 * NRC + 1; ++r)
+            for (int r = 0; r < 2 * NRC + 1; ++r)
 #pragma unroll
-            for (int c = 0; c < 2 * NRC + 1; ++c) {
-                const float d = box[r * TW + c] - mu;
-                q = fmaf(d, d, q);
-            }
-    } else {
-        for (int ii = i0; ii <= i1; ++ii) {
-            const float *row = tile + (ii - y0) * TW;
-            for (int jj = j0; jj <= j1; ++jj) {
-                const float d = row[jj - x0] - mu;
-                q = fmaf(d, d, q);
+                for (int c = 0; c < 2 * NRC + 1; ++c) {
+                    const float d = box[r * TW + c] - mu;
+                    q = fmaf(d, d, q);
+                }
+        } else {
+            for (int ii = i0; ii <= i1; ++ii) {
+                const float *row = tile + (ii - y0) * TW;
+                for (int jj = j0; jj <= j1; ++jj) {
+                    const float d = row[jj - x0] - mu;
+                    q = fmaf(d, d, q);
+                }
             }
         }
+        const float var = q * inv_n;
+        const float val = (tile[(ly + nr) * TW + threadIdx.x + nr] - mu) * rsqrtf(var + a.eps_n * a.eps_n);
+        if (a.prefilter)
+            a.tmp[(int64_t)i * a.pitch + j] = val;
+        else
+            st_store(static_cast<TS *>(a.out) + (int64_t)i * a.pitch + j, val);
     }
-    const float var = q * inv_n;
-    const float val = (tile[(threadIdx.y + nr) * TW + threadIdx.x + nr] - mu) * rsqrtf(var + a.eps_n * a.eps_n);
-    if (a.prefilter)
-        a.tmp[(int64_t)i * a.pitch + j] = val;
-    else
-        st_store(static_cast<TS *>(a.out) + (int64_t)i * a.pitch + j, val);
 }
 
 template <typename TI, typename TS, typename FR>
@@ -272,11 +277,12 @@ static cudaError_t ingest_t(const FR &p, const IngestArgs *f, int nframes, cudaS
     dim3 blk(32, 8);
     dim3 grd((W + 31) / 32, (H + 7) / 8, nframes);
     if (a.nr > 0 && a.nr <= 16) {
-        const size_t smem = sizeof(float) * (size_t)(8 + 2 * a.nr) * (32 + 2 * a.nr + 32);
+        const size_t smem = sizeof(float) * (size_t)(32 + 2 * a.nr) * (32 + 2 * a.nr + 32);
+        const dim3 grdn((W + 31) / 32, (H + 31) / 32, nframes);
         switch (a.in_type) {
-        case IN_U8: k_ingest_norm<uint8_t, TS, FR><<<grd, blk, smem, s>>>(p); break;
-        case IN_U16: k_ingest_norm<uint16_t, TS, FR><<<grd, blk, smem, s>>>(p); break;
-        default: k_ingest_norm<float, TS, FR><<<grd, blk, smem, s>>>(p); break;
+        case IN_U8: k_ingest_norm<uint8_t, TS, FR><<<grdn, blk, smem, s>>>(p); break;
+        case IN_U16: k_ingest_norm<uint16_t, TS, FR><<<grdn, blk, smem, s>>>(p); break;
+        default: k_ingest_norm<float, TS, FR><<<grdn, blk, smem, s>>>(p); break;
         }
     } else {
         switch (a.in_type) {
